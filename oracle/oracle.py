@@ -1,0 +1,265 @@
+"""Python front end of the FP64 CPU oracle (``pdf_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline arm.  The CUDA library never imports it; the two share
+no code.  ``build()`` compiles the C file with gcc (-O2, no FMA contraction, no
+fast-math, OpenMP) into ``oracle/_build/liborc.so``.
+
+Every function here only marshals numpy arrays into the C routines; the
+arithmetic is in ``pdf_oracle.c`` (see its header for the definition followed).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pdf_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle if the shared object is missing or stale."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Grid(C.Structure):
+    _fields_ = [
+        ("n_x", C.c_int), ("x_knots", C.POINTER(C.c_double)),
+        ("n_sub", C.c_int), ("n_q", C.POINTER(C.c_int)),
+        ("q_knots", C.POINTER(C.c_double)),
+        ("n_flav", C.c_int), ("pids", C.POINTER(C.c_int)),
+        ("n_members", C.c_int), ("values", C.POINTER(C.c_double)),
+        ("alphas", C.POINTER(C.c_double)),
+        ("U", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
+        ("row0", C.POINTER(C.c_int)), ("rows", C.c_int),
+    ]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int)
+_G = C.POINTER(_Grid)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_init.argtypes = [_G]
+            L.orc_init.restype = C.c_int
+            L.orc_xfxq2.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double]
+            L.orc_xfxq2.restype = C.c_double
+            L.orc_xfxq2_uw.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double, _D, _D]
+            L.orc_xfxq2_uw.restype = C.c_double
+            L.orc_xfxq2_grad.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double, _D, _D]
+            L.orc_xfxq2_grad.restype = C.c_double
+            L.orc_alphas.argtypes = [_G, C.c_double]
+            L.orc_alphas.restype = C.c_double
+            L.orc_alphas_w.argtypes = [_G, C.c_double]
+            L.orc_alphas_w.restype = C.c_double
+            L.orc_cell_weight_uw.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double]
+            L.orc_cell_weight_uw.restype = C.c_double
+            L.orc_xfxq2_batch.argtypes = [_G, C.c_int, _I, C.c_int, _D, _D, C.c_int64, _D]
+            L.orc_xfxq2_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D]
+            L.orc_alphas_batch.argtypes = [_G, _D, C.c_int64, _D]
+            L.orc_grad_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D, _D]
+            L.orc_kappa_batch.argtypes = [_G, C.c_int, _I, C.c_int, C.c_int, _D, _D,
+                                          C.c_int64, _D]
+            L.orc_dgrid_pw.argtypes = [_G, _I, _D, _D, _D, C.c_int64, _D]
+            L.orc_dgrid_batch.argtypes = [_G, _I, C.c_int, _D, _D, _D, C.c_int64, _D]
+            U8 = C.POINTER(C.c_ubyte)
+            L.orc_lumi_batch.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
+                                         C.c_int64, _D, _D]
+            L.orc_lumi_batch.restype = C.c_double
+            L.orc_lumi_dgrid.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
+                                         C.c_int64, _D]
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _i(a):
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def set_threads(n: int | None):
+    """OpenMP thread count for the batch drivers (None: leave as is)."""
+    if n is not None:
+        os.environ["OMP_NUM_THREADS"] = str(int(n))
+        try:
+            gomp = C.CDLL("libgomp.so.1")
+            gomp.omp_set_num_threads(C.c_int(int(n)))
+        except OSError:
+            pass
+
+
+class OracleGrid:
+    """A grid as the oracle sees it.  Arguments mirror the library's grid
+    description: x knots, knots per Q subgrid, Q knots (GeV, thresholds
+    duplicated), pids, values ``[members][rows][n_x][n_flav]`` and alpha_s
+    knot values ``[rows]`` (or None)."""
+
+    def __init__(self, x_knots, n_q, q_knots, pids, values, alphas=None):
+        self.x_knots = _f64(x_knots)
+        self.n_q = _i32(n_q)
+        self.q_knots = _f64(q_knots)
+        self.pids = _i32(pids)
+        v = _f64(values)
+        if v.ndim == 3:
+            v = v[None]
+        self.values = v
+        self.alphas = None if alphas is None else _f64(alphas)
+        self.U = np.empty(self.x_knots.size)
+        self.W = np.empty(self.q_knots.size)
+        self.row0 = np.empty(self.n_q.size, dtype=np.int32)
+        g = _Grid()
+        g.n_x = self.x_knots.size
+        g.x_knots = _d(self.x_knots)
+        g.n_sub = self.n_q.size
+        g.n_q = _i(self.n_q)
+        g.q_knots = _d(self.q_knots)
+        g.n_flav = self.pids.size
+        g.pids = _i(self.pids)
+        g.n_members = v.shape[0]
+        g.values = _d(self.values)
+        g.alphas = _d(self.alphas) if self.alphas is not None else None
+        g.U = _d(self.U)
+        g.W = _d(self.W)
+        g.row0 = _i(self.row0)
+        self._g = g
+        rc = lib().orc_init(C.byref(g))
+        if rc != 0:
+            raise ValueError(f"oracle grid rejected ({rc})")
+        assert self.values.shape[1:] == (g.rows, g.n_x, g.n_flav), "values shape"
+
+    @classmethod
+    def from_synth(cls, grid):
+        return cls(grid.x_knots, grid.n_q, grid.q_knots, grid.pids, grid.values, grid.alphas)
+
+    @property
+    def ptr(self):
+        return C.byref(self._g)
+
+    # -- scalar entry points
+    def xfxq2(self, pid, x, q2, member=0):
+        return lib().orc_xfxq2(self.ptr, member, int(pid), float(x), float(q2))
+
+    def xfxq2_uw(self, pid, u, w, member=0):
+        du, dw = C.c_double(), C.c_double()
+        v = lib().orc_xfxq2_uw(self.ptr, member, int(pid), float(u), float(w),
+                               C.byref(du), C.byref(dw))
+        return v, du.value, dw.value
+
+    def grad(self, pid, x, q2, member=0):
+        dx, dq2 = C.c_double(), C.c_double()
+        v = lib().orc_xfxq2_grad(self.ptr, member, int(pid), float(x), float(q2),
+                                 C.byref(dx), C.byref(dq2))
+        return v, dx.value, dq2.value
+
+    def alphas_q2(self, q2):
+        return lib().orc_alphas(self.ptr, float(q2))
+
+    def alphas_w(self, w):
+        return lib().orc_alphas_w(self.ptr, float(w))
+
+    def cell_weight(self, row, k, u, w):
+        return lib().orc_cell_weight_uw(self.ptr, int(row), int(k), float(u), float(w))
+
+    # -- batches
+    def xfxq2_batch(self, pids, x, q2, member=0):
+        pids, x, q2 = _i32(pids), _f64(x), _f64(q2)
+        out = np.empty((x.size, pids.size))
+        lib().orc_xfxq2_batch(self.ptr, member, _i(pids), pids.size, _d(x), _d(q2), x.size, _d(out))
+        return out
+
+    def xfxq2_pw(self, pid, x, q2, member=0):
+        pid, x, q2 = _i32(pid), _f64(x), _f64(q2)
+        out = np.empty(x.size)
+        lib().orc_xfxq2_pw_batch(self.ptr, member, _i(pid), _d(x), _d(q2), x.size, _d(out))
+        return out
+
+    def alphas_batch(self, q2):
+        q2 = _f64(q2)
+        out = np.empty(q2.size)
+        lib().orc_alphas_batch(self.ptr, _d(q2), q2.size, _d(out))
+        return out
+
+    def grad_pw(self, pid, x, q2, member=0):
+        pid, x, q2 = _i32(pid), _f64(x), _f64(q2)
+        dx, dq2 = np.empty(x.size), np.empty(x.size)
+        lib().orc_grad_pw_batch(self.ptr, member, _i(pid), _d(x), _d(q2), x.size, _d(dx), _d(dq2))
+        return dx, dq2
+
+    def kappa(self, pids, x, q2, member=0, pointwise=False):
+        pids, x, q2 = _i32(pids), _f64(x), _f64(q2)
+        shape = (x.size,) if pointwise else (x.size, pids.size)
+        out = np.empty(shape)
+        lib().orc_kappa_batch(self.ptr, member, _i(pids), pids.size, int(pointwise),
+                              _d(x), _d(q2), x.size, _d(out))
+        return out
+
+    def dgrid_pw(self, pid, x, q2, gw, member=0):
+        """dL/dvalues of member ``member`` for L = sum_i gw_i xf_{pid_i}."""
+        pid, x, q2, gw = _i32(pid), _f64(x), _f64(q2), _f64(gw)
+        sub = OracleGrid(self.x_knots, self.n_q, self.q_knots, self.pids,
+                         self.values[member:member + 1], self.alphas)
+        grad = np.zeros(self.values.shape[1:])
+        lib().orc_dgrid_pw(sub.ptr, _i(pid), _d(x), _d(q2), _d(gw), x.size, _d(grad))
+        return grad
+
+    def dgrid(self, pids, x, q2, gout):
+        pids, x, q2, gout = _i32(pids), _f64(x), _f64(q2), _f64(gout)
+        grad = np.zeros(self.values.shape[1:])
+        lib().orc_dgrid_batch(self.ptr, _i(pids), pids.size, _d(x), _d(q2), _d(gout),
+                              x.size, _d(grad))
+        return grad
+
+    def lumi(self, ev, member=0, n=None):
+        n = ev.ln_tau.size if n is None else int(n)
+        lt, y = _f64(ev.ln_tau[:n]), _f64(ev.y[:n])
+        fl = np.ascontiguousarray(ev.flags[:n], dtype=np.uint8)
+        lm, lx = _f64(ev.ln_mu2[:n]), _f64(ev.ln_x1[:n])
+        lum, a_s = np.empty(n), np.empty(n)
+        L = lib().orc_lumi_batch(self.ptr, member, _d(lt), _d(y),
+                                 fl.ctypes.data_as(C.POINTER(C.c_ubyte)), _d(lm), _d(lx),
+                                 float(ev.ln_s), n, _d(lum), _d(a_s))
+        return L, lum, a_s
+
+    def lumi_dgrid(self, ev, member=0, n=None):
+        n = ev.ln_tau.size if n is None else int(n)
+        lt, y = _f64(ev.ln_tau[:n]), _f64(ev.y[:n])
+        fl = np.ascontiguousarray(ev.flags[:n], dtype=np.uint8)
+        lm, lx = _f64(ev.ln_mu2[:n]), _f64(ev.ln_x1[:n])
+        grad = np.zeros(self.values.shape[1:])
+        lib().orc_lumi_dgrid(self.ptr, member, _d(lt), _d(y),
+                             fl.ctypes.data_as(C.POINTER(C.c_ubyte)), _d(lm), _d(lx),
+                             float(ev.ln_s), n, _d(grad))
+        return grad
