@@ -1,0 +1,234 @@
+/*
+ * pdfgpu — batched FP64 parton-density (x*f) and alpha_s interpolation on a
+ * GB300 GPU (sm_103a), the data-parallel hot path of PDFFlow
+ * (Rossi, Carrazza, Cruz-Martinez, arXiv:2012.08221).
+ *
+ * What is computed (PDFFlow Sec. 2.1: a set of flavours {a} and two arrays of
+ * equal length, x_i and Q_i, in; an array of interpolated values out; alpha_s
+ * interpolated the same way; Sec. 4: the LHAPDF grid layout and algorithms):
+ *
+ *   x*f_a(x, Q^2) by log-bicubic interpolation in (ln x, ln Q^2) on a grid of
+ *   knot values.  Q knots are split into subgrids at flavour thresholds; the
+ *   threshold knot is stored twice (last knot of subgrid s == first knot of
+ *   s+1) and interpolation never crosses a subgrid.  Along each axis the
+ *   interval cubic is the Hermite cubic whose knot derivatives are finite
+ *   differences: a one-sided secant at the first and last knot of an axis
+ *   (or subgrid), the mean of the two adjacent secants inside.  The interval
+ *   is the largest knot k with z_k <= z, clamped to the last interval; a Q^2
+ *   equal to an internal threshold belongs to the upper subgrid.  Outside the
+ *   grid the result continues linearly in ln x (from the two edge x columns)
+ *   and in ln Q^2 (from the two edge rows of the lowest/highest subgrid).
+ *   alpha_s(Q^2) is the same cubic in ln Q^2 on the alpha_s knot values.
+ *
+ * Conventions for every entry point:
+ *   - Return PDF_OK (0) or a negative PDF_E_* code; nothing is thrown across
+ *     the boundary.  pdf_last_error() gives a message for the calling thread.
+ *   - Arrays documented as DEVICE are device pointers owned by the caller;
+ *     the library only reads/writes them inside kernels launched on `stream`
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *     Calls are asynchronous unless documented otherwise.
+ *   - Arrays documented as HOST are read during the call (copied) unless
+ *     documented otherwise.
+ *   - Per-element domain errors do not fail a call: x <= 0, x > 1, Q^2 <= 0,
+ *     Q^2 infinite or any NaN input gives NaN for every requested flavour and
+ *     sets PDF_S_DOMAIN in the grid's status word.  A pid absent from the grid
+ *     gives 0 (pid 21 and pid 0 both mean the gluon).  n == 0 is a no-op.
+ *   - The output is x*f, not f (the paper's luminosity divides by x1*x2).
+ */
+#ifndef PDFGPU_H
+#define PDFGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pdfgpu_grid *pdfgpu_grid_t;     /* opaque, library-owned */
+typedef struct pdfgpu_batch *pdfgpu_batch_t;   /* opaque, library-owned */
+typedef void *pdfgpu_stream_t;                 /* a cudaStream_t */
+
+enum {
+    PDF_OK = 0,
+    PDF_E_ARG = -1,       /* null pointer, negative size, bad member, too many pids */
+    PDF_E_DESC = -2,      /* malformed grid description (knots, sizes, thresholds)   */
+    PDF_E_CUDA = -3,      /* a CUDA runtime call failed (message has the CUDA error)  */
+    PDF_E_UNBOUND = -4,   /* the grid has no values yet (pdf_bind_values not called)  */
+    PDF_E_NOMEM = -5,     /* device or host allocation failed                         */
+    PDF_E_RANGE = -6      /* a size exceeds a documented limit                        */
+};
+
+/* Status bits accumulated by kernels in the grid's device status word. */
+enum {
+    PDF_S_DOMAIN = 1u     /* some input x / Q^2 was out of the domain (output NaN)   */
+};
+
+#define PDF_MAX_PIDS 64   /* flavours per matrix-form call                  */
+#define PDF_MAX_FLAV 64   /* flavours stored in one grid                    */
+
+/* Grid description: every pointer is HOST memory, read and copied by
+ * pdf_load_grid.  Knots are in GeV (Q, not Q^2).
+ *   x_knots [n_x]          strictly ascending, 0 < x_k <= 1, n_x >= 2
+ *   n_q     [n_sub]        knots per Q subgrid, each >= 2
+ *   q_knots [sum n_q]      strictly ascending inside a subgrid; the last knot of
+ *                          subgrid s equals the first knot of s+1 (duplicated)
+ *   pids    [n_flav]       PDG ids, distinct; 0 or 21 is the gluon
+ *   values  [n_members][sum n_q][n_x][n_flav]  x*f at the knots (row-major),
+ *                          or NULL: bind later with pdf_bind_values
+ *   alphas  [sum n_q]      alpha_s at the Q knots, or NULL (no alpha_s)      */
+typedef struct {
+    int32_t n_x;
+    const double *x_knots;
+    int32_t n_sub;
+    const int32_t *n_q;
+    const double *q_knots;
+    int32_t n_flav;
+    const int32_t *pids;
+    int32_t n_members;
+    const double *values;
+    const double *alphas;
+} pdfgpu_grid_desc;
+
+/* Validate a grid description, upload it and build the interpolation tables
+ * on the current CUDA device (PDFFlow Sec. 2.1 `mkPDF`; Sec. 4 grid format).
+ * Synchronous.  On success *out owns device memory until pdf_free_grid. */
+int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out);
+
+/* (Re)build the per-cell bicubic coefficients of ALL members from a DEVICE
+ * array `dev_values` laid out as the description's `values`.  Used when the
+ * values live in a device tensor that changes (a fit).  The array is read on
+ * `stream` during the call and not kept.  Asynchronous on `stream`. */
+int pdf_bind_values(pdfgpu_grid_t g, const double *dev_values, pdfgpu_stream_t stream);
+
+/* Free every device allocation of the grid.  Synchronises the device. */
+int pdf_free_grid(pdfgpu_grid_t g);
+
+/* Sizes of a loaded grid (any pointer may be NULL). */
+int pdf_grid_info(pdfgpu_grid_t g, int32_t *n_x, int32_t *n_rows, int32_t *n_flav,
+                  int32_t *n_members, int32_t *has_alphas);
+
+/* Batched x*f for a shared pid list (PDFFlow Sec. 2.1; `xfxQ2(pids, x, q2)` of
+ * the luminosity example, Sec. 3.2).
+ *   member            0 <= member < n_members (member 0 = central replica)
+ *   pids   HOST  [n_pid], 1 <= n_pid <= PDF_MAX_PIDS
+ *   x, q2  DEVICE [n]
+ *   out    DEVICE [n][n_pid] row-major                                       */
+int xfxQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+          const double *x, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream);
+
+/* Same with Q instead of Q^2 (PDFFlow Sec. 2.1 `py_xfxQ`): Q^2 = q*q. */
+int xfxQ(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+         const double *x, const double *q, int64_t n, double *out, pdfgpu_stream_t stream);
+
+/* Pointwise form: one pid per point.
+ *   pid DEVICE [n], x, q2 DEVICE [n], out DEVICE [n]                         */
+int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
+             const double *q2, int64_t n, double *out, pdfgpu_stream_t stream);
+
+/* alpha_s(Q^2) (PDFFlow Sec. 2.1, `py_alphasQ`).  q2, out DEVICE [n].
+ * PDF_E_DESC if the grid was loaded without alpha_s values. */
+int alphasQ2(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream);
+int alphasQ(pdfgpu_grid_t g, const double *q, int64_t n, double *out, pdfgpu_stream_t stream);
+
+/* End-to-end form of xfxQ2 for HOST buffers: x, q2 HOST [n], out HOST
+ * [n][n_pid].  The library streams the points through device staging buffers
+ * it owns (chunks overlapped on internal streams), and returns when `out` is
+ * complete (synchronous).  Pinned host memory gives full copy bandwidth. */
+int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+               const double *x, const double *q2, int64_t n, double *out);
+
+/* Adjoint of xfxQ2 / xfxQ2_pw (the derivative PDF fits need).
+ * For L = sum_i sum_p grad_out[i][p] * xf_{pid_p}(x_i, Q^2_i):
+ *   pointwise == 0: pids HOST [n_pid] (shared), grad_out DEVICE [n][n_pid]
+ *   pointwise != 0: pids DEVICE [n] (one per point, n_pid ignored), grad_out DEVICE [n]
+ *   grad_x  DEVICE [n] or NULL: dL/dx_i      (overwritten)
+ *   grad_q2 DEVICE [n] or NULL: dL/dQ^2_i    (overwritten)
+ *   grad_values DEVICE [n_rows][n_x][n_flav] of `member`, or NULL: dL/dvalues,
+ *     ACCUMULATED (+=) with FP64 atomics (summation order is not fixed).
+ * Domain errors give NaN in grad_x / grad_q2 and add nothing to grad_values. */
+int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                   int32_t pointwise, const double *x, const double *q2, int64_t n,
+                   const double *grad_out, double *grad_x, double *grad_q2,
+                   double *grad_values, pdfgpu_stream_t stream);
+
+/* One request of a batched evaluation (several grids, members, flavour
+ * subsets and sizes in one launch).  grid/member/pids are read at prepare
+ * time; x, q2, out are DEVICE pointers that must stay valid while the batch
+ * exists (the launch reads and writes them on every pdf_batch_run). */
+typedef struct {
+    pdfgpu_grid_t grid;
+    int32_t member;
+    int32_t n_pid;                  /* 1..16 */
+    int32_t pids[16];
+    const double *x;
+    const double *q2;
+    int64_t n;
+    double *out;                    /* [n][n_pid] */
+} pdfgpu_batch_desc;
+
+/* Prepare a batched evaluation: choose the launch shape with the autotuner
+ * (block size, points per thread, shared-memory staging of the knot tables;
+ * results cached per workload signature in the JSON file named by
+ * $PDFGPU_TUNE_CACHE, if set), upload the request table and capture one
+ * persistent launch in a CUDA graph (the counterpart of PDFFlow's `trace()`
+ * warm-up, Sec. 2.1).  Tuning runs the kernel on `stream` (outputs are
+ * written).  Synchronous. */
+int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc, int32_t autotune,
+                      pdfgpu_stream_t stream, pdfgpu_batch_t *out);
+
+/* Replay the captured launch on `stream`: evaluates every request. */
+int pdf_batch_run(pdfgpu_batch_t b, pdfgpu_stream_t stream);
+
+/* Chosen launch shape: threads per block, points per thread, staging flag,
+ * persistent CTAs, and the tuned time of one launch (ms). */
+int pdf_batch_info(pdfgpu_batch_t b, int32_t *block, int32_t *qpt, int32_t *stage,
+                   int32_t *ctas, float *ms);
+int pdf_batch_free(pdfgpu_batch_t b);
+
+/* Fused parton-luminosity workload (PDFFlow Sec. 3.1-3.2: event kinematics,
+ * two xfxQ2 calls, luminosity formed from the products).  Per event e:
+ *   ln x1 = ln_tau/2 + y, ln x2 = ln_tau/2 - y, ln Q^2 = ln_tau + ln_s;
+ *   flags bit 0: ln Q^2 = ln_mu2[e]; flags bit 1: ln x1 = ln_x1[e];
+ *   lum[e] = sum_a xf_a(x1, Q^2) * xf_{-a}(x2, Q^2) over the grid's pids
+ *            (the gluon pairs with itself);  alphas[e] = alpha_s(Q^2).
+ *   *L = (1/n) sum_e lum[e], summed in a fixed order (deterministic).
+ * Inputs DEVICE [n]: ln_tau, y, flags (uint8); ln_mu2, ln_x1 may be NULL when
+ * no flag uses them.  Outputs DEVICE: lum [n] or NULL, alphas [n] or NULL
+ * (NULL also when the grid has no alpha_s), L one double.  Uses library-owned
+ * scratch of the grid handle for the block partial sums: calls on the same
+ * grid must not overlap in time. */
+int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double *y,
+             const uint8_t *flags, const double *ln_mu2, const double *ln_x1, double ln_s,
+             int64_t n, double *lum, double *alphas, double *L, pdfgpu_stream_t stream);
+
+/* dL/dvalues of `member` for L of pdf_lumi, times the HOST scalar dL:
+ * grad_values DEVICE [n_rows][n_x][n_flav], ACCUMULATED (+=). */
+int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double *y,
+                      const uint8_t *flags, const double *ln_mu2, const double *ln_x1,
+                      double ln_s, int64_t n, double dL, double *grad_values,
+                      pdfgpu_stream_t stream);
+
+/* Read and clear the grid's status word (PDF_S_* bits).  Synchronises
+ * `stream` first. */
+int pdf_get_status(pdfgpu_grid_t g, pdfgpu_stream_t stream, uint32_t *bits);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pdf_last_error(void);
+
+/* Measurement helpers (not part of the interpolation):
+ * FP64 FMA throughput of this GPU in FLOP/s (2 per FMA), from a kernel of
+ * independent fused multiply-add chains timed with CUDA events. Synchronous. */
+int pdf_probe_fp64_peak(double *flops);
+
+/* The kernels' natural log (table-driven argument reduction after
+ * P. T. P. Tang, ACM TOMS 16 (1990) 378, with a degree-5 series for
+ * ln(1+r), |r| <= 2^-11) applied to n DEVICE doubles: out[i] = ln(in[i]) for
+ * positive finite in[i].  Exposed for tests. */
+int pdf_debug_log(pdfgpu_grid_t g, const double *in, int64_t n, double *out,
+                  pdfgpu_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDFGPU_H */

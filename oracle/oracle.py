@@ -82,14 +82,14 @@ def lib():
             L.orc_grad_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D, _D]
             L.orc_kappa_batch.argtypes = [_G, C.c_int, _I, C.c_int, C.c_int, _D, _D,
                                           C.c_int64, _D]
-            L.orc_dgrid_pw.argtypes = [_G, _I, _D, _D, _D, C.c_int64, _D]
-            L.orc_dgrid_batch.argtypes = [_G, _I, C.c_int, _D, _D, _D, C.c_int64, _D]
+            L.orc_dgrid_pw.argtypes = [_G, _I, _D, _D, _D, C.c_int64, _D, C.c_int]
+            L.orc_dgrid_batch.argtypes = [_G, _I, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_int]
             U8 = C.POINTER(C.c_ubyte)
             L.orc_lumi_batch.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
                                          C.c_int64, _D, _D]
             L.orc_lumi_batch.restype = C.c_double
             L.orc_lumi_dgrid.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
-                                         C.c_int64, _D]
+                                         C.c_int64, _D, C.c_int]
             _lib = L
     return _lib
 
@@ -226,20 +226,19 @@ class OracleGrid:
                               _d(x), _d(q2), x.size, _d(out))
         return out
 
-    def dgrid_pw(self, pid, x, q2, gw, member=0):
-        """dL/dvalues of member ``member`` for L = sum_i gw_i xf_{pid_i}."""
+    def dgrid_pw(self, pid, x, q2, gw, absval=False):
+        """dL/dvalues for L = sum_i gw_i xf_{pid_i} (the weights do not depend
+        on the member).  absval: the sum of |term| instead (tolerance scale)."""
         pid, x, q2, gw = _i32(pid), _f64(x), _f64(q2), _f64(gw)
-        sub = OracleGrid(self.x_knots, self.n_q, self.q_knots, self.pids,
-                         self.values[member:member + 1], self.alphas)
         grad = np.zeros(self.values.shape[1:])
-        lib().orc_dgrid_pw(sub.ptr, _i(pid), _d(x), _d(q2), _d(gw), x.size, _d(grad))
+        lib().orc_dgrid_pw(self.ptr, _i(pid), _d(x), _d(q2), _d(gw), x.size, _d(grad), int(absval))
         return grad
 
-    def dgrid(self, pids, x, q2, gout):
+    def dgrid(self, pids, x, q2, gout, absval=False):
         pids, x, q2, gout = _i32(pids), _f64(x), _f64(q2), _f64(gout)
         grad = np.zeros(self.values.shape[1:])
         lib().orc_dgrid_batch(self.ptr, _i(pids), pids.size, _d(x), _d(q2), _d(gout),
-                              x.size, _d(grad))
+                              x.size, _d(grad), int(absval))
         return grad
 
     def lumi(self, ev, member=0, n=None):
@@ -253,7 +252,7 @@ class OracleGrid:
                                  float(ev.ln_s), n, _d(lum), _d(a_s))
         return L, lum, a_s
 
-    def lumi_dgrid(self, ev, member=0, n=None):
+    def lumi_dgrid(self, ev, member=0, n=None, absval=False):
         n = ev.ln_tau.size if n is None else int(n)
         lt, y = _f64(ev.ln_tau[:n]), _f64(ev.y[:n])
         fl = np.ascontiguousarray(ev.flags[:n], dtype=np.uint8)
@@ -261,5 +260,5 @@ class OracleGrid:
         grad = np.zeros(self.values.shape[1:])
         lib().orc_lumi_dgrid(self.ptr, member, _d(lt), _d(y),
                              fl.ctypes.data_as(C.POINTER(C.c_ubyte)), _d(lm), _d(lx),
-                             float(ev.ln_s), n, _d(grad))
+                             float(ev.ln_s), n, _d(grad), int(absval))
         return grad

@@ -400,9 +400,11 @@ void orc_kappa_batch(const orc_grid *g, int member, const int *pids, int n_pid, 
 }
 
 /* dL/dvalues for L = sum_i gw_i * xf_{pid_i}(x_i, Q^2_i), accumulated into
- * grad[rows][n_x][n_flav] (member's slice).  Serial: the sum order is fixed. */
+ * grad[rows][n_x][n_flav] (member's slice).  Serial: the sum order is fixed.
+ * absval != 0 accumulates |gw_i * weight| instead: the magnitude of the terms
+ * of each sum, used to scale rounding tolerances. */
 void orc_dgrid_pw(const orc_grid *g, const int *pid, const double *x, const double *q2,
-                  const double *gw, int64_t n, double *grad)
+                  const double *gw, int64_t n, double *grad, int absval)
 {
     for (int64_t i = 0; i < n; ++i) {
         int col = pid_column(g, pid[i]);
@@ -413,14 +415,15 @@ void orc_dgrid_pw(const orc_grid *g, const int *pid, const double *x, const doub
         for (int r = r0; r <= r1; ++r)
             for (int k = c0; k <= c1; ++k) {
                 double wt = orc_cell_weight_uw(g, r, k, u, w);
-                grad[((size_t)r * g->n_x + k) * g->n_flav + col] += gw[i] * wt;
+                double t = gw[i] * wt;
+                grad[((size_t)r * g->n_x + k) * g->n_flav + col] += absval ? fabs(t) : t;
             }
     }
 }
 
 /* Matrix form: gradient of L = sum_i sum_p gout[i][p] * xf_{pids[p]}(x_i, Q^2_i). */
 void orc_dgrid_batch(const orc_grid *g, const int *pids, int n_pid, const double *x,
-                     const double *q2, const double *gout, int64_t n, double *grad)
+                     const double *q2, const double *gout, int64_t n, double *grad, int absval)
 {
     for (int64_t i = 0; i < n; ++i) {
         if (bad_x(x[i]) || bad_q2(q2[i])) continue;
@@ -434,7 +437,8 @@ void orc_dgrid_batch(const orc_grid *g, const int *pids, int n_pid, const double
                 for (int p = 0; p < n_pid; ++p) {
                     int col = pid_column(g, pids[p]);
                     if (col < 0) continue;
-                    grad[((size_t)r * g->n_x + k) * g->n_flav + col] += gout[i * n_pid + p] * wt;
+                    double t = gout[i * n_pid + p] * wt;
+                    grad[((size_t)r * g->n_x + k) * g->n_flav + col] += absval ? fabs(t) : t;
                 }
             }
     }
@@ -484,7 +488,7 @@ double orc_lumi_batch(const orc_grid *g, int member, const double *ln_tau, const
 /* dL/dvalues (member's slice) for L = (1/N) sum_e lum_e. */
 void orc_lumi_dgrid(const orc_grid *g, int member, const double *ln_tau, const double *y,
                     const unsigned char *flags, const double *ln_mu2, const double *ln_x1,
-                    double ln_s, int64_t n, double *grad)
+                    double ln_s, int64_t n, double *grad, int absval)
 {
     int F = g->n_flav;
     double f1[64], f2[64];
@@ -510,7 +514,8 @@ void orc_lumi_dgrid(const orc_grid *g, int member, const double *ln_tau, const d
                          * side 1 (-a = b): f_{-b}(x1) times weight at x2. */
                         int cb = pid_column(g, -g->pids[b]);
                         if (cb < 0) continue;
-                        grad[((size_t)r * g->n_x + k) * F + b] += wt * other[cb] / (double)n;
+                        double t = wt * other[cb] / (double)n;
+                        grad[((size_t)r * g->n_x + k) * F + b] += absval ? fabs(t) : t;
                     }
                 }
         }

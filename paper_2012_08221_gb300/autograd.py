@@ -1,0 +1,79 @@
+"""torch.autograd bindings of the adjoint kernels.
+
+``XfxQ2Fn`` evaluates x*f with the grid values as a differentiable tensor:
+the forward rebuilds the interpolation coefficients from the tensor and runs
+the forward kernel; the backward runs the hand-written adjoint kernel, which
+returns dL/dx, dL/dQ^2 and the scatter of the 16 bicubic stencil weights
+into dL/dvalues (the derivative a PDF fit needs).  ``LumiFn`` does the same
+for the fused luminosity workload, L = (1/n) sum_e sum_a f_a(x1) f_-a(x2).
+"""
+from __future__ import annotations
+
+import torch
+
+from .pdf import PDF
+
+
+class XfxQ2Fn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, values, x, q2, pdf: PDF, pids, member: int, pointwise: bool):
+        pdf.bind_values(values)
+        if pointwise:
+            out = pdf.xfxQ2_pw(pids, x, q2, member)
+        else:
+            out = pdf.xfxQ2(pids, x, q2, member)
+        ctx.save_for_backward(values, x, q2)
+        ctx.pdf, ctx.pids, ctx.member, ctx.pointwise = pdf, pids, member, pointwise
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        values, x, q2 = ctx.saved_tensors
+        pdf: PDF = ctx.pdf
+        need_v, need_x, need_q = ctx.needs_input_grad[:3]
+        pdf.bind_values(values)           # the coefficients of these values
+        gvals = None
+        gslice = None
+        if need_v:
+            gvals = torch.zeros_like(values)
+            gslice = gvals[ctx.member] if values.dim() == 4 else gvals
+        gx, gq, _ = pdf.xfxQ2_backward(ctx.pids, x, q2, gout, ctx.member, ctx.pointwise,
+                                       grad_x=need_x, grad_q2=need_q, grad_values=gslice)
+        return gvals, gx, gq, None, None, None, None
+
+
+def xfxQ2(pdf: PDF, values, pids, x, q2, member: int = 0):
+    """Differentiable x*f for a shared pid list: ``[n][len(pids)]``."""
+    return XfxQ2Fn.apply(values, x, q2, pdf, pids, member, False)
+
+
+def xfxQ2_pw(pdf: PDF, values, pid, x, q2, member: int = 0):
+    """Differentiable x*f with one pid per point: ``[n]``."""
+    return XfxQ2Fn.apply(values, x, q2, pdf, pid, member, True)
+
+
+class LumiFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, values, pdf: PDF, events, member: int):
+        from .lumi import luminosity
+        pdf.bind_values(values)
+        L, lum, a_s = luminosity(pdf, events, member, want_lum=False, want_alphas=False)
+        ctx.save_for_backward(values)
+        ctx.pdf, ctx.events, ctx.member = pdf, events, member
+        return L
+
+    @staticmethod
+    def backward(ctx, gL):
+        from .lumi import luminosity_backward
+        (values,) = ctx.saved_tensors
+        pdf = ctx.pdf
+        pdf.bind_values(values)
+        gvals = torch.zeros_like(values)
+        gslice = gvals[ctx.member] if values.dim() == 4 else gvals
+        luminosity_backward(pdf, ctx.events, float(gL.item()), gslice, ctx.member)
+        return gvals, None, None, None
+
+
+def lumi(pdf: PDF, values, events, member: int = 0):
+    """Differentiable luminosity L(values) of the event sample."""
+    return LumiFn.apply(values, pdf, events, member)

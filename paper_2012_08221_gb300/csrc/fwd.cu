@@ -1,0 +1,271 @@
+// Forward kernels: x*f for a shared pid list (matrix form), for one pid per
+// point (pointwise form), alpha_s, and the host-buffer pipeline.
+//
+// PDFFlow Sec. 2.1: the query is a flavour set plus equal-length arrays of x
+// and Q; the answer is one interpolated value per point and flavour.
+#include <math.h>
+
+#include <algorithm>
+
+#include "pdf_internal.h"
+
+using namespace pdfgpu;
+
+namespace {
+
+constexpr int kBlock = 256;
+__device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000000000000ll); }
+
+// One point per thread (grid-stride over blocks).  Results of a block are
+// staged in shared memory and written out as one contiguous, coalesced run
+// of npid * blockDim doubles (the output is [n][npid] row-major).
+template <bool Q_IS_Q>
+__global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid, int member,
+                                                  const double *__restrict__ x,
+                                                  const double *__restrict__ q,
+                                                  int64_t n, double *__restrict__ out)
+{
+    extern __shared__ double sout[];
+    __shared__ signed char scol[PDF_MAX_PIDS];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < PDF_MAX_PIDS; ++k) scol[k] = cols.c[k];
+    }
+    __syncthreads();
+    const size_t cell_stride = (size_t)g.nflav * 16;
+    const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        bool live = i < n;
+        double xi = live ? x[i] : 0.5;
+        double qi = live ? q[i] : 10.0;
+        if (Q_IS_Q) qi = qi * qi;
+        bool bad = live && !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
+        flag_status(g, bad);
+        if (bad) {
+            xi = 0.5;
+            qi = 10.0;
+        }
+        double u, w;
+        Axis X = axis_x(g, xi, &u);
+        Axis Q = axis_q2(g, qi, &w);
+        const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
+        double *srow = sout + threadIdx.x * npid;
+        for (int a = 0; a < npid; ++a) {
+            int col = scol[a];
+            double v = col >= 0 ? patch(cell + col * 16, X, Q) : 0.0;
+            srow[a] = bad ? qnan() : v;
+        }
+        __syncthreads();
+        int64_t rows = min((int64_t)blockDim.x, n - base);
+        int64_t cnt = rows * npid;
+        double *dst = out + base * npid;
+        for (int64_t k = threadIdx.x; k < cnt; k += blockDim.x) dst[k] = sout[k];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
+                                                     const int *__restrict__ pid,
+                                                     const double *__restrict__ x,
+                                                     const double *__restrict__ q2,
+                                                     int64_t n, double *__restrict__ out)
+{
+    const size_t cell_stride = (size_t)g.nflav * 16;
+    const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double xi = x[i], qi = q2[i];
+        int col = pid_col(g, pid[i]);
+        bool bad = !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
+        flag_status(g, bad);
+        if (bad) {
+            xi = 0.5;
+            qi = 10.0;
+        }
+        double u, w;
+        Axis X = axis_x(g, xi, &u);
+        Axis Q = axis_q2(g, qi, &w);
+        double v = 0.0;
+        if (col >= 0) v = patch(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
+        out[i] = bad ? qnan() : v;
+    }
+}
+
+template <bool Q_IS_Q>
+__global__ void __launch_bounds__(kBlock) k_alphas(GridDev g, const double *__restrict__ q,
+                                                   int64_t n, double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double qi = q[i];
+        if (Q_IS_Q) qi = qi * qi;
+        bool bad = !q2_ok(dbits(qi));
+        flag_status(g, bad);
+        if (bad) qi = 10.0;
+        double w;
+        Axis Q = axis_q2(g, qi, &w);
+        const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
+        double2 a01 = __ldg(A), a23 = __ldg(A + 1);
+        double v = fma(Q.b3, a23.y, fma(Q.b2, a23.x, fma(Q.t, a01.y, a01.x)));
+        out[i] = bad ? qnan() : v;
+    }
+}
+
+__global__ void k_log(GridDev g, const double *__restrict__ in, int64_t n, double *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = dlog(g, in[i]);
+}
+
+int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n_pid,
+                  const double *x, const double *q, int64_t n, double *out, cudaStream_t s,
+                  bool q_is_q)
+{
+    clear_error();
+    int rc = check_grid(g, true);
+    if (rc) return rc;
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
+    Cols cols;
+    rc = resolve_cols(g, pids, n_pid, &cols);
+    if (rc) return rc;
+    if (n == 0) return PDF_OK;
+    if (!x || !q || !out) return fail(PDF_E_ARG, "null array");
+    size_t smem = (size_t)kBlock * n_pid * sizeof(double);
+    const void *kern = q_is_q ? (const void *)k_xfxq2<true> : (const void *)k_xfxq2<false>;
+    if (smem > 48 * 1024) PDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int grid = wave_grid(g, kern, kBlock, smem, n);
+    if (q_is_q)
+        k_xfxq2<true><<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out);
+    else
+        k_xfxq2<false><<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
+int launch_alphas(pdfgpu_grid *g, const double *q, int64_t n, double *out, cudaStream_t s, bool q_is_q)
+{
+    clear_error();
+    int rc = check_grid(g, false);
+    if (rc) return rc;
+    if (!g->has_alphas) return fail(PDF_E_DESC, "grid has no alpha_s values");
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (n == 0) return PDF_OK;
+    if (!q || !out) return fail(PDF_E_ARG, "null array");
+    const void *kern = q_is_q ? (const void *)k_alphas<true> : (const void *)k_alphas<false>;
+    int grid = wave_grid(g, kern, kBlock, 0, n);
+    if (q_is_q)
+        k_alphas<true><<<grid, kBlock, 0, s>>>(g->d, q, n, out);
+    else
+        k_alphas<false><<<grid, kBlock, 0, s>>>(g->d, q, n, out);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
+}  // namespace
+
+extern "C" int xfxQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                     const double *x, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
+{
+    return launch_matrix(g, member, pids, n_pid, x, q2, n, out, (cudaStream_t)stream, false);
+}
+
+extern "C" int xfxQ(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                    const double *x, const double *q, int64_t n, double *out, pdfgpu_stream_t stream)
+{
+    return launch_matrix(g, member, pids, n_pid, x, q, n, out, (cudaStream_t)stream, true);
+}
+
+extern "C" int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
+                        const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
+{
+    clear_error();
+    int rc = check_grid(g, true);
+    if (rc) return rc;
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
+    if (n == 0) return PDF_OK;
+    if (!pid || !x || !q2 || !out) return fail(PDF_E_ARG, "null array");
+    int grid = wave_grid(g, (const void *)k_xfxq2_pw, kBlock, 0, n);
+    k_xfxq2_pw<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, member, pid, x, q2, n, out);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
+extern "C" int alphasQ2(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
+{
+    return launch_alphas(g, q2, n, out, (cudaStream_t)stream, false);
+}
+
+extern "C" int alphasQ(pdfgpu_grid_t g, const double *q, int64_t n, double *out, pdfgpu_stream_t stream)
+{
+    return launch_alphas(g, q, n, out, (cudaStream_t)stream, true);
+}
+
+extern "C" int pdf_debug_log(pdfgpu_grid_t g, const double *in, int64_t n, double *out,
+                             pdfgpu_stream_t stream)
+{
+    clear_error();
+    int rc = check_grid(g, false);
+    if (rc) return rc;
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (n == 0) return PDF_OK;
+    if (!in || !out) return fail(PDF_E_ARG, "null array");
+    int grid = wave_grid(g, (const void *)k_log, kBlock, 0, n);
+    k_log<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, in, n, out);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
+// Host buffers: chunks of points flow through three device staging slots on
+// three internal streams, so the copy-in of one chunk, the kernel of the
+// next and the copy-out of a third overlap.
+extern "C" int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                          const double *x, const double *q2, int64_t n, double *out)
+{
+    clear_error();
+    int rc = check_grid(g, true);
+    if (rc) return rc;
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (n_pid < 1 || n_pid > PDF_MAX_PIDS) return fail(PDF_E_RANGE, "bad pid count");
+    if (n == 0) return PDF_OK;
+    if (!x || !q2 || !out) return fail(PDF_E_ARG, "null array");
+    std::lock_guard<std::mutex> lock(g->host_mu);
+    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 21);
+    if (g->stage_pts < chunk || g->stage_pid < n_pid) {
+        for (int s = 0; s < 3; ++s)
+            for (int k = 0; k < 3; ++k) {
+                if (g->stage[s][k]) cudaFree(g->stage[s][k]);
+                g->stage[s][k] = nullptr;
+            }
+        int64_t pts = std::max<int64_t>(chunk, g->stage_pts);
+        int np = std::max(n_pid, g->stage_pid);
+        for (int s = 0; s < 3; ++s) {
+            if (cudaMalloc(&g->stage[s][0], pts * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&g->stage[s][1], pts * sizeof(double)) != cudaSuccess ||
+                cudaMalloc(&g->stage[s][2], pts * np * sizeof(double)) != cudaSuccess)
+                return fail(PDF_E_NOMEM, "staging allocation failed");
+        }
+        g->stage_pts = pts;
+        g->stage_pid = np;
+    }
+    for (int s = 0; s < 3; ++s)
+        if (!g->hs[s]) PDF_CUDA(cudaStreamCreateWithFlags(&g->hs[s], cudaStreamNonBlocking));
+    int64_t nchunks = (n + chunk - 1) / chunk;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        int s = (int)(c % 3);
+        cudaStream_t st = g->hs[s];
+        int64_t off = c * chunk, m = std::min(chunk, n - off);
+        PDF_CUDA(cudaMemcpyAsync(g->stage[s][0], x + off, m * sizeof(double), cudaMemcpyHostToDevice, st));
+        PDF_CUDA(cudaMemcpyAsync(g->stage[s][1], q2 + off, m * sizeof(double), cudaMemcpyHostToDevice, st));
+        rc = launch_matrix(g, member, pids, n_pid, g->stage[s][0], g->stage[s][1], m, g->stage[s][2], st, false);
+        if (rc) return rc;
+        PDF_CUDA(cudaMemcpyAsync(out + off * n_pid, g->stage[s][2], m * n_pid * sizeof(double),
+                                 cudaMemcpyDeviceToHost, st));
+    }
+    for (int s = 0; s < 3; ++s) PDF_CUDA(cudaStreamSynchronize(g->hs[s]));
+    return PDF_OK;
+}

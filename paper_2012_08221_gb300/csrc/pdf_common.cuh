@@ -1,0 +1,276 @@
+// Shared device-side building blocks of the pdfgpu kernels.
+//
+// The interpolant (PDFFlow Sec. 2.1 and Sec. 4: LHAPDF-style log-bicubic with
+// Q subgrids; formulas in include/pdfgpu.h) is stored per grid cell as the 16
+// monomial coefficients C[n][m] of the bicubic patch in the local coordinates
+// tx = (ln x - U_k)/dU_k and tq = (ln Q^2 - W_c)/dW_c.  These are the Hermite
+// cubics with finite-difference knot derivatives, expanded once at load time,
+// so a query costs two table lookups, two knot searches and 15 FP64 FMAs per
+// flavour:   P = sum_n bq_n sum_m bx_m C[n][m],  b = (1, t, t^2, t^3).
+// Outside the grid the basis becomes (1, t, t, t): that turns the edge patch
+// into the linear continuation from its two edge knots (P(0) + t (P(1)-P(0))).
+//
+// The knot searches compare IEEE bit patterns as integers (the FP64 pipe of
+// this GPU is ~60x slower than its integer pipes), and ln is a table-driven
+// routine (Tang's method, ACM TOMS 16 (1990) 378) that costs 8 FP64
+// operations instead of the ~36-slot library log.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "pdfgpu.h"
+
+#if defined(__CUDACC__)
+#define PDF_HD __host__ __device__ __forceinline__
+#else
+#define PDF_HD inline
+#endif
+
+namespace pdfgpu {
+
+constexpr int kLogBits = 10;              // table index: top 10 mantissa bits
+constexpr int kLogTab = 1 << kLogBits;
+constexpr int kMaxStencilRows = 4;
+
+PDF_HD uint64_t dbits(double x)
+{
+#ifdef __CUDA_ARCH__
+    return (uint64_t)__double_as_longlong(x);
+#else
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    return b;
+#endif
+}
+
+PDF_HD double dfrom(uint64_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    memcpy(&x, &b, 8);
+    return x;
+#endif
+}
+
+// Signed-integer key with the same order as the double (both signs).
+PDF_HD int64_t dkey(double x)
+{
+    int64_t b = (int64_t)dbits(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFll);
+}
+
+// ln x for a positive, finite, normal double.
+//   x = 2^e m, m in [1,2); j = top 10 bits of m; c_j = 1 + (j + 1/2)/1024,
+//   except c_0 = 1 and c_1023 = 2 (so that ln is exact at 1 and accurate to
+//   relative rounding on both sides of 1); tab[j] = (1/c_j rounded, and the
+//   high and low parts of -ln of that reciprocal); r = m/c_j - 1 by one FMA
+//   (|r| <= 2^-10); ln(1+r) = r - r^2/2 + r^3/3 - r^4/4 + r^5/5 (next term
+//   < 2e-19); etab[biased e] = e ln 2 as high and low parts.  The result is
+//   (E_hi + L_hi) + (p + (E_lo + L_lo)): the high parts cancel exactly where
+//   they nearly cancel, and the error stays within about one unit in the
+//   last place.  Both sides of the library (host tables, device kernels)
+//   call this same routine, so knot logs and query logs agree bit for bit.
+struct LogEntry {
+    double inv_c, lhi, llo, pad;
+};
+
+PDF_HD double tlog(double x, const LogEntry *tab, const double2 *etab)
+{
+    uint64_t b = dbits(x);
+    uint32_t eb = (uint32_t)(b >> 52);
+    uint32_t j = (uint32_t)(b >> (52 - kLogBits)) & (kLogTab - 1);
+    double m = dfrom((b & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull);
+    const LogEntry &L = tab[j];
+    const double2 E = etab[eb];
+    double r = fma(m, L.inv_c, -1.0);
+    double a = fma(r, 0.2, -0.25);
+    a = fma(r, a, 1.0 / 3.0);
+    a = fma(r, a, -0.5);
+    double r2 = r * r;
+    double p = fma(r2, a, r);
+    double hi = E.x + L.lhi;
+    double lo = p + (E.y + L.llo);
+    return hi + lo;
+}
+
+// Device view of one loaded grid (passed by value to kernels).
+struct GridDev {
+    int nx, nxc;          // x knots, x cells (nx - 1)
+    int nqc;              // Q cells over all subgrids
+    int nrows, nsub, nflav, nmem;
+    int xstep, qstep;     // search start steps (largest power of two < cells)
+    uint64_t xlo, xhi;    // bit patterns of the first / last x knot
+    uint64_t qlo, qhi;    // bit patterns of the first / last Q^2 knot
+    int64_t ulo, uhi;     // order keys of ln(first / last x knot)
+    int64_t wlo, whi;     // order keys of ln(first / last Q^2 knot)
+    const uint64_t *xbits;   // [nxc] bits of each x cell's lower knot
+    const int64_t *ukey;     // [nxc] order keys of each x cell's lower ln x
+    const double2 *xcell;    // [nxc] (U_k, 1/dU_k)
+    const uint64_t *qbits;   // [nqc] bits of each Q cell's lower Q^2 knot
+    const int64_t *wkey;     // [nqc] order keys of each Q cell's lower ln Q^2
+    const double2 *qcell;    // [nqc] (W_c, 1/dW_c)
+    const LogEntry *logtab;  // [kLogTab]
+    const double2 *etab;     // [2048] (hi, lo) of e ln 2
+    const double *coef;      // [nmem][nqc][nxc][nflav][16]
+    const double *acoef;     // [nqc][4] alpha_s cubic in tq, or null
+    const double *mx;        // [nxc][16] stencil -> monomial matrix M[m][i]
+    const double *mq;        // [nqc][16]
+    const int *qrow;         // [nqc] grid row of each Q cell's lower knot
+    const int *qmask;        // [nqc] bit i (0..3): stencil row i-1 exists
+    const signed char *pidmap;  // [129] column of pid in [-64, 64], -1 absent
+    uint32_t *status;
+};
+
+// Largest cell c in [0, ncell) whose lower key is <= key (0 below the grid).
+// Tables are read with generic loads: they may sit in global or shared memory.
+template <typename K>
+__device__ __forceinline__ int find_cell(const K *keys, int ncell, int step, K key)
+{
+    int lo = 0;
+    for (int s = step; s > 0; s >>= 1) {
+        int c = lo + s;
+        if (c < ncell && keys[c] <= key) lo = c;
+    }
+    return lo;
+}
+
+// Per-axis local coordinate and basis of one query.
+struct Axis {
+    int cell;
+    double t, b2, b3;     // basis (1, t, b2, b3)
+    bool in;              // inside the knot range
+};
+
+__device__ __forceinline__ void make_basis(Axis &A, double t)
+{
+    A.t = t;
+    double t2 = t * t;
+    double t3 = t2 * t;
+    A.b2 = A.in ? t2 : t;
+    A.b3 = A.in ? t3 : t;
+}
+
+// Domain checks on bit patterns: x in (0, 1], Q^2 in (0, max finite].
+__device__ __forceinline__ bool x_ok(uint64_t b) { return b - 1ull < 0x3FF0000000000000ull; }
+__device__ __forceinline__ bool q2_ok(uint64_t b) { return b - 1ull < 0x7FEFFFFFFFFFFFFFull; }
+
+// ln for any positive finite double (subnormals rescaled; rare path).
+__device__ __forceinline__ double dlog(const GridDev &g, double v)
+{
+    if (dbits(v) < 0x0010000000000000ull) {
+        return tlog(v * 18014398509481984.0 /* 2^54 */, g.logtab, g.etab) -
+               37.4299477502370467085305 /* 54 ln 2 */;
+    }
+    return tlog(v, g.logtab, g.etab);
+}
+
+// x axis from x (bit search on x), returns u = ln x in *u.
+__device__ __forceinline__ Axis axis_x(const GridDev &g, double x, double *u)
+{
+    uint64_t b = dbits(x);
+    Axis A;
+    A.cell = find_cell<uint64_t>(g.xbits, g.nxc, g.xstep, b);
+    A.in = (b >= g.xlo) & (b <= g.xhi);
+    double uu = dlog(g, x);
+    double2 c = g.xcell[A.cell];
+    make_basis(A, (uu - c.x) * c.y);
+    *u = uu;
+    return A;
+}
+
+// x axis from u = ln x directly (order-key search on u).
+__device__ __forceinline__ Axis axis_u(const GridDev &g, double u)
+{
+    int64_t k = dkey(u);
+    Axis A;
+    A.cell = find_cell<int64_t>(g.ukey, g.nxc, g.xstep, k);
+    A.in = (k >= g.ulo) & (k <= g.uhi);
+    double2 c = g.xcell[A.cell];
+    make_basis(A, (u - c.x) * c.y);
+    return A;
+}
+
+__device__ __forceinline__ Axis axis_q2(const GridDev &g, double q2, double *w)
+{
+    uint64_t b = dbits(q2);
+    Axis A;
+    A.cell = find_cell<uint64_t>(g.qbits, g.nqc, g.qstep, b);
+    A.in = (b >= g.qlo) & (b <= g.qhi);
+    double ww = dlog(g, q2);
+    double2 c = g.qcell[A.cell];
+    make_basis(A, (ww - c.x) * c.y);
+    *w = ww;
+    return A;
+}
+
+__device__ __forceinline__ Axis axis_w(const GridDev &g, double w)
+{
+    int64_t k = dkey(w);
+    Axis A;
+    A.cell = find_cell<int64_t>(g.wkey, g.nqc, g.qstep, k);
+    A.in = (k >= g.wlo) & (k <= g.whi);
+    double2 c = g.qcell[A.cell];
+    make_basis(A, (w - c.x) * c.y);
+    return A;
+}
+
+// 16-coefficient patch contraction: 15 FP64 FMAs.
+__device__ __forceinline__ double patch(const double *__restrict__ C, const Axis &X, const Axis &Q)
+{
+    const double2 *C2 = reinterpret_cast<const double2 *>(C);
+    double2 c0 = __ldg(C2 + 0), c1 = __ldg(C2 + 1), c2 = __ldg(C2 + 2), c3 = __ldg(C2 + 3);
+    double2 c4 = __ldg(C2 + 4), c5 = __ldg(C2 + 5), c6 = __ldg(C2 + 6), c7 = __ldg(C2 + 7);
+    double i0 = fma(X.b3, c1.y, fma(X.b2, c1.x, fma(X.t, c0.y, c0.x)));
+    double i1 = fma(X.b3, c3.y, fma(X.b2, c3.x, fma(X.t, c2.y, c2.x)));
+    double i2 = fma(X.b3, c5.y, fma(X.b2, c5.x, fma(X.t, c4.y, c4.x)));
+    double i3 = fma(X.b3, c7.y, fma(X.b2, c7.x, fma(X.t, c6.y, c6.x)));
+    return fma(Q.b3, i3, fma(Q.b2, i2, fma(Q.t, i1, i0)));
+}
+
+// Patch value and its derivatives with respect to tx and tq.
+__device__ __forceinline__ void patch_d(const double *__restrict__ C, const Axis &X, const Axis &Q,
+                                        double dx2, double dx3, double dq2, double dq3,
+                                        double *dtx, double *dtq)
+{
+    const double2 *C2 = reinterpret_cast<const double2 *>(C);
+    double i[4], j[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        double2 a = __ldg(C2 + 2 * n), b = __ldg(C2 + 2 * n + 1);
+        i[n] = fma(X.b3, b.y, fma(X.b2, b.x, fma(X.t, a.y, a.x)));
+        j[n] = fma(dx3, b.y, fma(dx2, b.x, a.y));
+    }
+    *dtx = fma(Q.b3, j[3], fma(Q.b2, j[2], fma(Q.t, j[1], j[0])));
+    *dtq = fma(dq3, i[3], fma(dq2, i[2], i[1]));
+}
+
+// Stencil weights W_i = sum_m M[m][i] b_m of one axis (i <-> knot cell-1+i).
+__device__ __forceinline__ void stencil_weights(const double *__restrict__ M, const Axis &A, double W[4])
+{
+    const double2 *M2 = reinterpret_cast<const double2 *>(M);
+    double2 r0a = __ldg(M2 + 0), r0b = __ldg(M2 + 1);
+    double2 r1a = __ldg(M2 + 2), r1b = __ldg(M2 + 3);
+    double2 r2a = __ldg(M2 + 4), r2b = __ldg(M2 + 5);
+    double2 r3a = __ldg(M2 + 6), r3b = __ldg(M2 + 7);
+    W[0] = fma(A.b3, r3a.x, fma(A.b2, r2a.x, fma(A.t, r1a.x, r0a.x)));
+    W[1] = fma(A.b3, r3a.y, fma(A.b2, r2a.y, fma(A.t, r1a.y, r0a.y)));
+    W[2] = fma(A.b3, r3b.x, fma(A.b2, r2b.x, fma(A.t, r1b.x, r0b.x)));
+    W[3] = fma(A.b3, r3b.y, fma(A.b2, r2b.y, fma(A.t, r1b.y, r0b.y)));
+}
+
+__device__ __forceinline__ void flag_status(const GridDev &g, bool bad)
+{
+    unsigned m = __ballot_sync(__activemask(), bad);
+    if (m && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(g.status, (unsigned)PDF_S_DOMAIN);
+}
+
+__device__ __forceinline__ int pid_col(const GridDev &g, int pid)
+{
+    return (pid >= -64 && pid <= 64) ? (int)__ldg(g.pidmap + pid + 64) : -1;
+}
+
+}  // namespace pdfgpu

@@ -1,0 +1,65 @@
+// Host-side internals shared by the pdfgpu translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pdf_common.cuh"
+
+struct pdfgpu_grid {
+    int device = 0;
+    int sm_count = 0;
+    pdfgpu::GridDev d{};            // device view (pointers into `blocks`)
+    std::vector<void *> blocks;     // device allocations owned by the grid
+    bool bound = false;             // coefficients built
+    bool has_alphas = false;
+    std::vector<int32_t> pids;      // host copy
+    std::vector<int32_t> n_q;
+    std::vector<double> U, W;       // knot logs (host)
+    // scratch for the luminosity reduction (block partial sums)
+    double *partials = nullptr;
+    int partials_cap = 0;
+    // staging for the host-buffer entry point
+    std::mutex host_mu;
+    cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
+    double *stage[3][3] = {{nullptr}};  // [slot][x, q2, out]
+    int64_t stage_pts = 0;
+    int stage_pid = 0;
+};
+
+namespace pdfgpu {
+
+// Thread-local error message and return-code helpers.
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+void clear_error();
+
+#define PDF_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e__ = (call);                           \
+        if (e__ != cudaSuccess) return pdfgpu::cuda_fail(e__, #call); \
+    } while (0)
+
+// Resident CTAs per SM for a kernel at a block size and dynamic smem.
+int occupancy(const void *kernel, int block, size_t smem);
+
+// Grid of a grid-stride launch: enough CTAs for n items, at most one wave.
+int wave_grid(const pdfgpu_grid *g, const void *kernel, int block, size_t smem, int64_t items);
+
+// Coefficient build (grid.cu) used by load and bind.
+int build_coefficients(pdfgpu_grid *g, const double *dev_values, cudaStream_t s);
+
+// Column list of a matrix-form call (resolved from the pid list on the host).
+struct Cols {
+    signed char c[PDF_MAX_PIDS];
+};
+int resolve_cols(const pdfgpu_grid *g, const int32_t *pids, int32_t n_pid, Cols *cols);
+
+// Shared argument checks.
+int check_grid(const pdfgpu_grid *g, bool need_values);
+
+}  // namespace pdfgpu

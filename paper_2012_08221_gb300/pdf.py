@@ -1,0 +1,255 @@
+"""The PDF object: a grid loaded on the GPU and the queries of PDFFlow.
+
+Mirrors the paper's Python interface (PDFFlow Sec. 2.1, Fig. 1): ``mkPDF``
+builds a PDF object; ``xfxQ2`` / ``py_xfxQ`` evaluate x*f for a pid list over
+arrays of x and Q^2 (or Q); ``alphasQ2`` / ``py_alphasQ`` give alpha_s;
+``trace`` / ``alphas_trace`` warm the kernels up.  Every call only marshals
+torch tensors (device memory, the current stream) into the C ABI of
+``include/pdfgpu.h``; all arithmetic runs in the CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._lib import GridDesc, PDF_S_DOMAIN, check, lib
+
+__all__ = ["PDF", "mkPDF", "PDF_S_DOMAIN"]
+
+
+def _stream(device=None):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _f64_cuda(a, device):
+    if isinstance(a, torch.Tensor):
+        t = a.to(device=device, dtype=torch.float64)
+    else:
+        t = torch.as_tensor(np.asarray(a, dtype=np.float64), device=device)
+    return t.contiguous()
+
+
+def _pids_host(pids):
+    arr = np.ascontiguousarray(np.atleast_1d(np.asarray(pids, dtype=np.int32)))
+    return arr, arr.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+class PDF:
+    """One PDF set (all its members) resident on a CUDA device.
+
+    ``values`` is ``[members][rows][n_x][n_flav]`` (or ``[rows][n_x][n_flav]``)
+    of x*f on the knots; Q knots are in GeV with duplicated thresholds.
+    """
+
+    def __init__(self, x_knots, n_q, q_knots, pids, values=None, alphas=None, device="cuda:0"):
+        self.device = torch.device(device)
+        torch.cuda.set_device(self.device)
+        self._x = np.ascontiguousarray(x_knots, dtype=np.float64)
+        self._nq = np.ascontiguousarray(n_q, dtype=np.int32)
+        self._q = np.ascontiguousarray(q_knots, dtype=np.float64)
+        self._pids = np.ascontiguousarray(pids, dtype=np.int32)
+        v = None
+        if values is not None:
+            v = np.ascontiguousarray(values, dtype=np.float64)
+            if v.ndim == 3:
+                v = v[None]
+        a = None if alphas is None else np.ascontiguousarray(alphas, dtype=np.float64)
+        self.n_members = 1 if v is None else v.shape[0]
+        desc = GridDesc()
+        desc.n_x = self._x.size
+        desc.x_knots = self._x.ctypes.data_as(C.POINTER(C.c_double))
+        desc.n_sub = self._nq.size
+        desc.n_q = self._nq.ctypes.data_as(C.POINTER(C.c_int32))
+        desc.q_knots = self._q.ctypes.data_as(C.POINTER(C.c_double))
+        desc.n_flav = self._pids.size
+        desc.pids = self._pids.ctypes.data_as(C.POINTER(C.c_int32))
+        desc.n_members = self.n_members
+        desc.values = v.ctypes.data_as(C.POINTER(C.c_double)) if v is not None else None
+        desc.alphas = a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+        h = C.c_void_p()
+        check("pdf_load_grid", lib().pdf_load_grid(C.byref(desc), C.byref(h)))
+        self.handle = h
+        self.n_x = int(self._x.size)
+        self.n_rows = int(self._q.size)
+        self.n_flav = int(self._pids.size)
+        self.pids = self._pids.copy()
+        self.has_alphas = a is not None
+
+    @classmethod
+    def from_grid(cls, grid, device="cuda:0", with_values=True):
+        """From a ``synth.Grid`` (or any object with the same fields)."""
+        return cls(grid.x_knots, grid.n_q, grid.q_knots, grid.pids,
+                   grid.values if with_values else None, grid.alphas, device)
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().pdf_free_grid(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -------------------------------------------------------------- values
+    def value_shape(self):
+        return (self.n_members, self.n_rows, self.n_x, self.n_flav)
+
+    def bind_values(self, values: torch.Tensor):
+        """Rebuild the interpolation coefficients from a device tensor of
+        shape ``[members][rows][n_x][n_flav]`` (float64, contiguous)."""
+        v = values.detach()
+        if v.dim() == 3:
+            v = v.unsqueeze(0)
+        assert tuple(v.shape) == self.value_shape(), (tuple(v.shape), self.value_shape())
+        v = v.to(device=self.device, dtype=torch.float64).contiguous()
+        check("pdf_bind_values", lib().pdf_bind_values(self.handle, _ptr(v), _stream(self.device)))
+        self._bound_ref = v      # keep alive until the stream has read it
+
+    # ------------------------------------------------------------- queries
+    def xfxQ2(self, pids, x, q2, member=0, out=None):
+        """x*f for every pid in ``pids`` at each (x_i, Q^2_i): ``[n][len(pids)]``."""
+        return self._matrix("xfxQ2", pids, x, q2, member, out)
+
+    def xfxQ(self, pids, x, q, member=0, out=None):
+        return self._matrix("xfxQ", pids, x, q, member, out)
+
+    py_xfxQ2 = xfxQ2
+    py_xfxQ = xfxQ
+
+    def _matrix(self, name, pids, x, q, member, out):
+        arr, pp = _pids_host(pids)
+        x = _f64_cuda(x, self.device)
+        q = _f64_cuda(q, self.device)
+        n = x.numel()
+        assert q.numel() == n, "x and Q arrays differ in length"
+        if out is None:
+            out = torch.empty((n, arr.size), dtype=torch.float64, device=self.device)
+        f = getattr(lib(), name)
+        check(name, f(self.handle, int(member), pp, arr.size, _ptr(x), _ptr(q), n, _ptr(out),
+                      _stream(self.device)))
+        return out
+
+    def xfxQ2_pw(self, pid, x, q2, member=0, out=None):
+        """One pid per point: ``out[i] = x*f_{pid_i}(x_i, Q^2_i)``."""
+        x = _f64_cuda(x, self.device)
+        q2 = _f64_cuda(q2, self.device)
+        pid = torch.as_tensor(pid, device=self.device).to(torch.int32).contiguous()
+        n = x.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=self.device)
+        check("xfxQ2_pw", lib().xfxQ2_pw(self.handle, int(member), _ptr(pid), _ptr(x), _ptr(q2), n,
+                                         _ptr(out), _stream(self.device)))
+        return out
+
+    def alphasQ2(self, q2, out=None):
+        return self._alphas("alphasQ2", q2, out)
+
+    def alphasQ(self, q, out=None):
+        return self._alphas("alphasQ", q, out)
+
+    py_alphasQ2 = alphasQ2
+    py_alphasQ = alphasQ
+
+    def _alphas(self, name, q, out):
+        q = _f64_cuda(q, self.device)
+        n = q.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=self.device)
+        check(name, getattr(lib(), name)(self.handle, _ptr(q), n, _ptr(out), _stream(self.device)))
+        return out
+
+    def xfxQ2_host(self, pids, x, q2, member=0, out=None):
+        """End-to-end call on HOST arrays (CPU tensors, pinned for full copy
+        speed); returns a CPU tensor ``[n][len(pids)]``."""
+        arr, pp = _pids_host(pids)
+        x = torch.as_tensor(x, dtype=torch.float64).contiguous()
+        q2 = torch.as_tensor(q2, dtype=torch.float64).contiguous()
+        assert not x.is_cuda and not q2.is_cuda
+        n = x.numel()
+        if out is None:
+            out = torch.empty((n, arr.size), dtype=torch.float64, pin_memory=True)
+        check("xfxQ2_host", lib().xfxQ2_host(self.handle, int(member), pp, arr.size, _ptr(x),
+                                             _ptr(q2), n, _ptr(out)))
+        return out
+
+    # --------------------------------------------------------------- adjoint
+    def xfxQ2_backward(self, pids, x, q2, grad_out, member=0, pointwise=False,
+                       grad_x=True, grad_q2=True, grad_values=None):
+        """dL/dx, dL/dQ^2 and (accumulated into ``grad_values``, shape
+        ``[rows][n_x][n_flav]``) dL/dvalues for
+        L = sum grad_out * xf.  Returns (grad_x, grad_q2, grad_values)."""
+        x = _f64_cuda(x, self.device)
+        q2 = _f64_cuda(q2, self.device)
+        n = x.numel()
+        gout = grad_out.to(device=self.device, dtype=torch.float64).contiguous()
+        gx = torch.empty(n, dtype=torch.float64, device=self.device) if grad_x else None
+        gq = torch.empty(n, dtype=torch.float64, device=self.device) if grad_q2 else None
+        if pointwise:
+            pid = torch.as_tensor(pids, device=self.device).to(torch.int32).contiguous()
+            pp, npid, keep = _ptr(pid), 0, pid
+        else:
+            arr, _ = _pids_host(pids)
+            keep = arr
+            pp, npid = C.c_void_p(arr.ctypes.data), arr.size
+        check("xfxQ2_backward", lib().xfxQ2_backward(
+            self.handle, int(member), pp, npid, int(bool(pointwise)), _ptr(x), _ptr(q2), n,
+            _ptr(gout), _ptr(gx), _ptr(gq), _ptr(grad_values), _stream(self.device)))
+        del keep
+        return gx, gq, grad_values
+
+    # ------------------------------------------------------------- warm-up
+    def trace(self):
+        """Run every x*f kernel once on a tiny input (PDFFlow's `trace()`)."""
+        x = torch.tensor([1e-3, 0.2], dtype=torch.float64, device=self.device)
+        q2 = torch.tensor([10.0, 1e4], dtype=torch.float64, device=self.device)
+        self.xfxQ2(self.pids, x, q2)
+        self.xfxQ(self.pids, x, q2)
+        self.xfxQ2_pw(self.pids[:1].repeat(2), x, q2)
+        torch.cuda.synchronize(self.device)
+
+    def alphas_trace(self):
+        if self.has_alphas:
+            self.alphasQ2(torch.tensor([10.0], dtype=torch.float64, device=self.device))
+            torch.cuda.synchronize(self.device)
+
+    # -------------------------------------------------------------- status
+    def status(self) -> int:
+        """Read and clear the status bits (synchronises the current stream)."""
+        bits = C.c_uint32()
+        check("pdf_get_status", lib().pdf_get_status(self.handle, _stream(self.device), C.byref(bits)))
+        return bits.value
+
+    def debug_log(self, v):
+        v = _f64_cuda(v, self.device)
+        out = torch.empty_like(v)
+        check("pdf_debug_log", lib().pdf_debug_log(self.handle, _ptr(v), v.numel(), _ptr(out),
+                                                   _stream(self.device)))
+        return out
+
+
+def mkPDF(grid, device="cuda:0") -> PDF:
+    """Build a PDF object from an in-memory grid (PDFFlow Sec. 2.1 `mkPDF`;
+    the LHAPDF file loader is not part of this library)."""
+    return PDF.from_grid(grid, device)
+
+
+def fp64_peak() -> float:
+    """Measured FP64 FMA throughput of the current GPU in FLOP/s."""
+    v = C.c_double()
+    check("pdf_probe_fp64_peak", lib().pdf_probe_fp64_peak(C.byref(v)))
+    return v.value

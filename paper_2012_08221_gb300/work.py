@@ -1,0 +1,74 @@
+"""Algorithmic work per unit of each kernel: the numerators of the roofline.
+
+FP64 flops count a fused multiply-add as 2 and an add or multiply as 1; they
+are the operations the method needs in the formulation the kernels use
+(bicubic patch coefficients, table-driven log), not instruction counts
+measured on the GPU.  Bytes are the compulsory HBM traffic: inputs read once
+and outputs written once (the grid tables are cache-resident parameters).
+
+Per point of the x*f kernel with F flavours:
+  2 logs x 15 flops (1 FMA reduction, 4 FMA series, 1 multiply, 4 adds),
+  2 axes x (subtract, multiply) for t, 2 axes x 2 multiplies for t^2, t^3,
+  15 FMA per flavour for the 16-coefficient patch:  38 + 30 F flops.
+"""
+from __future__ import annotations
+
+LOG_FLOPS = 15
+AXIS_FLOPS = 4          # t = (ln z - Z) * (1/dZ), then t^2, t^3
+PATCH_FLOPS = 30        # 15 FMA
+
+
+def xfxq2_point_flops(n_flav: int) -> int:
+    return 2 * LOG_FLOPS + 2 * AXIS_FLOPS + PATCH_FLOPS * n_flav
+
+
+def xfxq2_point_bytes(n_flav: int) -> int:
+    return 16 + 8 * n_flav            # x, Q^2 in; F outputs
+
+
+def alphas_point_flops() -> int:
+    return LOG_FLOPS + AXIS_FLOPS + 6  # 3 FMA for the cubic
+
+
+ALPHAS_POINT_BYTES = 16
+
+
+def pw_fwd_point_flops() -> int:
+    return xfxq2_point_flops(1)
+
+
+PW_FWD_POINT_BYTES = 28                # x, Q^2, pid, out
+
+
+def pw_bwd_point_flops() -> int:
+    """Adjoint of one pointwise point: recomputed coordinates (2 logs, t,
+    bases), derivative bases (2 multiplies per axis for 2t, 3t^2), patch
+    value-derivatives (12 FMA for the x rows, 8 for their tx-derivatives,
+    3 + 2 for the tq sums), 2 FMA for the weighted sums, stencil weights of
+    both axes (2 x 12 FMA), 4 + 16 multiplies for the 16 cell weights, and
+    the chain rule to x and Q^2 (2 x 2 multiplies and a reciprocal)."""
+    coords = 2 * LOG_FLOPS + 2 * AXIS_FLOPS
+    return coords + 4 + 2 * (12 + 8 + 3 + 2) + 4 + 2 * 2 * 12 + 20 + 2 * 2 + 2 * 4
+
+
+PW_BWD_POINT_BYTES = 44                # grad_out, x, Q^2, pid in; dx, dQ^2 out
+
+
+def lumi_event_flops(n_flav: int) -> int:
+    """Kinematics (1 multiply, 3 adds), t and bases for 3 axes, 2 F patches,
+    F FMA for the flavour-paired sum, alpha_s cubic (3 FMA), 1 add to the
+    running sum."""
+    return 4 + 3 * AXIS_FLOPS + 2 * PATCH_FLOPS * n_flav + 2 * n_flav + 6 + 1
+
+
+LUMI_EVENT_BYTES = 8 + 8 + 1 + 16      # ln tau, y, flags in; lum, alpha_s out
+
+
+def lumi_bwd_event_flops(n_flav: int) -> int:
+    """Recompute 2 F patches and the coordinates, stencil weights of 3 axes
+    (3 x 12 FMA), then per flavour and parton 2 multiplies for the scaled
+    partner value and 4 + 16 multiplies for the 16 cell contributions."""
+    return 4 + 3 * AXIS_FLOPS + 2 * PATCH_FLOPS * n_flav + 3 * 24 + 2 * n_flav * (1 + 4 + 16)
+
+
+LUMI_BWD_EVENT_BYTES = 8 + 8 + 1

@@ -1,0 +1,170 @@
+"""GPU adjoint: dL/dx, dL/dQ^2 and dL/dvalues against the oracle's analytic
+derivative (1e-9 relative), central finite differences, torch.autograd.gradcheck,
+and exact sum rules of the grid gradient at the full 1e7-point size."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleGrid
+from paper_2012_08221_gb300 import synth
+from tests.tinygrids import tiny_two_sub
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GRAD_RTOL = 1e-9
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+@pytest.fixture(scope="module")
+def diffgrid():
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    g = synth.grid_small(seed=1003, pids=synth.PIDS_13)
+    return g, PDF.from_grid(g), OracleGrid.from_synth(g)
+
+
+def _check(got, ref, scale, what):
+    err = np.abs(got - ref)
+    bound = GRAD_RTOL * np.maximum(np.abs(ref), scale) + 1e-300
+    assert np.all(err <= bound), (what, float(np.max(err / bound)))
+
+
+def test_pointwise_gradients_against_oracle(diffgrid):
+    g, pdf, o = diffgrid
+    pid, x, q2, w = synth.queries_pointwise(20_011, seed=41)
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    gx, gq, _ = pdf.xfxQ2_backward(cuda(pid), cuda(x), cuda(q2), cuda(w), pointwise=True,
+                                   grad_values=gv)
+    rdx, rdq = o.grad_pw(pid, x, q2)
+    kap = o.kappa(pid, x, q2, pointwise=True)
+    U = np.log(g.x_knots)
+    W = np.log(g.q_knots ** 2)
+    sx = 4 * kap / (np.min(np.diff(U)) * x)
+    sq = 4 * kap / (np.min(np.diff(W)) * q2)
+    _check(gx.cpu().numpy(), w * rdx, np.abs(w) * sx, "dL/dx")
+    _check(gq.cpu().numpy(), w * rdq, np.abs(w) * sq, "dL/dQ2")
+    ref = o.dgrid_pw(pid, x, q2, w)
+    _check(gv.cpu().numpy(), ref, o.dgrid_pw(pid, x, q2, w, absval=True), "dL/dvalues")
+
+
+def test_matrix_gradients_against_oracle(lib_small=None):
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_small()
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    x, q2 = synth.queries_small(5003, seed=42)
+    x[:7] = [1e-9, 1e-9, 0.95, 1.0, 2e-3, 2e-3, 0.5]
+    q2[:7] = [1.0, 1e9, 1e9, 30.0, 0.5, 2e8, 1e3]        # extrapolation corners
+    pids = np.array([-3, 0, 2, 5, 6], dtype=np.int32)     # 6 absent
+    gout = np.random.default_rng(2).standard_normal((x.size, pids.size))
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    gx, gq, _ = pdf.xfxQ2_backward(pids, cuda(x), cuda(q2), cuda(gout), grad_values=gv)
+    ref = o.dgrid(pids, x, q2, gout)
+    _check(gv.cpu().numpy(), ref, o.dgrid(pids, x, q2, gout, absval=True), "matrix dL/dvalues")
+    rdx = np.zeros(x.size)
+    rdq = np.zeros(x.size)
+    for p in range(pids.size):
+        dx, dq = o.grad_pw(np.full(x.size, pids[p]), x, q2)
+        rdx += gout[:, p] * dx
+        rdq += gout[:, p] * dq
+    kap = o.kappa(pids, x, q2).sum(axis=1)
+    U = np.log(g.x_knots)
+    W = np.log(g.q_knots ** 2)
+    gs = np.abs(gout).max(axis=1)
+    _check(gx.cpu().numpy(), rdx, gs * 4 * kap / (np.min(np.diff(U)) * x), "matrix dL/dx")
+    _check(gq.cpu().numpy(), rdq, gs * 4 * kap / (np.min(np.diff(W)) * q2), "matrix dL/dQ2")
+
+
+def test_central_finite_differences(diffgrid):
+    """h = 1e-6 relative, on points more than 2h (in log) from every knot."""
+    g, pdf, o = diffgrid
+    rng = np.random.default_rng(43)
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    x = np.exp(rng.uniform(math.log(1e-6), math.log(0.9), 3000))
+    q2 = np.exp(rng.uniform(math.log(4), math.log(2.5e7), 3000))
+    h = 1e-6
+    far = (np.min(np.abs(np.log(x)[:, None] - U[None]), axis=1) > 4 * h) & \
+          (np.min(np.abs(np.log(q2)[:, None] - W[None]), axis=1) > 4 * h)
+    x, q2 = x[far][:1000], q2[far][:1000]
+    pid = rng.choice(g.pids, x.size).astype(np.int32)
+    ones = np.ones(x.size)
+    gx, gq, _ = pdf.xfxQ2_backward(cuda(pid), cuda(x), cuda(q2), cuda(ones), pointwise=True)
+    f = lambda xx, qq: pdf.xfxQ2_pw(cuda(pid), cuda(xx), cuda(qq)).cpu().numpy()
+    fdx = (f(x * (1 + h), q2) - f(x * (1 - h), q2)) / (2 * h * x)
+    fdq = (f(x, q2 * (1 + h)) - f(x, q2 * (1 - h))) / (2 * h * q2)
+    v = f(x, q2)
+    assert np.all(np.abs(gx.cpu().numpy() - fdx) <= 1e-5 * (np.abs(fdx) + np.abs(v) / x))
+    assert np.all(np.abs(gq.cpu().numpy() - fdq) <= 1e-5 * (np.abs(fdq) + np.abs(v) / q2))
+
+
+def test_autograd_gradcheck_tiny_grid():
+    from paper_2012_08221_gb300.autograd import xfxQ2
+    from paper_2012_08221_gb300.pdf import PDF
+    g = tiny_two_sub(seed=5)
+    pdf = PDF.from_grid(g)
+    vals = torch.tensor(g.values, dtype=torch.float64, device="cuda", requires_grad=True)
+    rng = np.random.default_rng(44)
+    x = torch.tensor(np.exp(rng.uniform(math.log(3e-5), math.log(0.5), 7)), device="cuda",
+                     requires_grad=True)
+    q2 = torch.tensor(np.exp(rng.uniform(math.log(1.2), math.log(1500.0), 7)), device="cuda",
+                      requires_grad=True)
+    pids = np.array([-1, 0, 1], dtype=np.int32)
+    assert torch.autograd.gradcheck(lambda v, a, b: xfxQ2(pdf, v, pids, a, b), (vals, x, q2),
+                                    eps=1e-7, atol=1e-7, rtol=1e-5)
+
+
+def test_autograd_matches_oracle_gradient(diffgrid):
+    from paper_2012_08221_gb300.autograd import xfxQ2_pw
+    g, pdf, o = diffgrid
+    pid, x, q2, w = synth.queries_pointwise(5000, seed=45)
+    vals = torch.tensor(g.values, device="cuda", requires_grad=True)
+    X = cuda(x).requires_grad_(True)
+    Q = cuda(q2).requires_grad_(True)
+    L = (xfxQ2_pw(pdf, vals, cuda(pid), X, Q) * cuda(w)).sum()
+    L.backward()
+    ref = o.dgrid_pw(pid, x, q2, w)
+    got = vals.grad[0].cpu().numpy()
+    _check(got, ref, o.dgrid_pw(pid, x, q2, w, absval=True), "autograd grid")
+    rdx, rdq = o.grad_pw(pid, x, q2)
+    assert np.allclose(X.grad.cpu().numpy(), w * rdx, rtol=1e-9, atol=1e-9 * np.max(np.abs(w * rdx)))
+    assert np.allclose(Q.grad.cpu().numpy(), w * rdq, rtol=1e-9, atol=1e-9 * np.max(np.abs(w * rdq)))
+
+
+def test_full_size_sum_rules(diffgrid):
+    """Full 1e7 pointwise workload through autograd.  Exact sum rules of the
+    grid gradient (the interpolation reproduces constants and functions
+    linear in ln x): sum_cells dL/dv[.][a] = sum_{i: a_i = a} w_i and
+    sum_cells U_k dL/dv[.][k][a] = sum_{i: a_i = a} w_i ln x_i; plus sampled
+    dL/dx against the oracle."""
+    from paper_2012_08221_gb300.autograd import xfxQ2_pw
+    g, pdf, o = diffgrid
+    pid, x, q2, w = synth.queries_pointwise()
+    vals = torch.tensor(g.values, device="cuda", requires_grad=True)
+    X = cuda(x).requires_grad_(True)
+    Q = cuda(q2).requires_grad_(True)
+    W_ = cuda(w)
+    L = (xfxQ2_pw(pdf, vals, cuda(pid), X, Q) * W_).sum()
+    L.backward()
+    G = vals.grad[0].cpu().numpy()
+    U = np.log(g.x_knots)
+    for a, p in enumerate(g.pids):
+        m = pid == p
+        s0 = G[:, :, a].sum()
+        want0 = w[m].sum()
+        assert abs(s0 - want0) <= 1e-9 * np.abs(w[m]).sum()
+        s1 = (G[:, :, a] * U[None, :]).sum()
+        want1 = (w[m] * np.log(x[m])).sum()
+        assert abs(s1 - want1) <= 1e-9 * np.abs(w[m] * np.log(x[m])).sum()
+    idx = np.random.default_rng(6).choice(x.size, 2000, replace=False)
+    rdx, rdq = o.grad_pw(pid[idx], x[idx], q2[idx])
+    gx = X.grad[cuda(idx)].cpu().numpy()
+    gq = Q.grad[cuda(idx)].cpu().numpy()
+    kap = o.kappa(pid[idx], x[idx], q2[idx], pointwise=True)
+    Ud, Wd = np.min(np.diff(U)), np.min(np.diff(np.log(g.q_knots ** 2)))
+    _check(gx, w[idx] * rdx, np.abs(w[idx]) * 4 * kap / (Ud * x[idx]), "full dL/dx")
+    _check(gq, w[idx] * rdq, np.abs(w[idx]) * 4 * kap / (Wd * q2[idx]), "full dL/dQ2")

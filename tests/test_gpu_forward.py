@@ -1,0 +1,211 @@
+"""GPU parity of the forward kernels against the FP64 oracle (through the C ABI).
+
+Sizes: the small grid workload in full (1e5 points x 11 flavours), the
+NNPDF-shaped workload on 300001 points (many tiles plus a ragged tail) and at
+its full 1e7 points in the benchmark's launch configuration, checked on a
+random sample of outputs the oracle recomputes one by one.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleGrid
+from paper_2012_08221_gb300 import synth
+from tests import parity
+from tests.golden_io import load as load_golden
+from tests.tinygrids import tiny_two_sub
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def lib_built():
+    from paper_2012_08221_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+@pytest.fixture(scope="module")
+def small(lib_built):
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_small()
+    return g, PDF.from_grid(g), OracleGrid.from_synth(g)
+
+
+@pytest.fixture(scope="module")
+def nnpdf(lib_built):
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_nnpdf()
+    return g, PDF.from_grid(g), OracleGrid.from_synth(g)
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def test_small_grid_full_workload(small):
+    g, pdf, o = small
+    x, q2 = synth.queries_small()
+    got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
+    ref = o.xfxq2_batch(g.pids, x, q2)
+    kap = o.kappa(g.pids, x, q2)
+    parity.check(got, ref, kap, what="small grid xfxQ2")
+    assert pdf.status() == 0
+
+
+def test_nnpdf_many_tiles_ragged_tail(nnpdf):
+    g, pdf, o = nnpdf
+    x, q2, _ = synth.queries_nnpdf(300_001, seed=12)
+    got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
+    ref = o.xfxq2_batch(g.pids, x, q2)
+    kap = o.kappa(g.pids, x, q2)
+    parity.check(got, ref, kap, what="nnpdf xfxQ2")
+
+
+def test_nnpdf_full_size_sampled(nnpdf):
+    """The full 1e7-point workload in one launch; 3000 sampled points are
+    recomputed by the oracle."""
+    g, pdf, o = nnpdf
+    x, q2, q2a = synth.queries_nnpdf()
+    X, Q = cuda(x), cuda(q2)
+    out = pdf.xfxQ2(g.pids, X, Q)
+    a_s = pdf.alphasQ2(cuda(q2a))
+    idx = np.random.default_rng(3).choice(x.size, 3000, replace=False)
+    idx = np.concatenate([idx, [0, x.size - 1]])
+    got = out[cuda(idx)].cpu().numpy()
+    ref = o.xfxq2_batch(g.pids, x[idx], q2[idx])
+    parity.check(got, ref, o.kappa(g.pids, x[idx], q2[idx]), what="nnpdf full size")
+    ga = a_s[cuda(idx)].cpu().numpy()
+    parity.check(ga, o.alphas_batch(q2a[idx]), np.abs(o.alphas_batch(q2a[idx])) * 8, what="alphas full")
+
+
+def test_alphas_parity(small, nnpdf):
+    for g, pdf, o in (small, nnpdf):
+        q2 = np.exp(np.random.default_rng(4).uniform(math.log(0.01), math.log(1e12), 200_003))
+        got = pdf.alphasQ2(cuda(q2)).cpu().numpy()
+        ref = o.alphas_batch(q2)
+        # alpha_s values are O(0.1-1) and positive; the terms are bounded by a
+        # few times the knot values, so kappa = 8 |ref| is a safe term scale
+        parity.check(got, ref, 8 * np.abs(ref), what=f"alphas {g.name}")
+
+
+def test_xfxq_is_xfxq2_of_q_squared(small):
+    g, pdf, o = small
+    x, q2 = synth.queries_small(10_007, seed=31)
+    q = np.sqrt(q2)
+    a = pdf.xfxQ(g.pids, cuda(x), cuda(q)).cpu().numpy()
+    b = pdf.xfxQ2(g.pids, cuda(x), cuda(q * q)).cpu().numpy()
+    assert np.array_equal(a, b)
+    qa = pdf.alphasQ(cuda(q)).cpu().numpy()
+    qb = pdf.alphasQ2(cuda(q * q)).cpu().numpy()
+    assert np.array_equal(qa, qb)
+
+
+def test_pointwise_parity(lib_built):
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_small(seed=1003, pids=synth.PIDS_13)
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    pid, x, q2, _ = synth.queries_pointwise(200_003)
+    pid[::7] = 21                               # the gluon under its other name
+    pid[::11] = 9                               # a pid not in the grid
+    got = pdf.xfxQ2_pw(cuda(pid), cuda(x), cuda(q2)).cpu().numpy()
+    ref = o.xfxq2_pw(pid, x, q2)
+    kap = o.kappa(pid, x, q2, pointwise=True)
+    parity.check(got, ref, kap, what="pointwise")
+    assert np.all(got[::11] == 0.0)
+    # matrix form, same points: column of the point's pid
+    full = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
+    col = {int(p): i for i, p in enumerate(g.pids)}
+    sel = np.array([col.get(0 if p == 21 else int(p), -1) for p in pid])
+    m = sel >= 0
+    assert np.array_equal(full[np.arange(x.size)[m], sel[m]], got[m])
+
+
+def test_golden_exact_values(lib_built):
+    from paper_2012_08221_gb300.pdf import PDF
+    g, x, q2, exp, exp_as = load_golden()
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
+    parity.check(got, exp, o.kappa(g.pids, x, q2), what="golden")
+    parity.check(pdf.alphasQ2(cuda(q2)).cpu().numpy(), exp_as, 8 * np.abs(exp_as), what="golden alphas")
+
+
+def test_edge_cases(nnpdf):
+    g, pdf, o = nnpdf
+    pids = np.array([-6, 0, 21, 3, 7, 22], dtype=np.int32)     # 7, 22 absent
+    xs, qs = [], []
+    for k in range(g.n_x):                       # every knot, several rows
+        for r in (0, 7, 8, 19, 20, 39, 40, 49):
+            xs.append(g.x_knots[k])
+            qs.append(g.q_knots[r] ** 2)
+    for v in (1.0, np.nextafter(1.0, 0), 1e-9, np.nextafter(1e-9, 0), 1e-12, 3e-300, 5e-324):
+        for q2 in (1.0, np.nextafter(1.0, 0), 0.04, 1e10, 3e10, 1.51 ** 2, 4.92 ** 2, 172.5 ** 2):
+            xs.append(v)
+            qs.append(q2)
+    nan, inf = float("nan"), float("inf")
+    bad = [(0.0, 10.0), (-1e-3, 10.0), (1.0 + 2e-16, 10.0), (0.1, 0.0), (0.1, -4.0), (nan, 10.0),
+           (0.1, nan), (0.1, inf), (inf, 10.0), (-0.0, 10.0)]
+    xs += [b[0] for b in bad]
+    qs += [b[1] for b in bad]
+    x, q2 = np.array(xs), np.array(qs)
+    pdf.status()
+    got = pdf.xfxQ2(pids, cuda(x), cuda(q2)).cpu().numpy()
+    assert pdf.status() & 1
+    assert pdf.status() == 0                     # reading clears
+    ref = o.xfxq2_batch(pids, x, q2)
+    kap = o.kappa(pids, x, q2)
+    parity.check(got, ref, kap, what="edge cases")
+    nb = len(bad)
+    assert np.all(np.isnan(got[-nb:]))
+    assert np.all(got[:-nb, 4] == 0.0) and np.all(got[:-nb, 5] == 0.0)
+    assert np.array_equal(got[:, 1], got[:, 2], equal_nan=True)  # pid 0 and 21
+    # knots reproduce the stored values (upper subgrid at thresholds)
+    n_k = g.n_x * 8
+    rows = np.tile([0, 8, 8, 20, 20, 40, 40, 49], g.n_x)
+    ks = np.repeat(np.arange(g.n_x), 8)
+    want = g.values[0, rows, ks][:, [0, 6, 9]]
+    err = np.abs(got[:n_k][:, [0, 1, 3]] - want)
+    assert np.all(err <= 1e-13 * (np.abs(want) + 1e-3))
+
+
+def test_empty_and_tiny_batches(small):
+    g, pdf, o = small
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    assert pdf.xfxQ2(g.pids, e, e).shape == (0, g.n_flav)
+    assert pdf.alphasQ2(e).shape == (0,)
+    assert pdf.xfxQ2_pw(torch.empty(0, dtype=torch.int32, device="cuda"), e, e).shape == (0,)
+    for n in (1, 31, 255, 257):
+        x, q2 = synth.queries_small(n, seed=n)
+        got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
+        parity.check(got, o.xfxq2_batch(g.pids, x, q2), o.kappa(g.pids, x, q2), what=f"n={n}")
+
+
+def test_two_subgrid_tiny_grid_everywhere(lib_built):
+    """A tiny grid with unequal duplicated rows: exercises the threshold rule."""
+    from paper_2012_08221_gb300.pdf import PDF
+    g = tiny_two_sub(seed=3, dup_equal=False)
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    rng = np.random.default_rng(8)
+    x = np.exp(rng.uniform(math.log(1e-7), 0, 50_000))
+    q2 = np.exp(rng.uniform(math.log(0.2), math.log(1e4), 50_000))
+    x[:6] = g.x_knots[[0, 1, 2, 3, 4, 4]]
+    q2[:6] = g.q_knots[[2, 3, 3, 2, 0, 5]] ** 2
+    got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
+    parity.check(got, o.xfxq2_batch(g.pids, x, q2), o.kappa(g.pids, x, q2), what="tiny two-subgrid")
+
+
+def test_table_log_against_cuda_log(small):
+    g, pdf, o = small
+    rng = np.random.default_rng(5)
+    v = np.concatenate([np.exp(rng.uniform(-700, 700, 200_000)), [5e-324, 1e-310, 2.2250738585072014e-308,
+                        1.0, np.nextafter(1.0, 2), np.nextafter(1.0, 0), 1.7976931348623157e308]])
+    V = cuda(v)
+    got = pdf.debug_log(V).cpu().numpy()
+    ref = torch.log(V).cpu().numpy()
+    # within 3 units in the last place of CUDA's log, or 1e-18 absolute
+    ulp = np.spacing(np.abs(ref))
+    assert np.all(np.abs(got - ref) <= 3 * ulp + 1e-18)
+    assert got[-4] == 0.0                        # ln 1 is exact

@@ -1,0 +1,142 @@
+"""GPU fused luminosity workload: per-event luminosity, alpha_s and
+L = (1/n) sum lum against the oracle (including the injected low tail that
+exercises the extrapolation), and the grid gradient of L."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleGrid
+from paper_2012_08221_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+@pytest.fixture(scope="module")
+def lhc():
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    g = synth.grid_nnpdf(seeds=(1005, 1006, 1007))   # three replicas, member 0 used
+    return g, PDF.from_grid(g), OracleGrid.from_synth(g)
+
+
+def _event_logs(ev, n):
+    h = 0.5 * ev.ln_tau[:n]
+    u1 = h + ev.y[:n]
+    u2 = h - ev.y[:n]
+    w = ev.ln_tau[:n] + ev.ln_s
+    f = ev.flags[:n]
+    w = np.where(f & 1, ev.ln_mu2[:n], w)
+    u1 = np.where(f & 2, ev.ln_x1[:n], u1)
+    return u1, u2, w
+
+
+def _lum_kappa(g, o, ev, n):
+    """Term scale of lum: sum_a kappa(x1)_a |f(x2)_-a| + |f(x1)_a| kappa(x2)_-a."""
+    u1, u2, w = _event_logs(ev, n)
+    x1, x2, q2 = np.exp(u1), np.exp(u2), np.exp(w)
+    k1 = o.kappa(g.pids, x1, q2)
+    k2 = o.kappa(g.pids, x2, q2)
+    f1 = np.abs(o.xfxq2_batch(g.pids, x1, q2))
+    f2 = np.abs(o.xfxq2_batch(g.pids, x2, q2))
+    anti = np.array([list(g.pids).index(-p) for p in g.pids])
+    return np.sum(k1 * f2[:, anti] + f1 * k2[:, anti] + k1 * k2[:, anti], axis=1)
+
+
+def test_luminosity_parity(lhc):
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity
+    g, pdf, o = lhc
+    n = 30_011
+    ev = synth.events_lhc(n, seed=91)
+    dev = DeviceEvents.from_host(ev)
+    L, lum, a_s = luminosity(pdf, dev)
+    Lr, lumr, asr = o.lumi(ev)
+    kap = _lum_kappa(g, o, ev, n)
+    parity.check(lum.cpu().numpy(), lumr, kap, what="lum")
+    parity.check(a_s.cpu().numpy(), asr, 8 * np.abs(asr), what="lumi alpha_s")
+    assert abs(L.item() - Lr) <= 1e-12 * kap.sum() / n
+    assert np.sum(ev.flags != 0) > 0.03 * n          # the tail is there
+
+
+def test_luminosity_tail_only(lhc):
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity
+    g, pdf, o = lhc
+    ev = synth.events_lhc(4000, seed=92, tail=1.0)   # every event in the low tail
+    L, lum, a_s = luminosity(pdf, DeviceEvents.from_host(ev))
+    Lr, lumr, asr = o.lumi(ev)
+    parity.check(lum.cpu().numpy(), lumr, _lum_kappa(g, o, ev, 4000), what="tail lum")
+    parity.check(a_s.cpu().numpy(), asr, 8 * np.abs(asr), what="tail alpha_s")
+
+
+def test_luminosity_gradient_against_oracle(lhc):
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity_backward
+    g, pdf, o = lhc
+    ev = synth.events_lhc(3001, seed=93)
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    luminosity_backward(pdf, DeviceEvents.from_host(ev), 1.0, gv)
+    ref = o.lumi_dgrid(ev)
+    got = gv.cpu().numpy()
+    tol = 1e-9 * np.maximum(np.abs(ref), o.lumi_dgrid(ev, absval=True)) + 1e-300
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+
+
+def test_luminosity_autograd(lhc):
+    from paper_2012_08221_gb300.autograd import lumi
+    from paper_2012_08221_gb300.lumi import DeviceEvents
+    g, pdf, o = lhc
+    ev = synth.events_lhc(2000, seed=94)
+    vals = torch.tensor(g.values, device="cuda", requires_grad=True)
+    L = lumi(pdf, vals, DeviceEvents.from_host(ev))
+    (3.0 * L).backward()
+    ref = 3.0 * o.lumi_dgrid(ev)
+    got = vals.grad[0].cpu().numpy()
+    kap = 3.0 * o.lumi_dgrid(ev, absval=True)
+    assert np.all(np.abs(got - ref) <= 1e-9 * np.maximum(np.abs(ref), kap) + 1e-300)
+    assert torch.count_nonzero(vals.grad[1:]) == 0
+    assert abs(L.item() - o.lumi(ev)[0]) <= 1e-12 * abs(L.item()) + 1e-15
+
+
+def test_full_size_luminosity_sampled(lhc):
+    """1e8 events in one launch: L equals the mean of the per-event values,
+    sampled events match the oracle, and the grid gradient obeys the exact
+    flavour sum rule sum_cells dL/dv[.][b] = mean_e(f_-b(x2) + f_-b(x1))."""
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
+    g, pdf, o = lhc
+    n = 100_000_000
+    ev = synth.events_lhc(n)
+    dev = DeviceEvents.from_host(ev)
+    L, lum, a_s = luminosity(pdf, dev)
+    lum_h = lum.cpu().numpy()
+    assert abs(L.item() - lum_h.sum() / n) <= 1e-12 * np.abs(lum_h).sum() / n
+    idx = np.random.default_rng(5).choice(n, 1500, replace=False)
+    sub = synth.Events(ev.ln_tau[idx], ev.y[idx], ev.flags[idx], ev.ln_mu2[idx], ev.ln_x1[idx], ev.ln_s)
+    Lr, lumr, asr = o.lumi(sub)
+    parity.check(lum_h[idx], lumr, _lum_kappa(g, o, sub, idx.size), what="full lum")
+    parity.check(a_s[cuda(idx)].cpu().numpy(), asr, 8 * np.abs(asr), what="full alpha_s")
+    del lum, a_s
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    luminosity_backward(pdf, dev, 1.0, gv)
+    G = gv.cpu().numpy()
+    # sum rule from the forward kernel on the same points (x from ln x)
+    u1, u2, w = _event_logs(ev, n)
+    anti = [list(g.pids).index(-p) for p in g.pids]
+    acc = np.zeros(g.n_flav)
+    acc_abs = np.zeros(g.n_flav)
+    step = 10_000_000
+    for s in range(0, n, step):
+        X1, X2, Q2 = cuda(np.exp(u1[s:s + step])), cuda(np.exp(u2[s:s + step])), cuda(np.exp(w[s:s + step]))
+        f1 = pdf.xfxQ2(g.pids, X1, Q2).sum(0).cpu().numpy()
+        f2 = pdf.xfxQ2(g.pids, X2, Q2).sum(0).cpu().numpy()
+        acc += f1 + f2
+        a1 = pdf.xfxQ2(g.pids, X1, Q2).abs().sum(0).cpu().numpy()
+        acc_abs += a1
+    for b in range(g.n_flav):
+        want = acc[anti[b]] / n
+        assert abs(G[:, :, b].sum() - want) <= 1e-9 * (abs(want) + acc_abs[anti[b]] / n)
