@@ -166,8 +166,9 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+def measured_traffic(kernel, units):
+    """DRAM bytes (read + write) per launch of `kernel` over `units` points,
+    scaled from the committed ncu capture's bytes per point, if that capture
     was taken on the current kernel sources (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -177,7 +178,7 @@ def measured_traffic(kernel):
     e = d.get(kernel)
     if not e or e.get("source_hash") != source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e["dram_bytes_per_unit"] * units
 
 
 def peaks():
@@ -195,6 +196,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="all", help="comma list of fwdbwd,batched,lumi or all/none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=N_POINTS,
+                    help="points of the headline workload (smaller only for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -253,12 +256,13 @@ def main():
     # ---------------------------------------------------- headline workload
     g = synth.grid_nnpdf()
     pdf = PDF.from_grid(g, device=dev)
-    x, q2, q2a = synth.queries_nnpdf(N_POINTS, seed=2002)
+    npts = args.points
+    x, q2, q2a = synth.queries_nnpdf(npts, seed=2002)
     X = torch.as_tensor(x, device=dev)
     Q = torch.as_tensor(q2, device=dev)
     QA = torch.as_tensor(q2a, device=dev)
-    OUT = torch.empty((N_POINTS, g.n_flav), dtype=torch.float64, device=dev)
-    AS = torch.empty(N_POINTS, dtype=torch.float64, device=dev)
+    OUT = torch.empty((npts, g.n_flav), dtype=torch.float64, device=dev)
+    AS = torch.empty(npts, dtype=torch.float64, device=dev)
     pids = g.pids
 
     def step():
@@ -274,12 +278,12 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     ms, k_ms = timed(step, args.steps, args.warmup, kstep)
-    evals = N_POINTS * g.n_flav
+    evals = npts * g.n_flav
     value = world * evals / (ms * 1e-3)
-    flops_launch = N_POINTS * work.xfxq2_point_flops(g.n_flav)
-    bytes_launch = N_POINTS * work.xfxq2_point_bytes(g.n_flav)
+    flops_launch = npts * work.xfxq2_point_flops(g.n_flav)
+    bytes_launch = npts * work.xfxq2_point_bytes(g.n_flav)
     achieved = flops_launch / (k_ms * 1e-3)
-    traffic = measured_traffic("k_xfxq2")
+    traffic = measured_traffic("k_xfxq2", npts)
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": "k_xfxq2",
                 "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
@@ -391,7 +395,7 @@ def main():
     # ----------------------------------------------------------- end to end
     xh = torch.as_tensor(x).pin_memory()
     qh = torch.as_tensor(q2).pin_memory()
-    oh = torch.empty((N_POINTS, g.n_flav), dtype=torch.float64).pin_memory()
+    oh = torch.empty((npts, g.n_flav), dtype=torch.float64).pin_memory()
     pdf.xfxQ2_host(pids, xh, qh, out=oh)
     KE = max(2, min(args.steps, 5))
     barrier()
@@ -400,8 +404,8 @@ def main():
         pdf.xfxQ2_host(pids, xh, qh, out=oh)
     barrier()
     e2e_s = max_ranks((time.perf_counter() - t0) / KE)
-    e2e = {"value": world * evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 16 * N_POINTS,
-           "d2h_bytes_per_step": 8 * g.n_flav * N_POINTS, "ms_per_step": 1e3 * e2e_s,
+    e2e = {"value": world * evals / e2e_s, "unit": "evals/s", "h2d_bytes_per_step": 16 * npts,
+           "d2h_bytes_per_step": 8 * g.n_flav * npts, "ms_per_step": 1e3 * e2e_s,
            "entry_point": "xfxQ2_host (pinned host buffers, chunked copy/compute overlap)"}
 
     cpu = None
@@ -416,8 +420,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded NNPDF-shaped grid and log-uniform queries)",
-                "config": {"workload": WORKLOAD, "n_points": N_POINTS, "n_flav": int(g.n_flav),
-                           "alphas_points": N_POINTS, "parallelism": f"replicas x{world}",
+                "config": {"workload": WORKLOAD if npts == N_POINTS else WORKLOAD + f" (reduced to {npts} points)",
+                           "n_points": npts, "n_flav": int(g.n_flav), "alphas_points": npts, "parallelism": f"replicas x{world}",
                            "l2": "inputs + outputs of a step (1.36 GB) exceed the 129 MB L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 2 * args.steps, "clocks": clk, "forms": forms}

@@ -248,7 +248,8 @@ __device__ __forceinline__ void patch_d(const double *__restrict__ C, const Axis
     *dtq = fma(dq3, i[3], fma(dq2, i[2], i[1]));
 }
 
-// Stencil weights W_i = sum_m M[m][i] b_m of one axis (i <-> knot cell-1+i).
+// Stencil weights W_i = sum_m M[m][i] b_m of one axis (i <-> knot cell-1+i);
+// outside the knot range the exact weights of the linear continuation.
 __device__ __forceinline__ void stencil_weights(const double *__restrict__ M, const Axis &A, double W[4])
 {
     const double2 *M2 = reinterpret_cast<const double2 *>(M);
@@ -260,6 +261,13 @@ __device__ __forceinline__ void stencil_weights(const double *__restrict__ M, co
     W[1] = fma(A.b3, r3a.y, fma(A.b2, r2a.y, fma(A.t, r1a.y, r0a.y)));
     W[2] = fma(A.b3, r3b.x, fma(A.b2, r2b.x, fma(A.t, r1b.x, r0b.x)));
     W[3] = fma(A.b3, r3b.y, fma(A.b2, r2b.y, fma(A.t, r1b.y, r0b.y)));
+    if (!A.in) {
+        // linear continuation: exactly (1 - t, t) on the cell's two knots
+        W[0] = 0.0;
+        W[1] = 1.0 - A.t;
+        W[2] = A.t;
+        W[3] = 0.0;
+    }
 }
 
 __device__ __forceinline__ void flag_status(const GridDev &g, bool bad)

