@@ -185,6 +185,26 @@ int pdf_batch_info(pdfgpu_batch_t b, int32_t *block, int32_t *qpt, int32_t *stag
                    int32_t *ctas, float *ms);
 int pdf_batch_free(pdfgpu_batch_t b);
 
+/* Batched evaluation that allocates nothing (the paper has no counterpart).
+ * For callers that cannot allocate device memory when they evaluate: a host
+ * framework that reserved all device memory up front, or an event loop that
+ * must not call cudaMalloc (it can fail on a full device and can synchronise
+ * the whole device).  Evaluates the requests like pdf_batch_prepare +
+ * pdf_batch_run, in one launch of the same persistent kernel with a fixed
+ * shape (256 threads, 2 points per thread), but keeps its scratch -- the tile
+ * ticket and the request and grid tables -- in one static device array of the
+ * library (about 85 KB, held on every GPU that loads the library until the
+ * process exits) instead of allocating per batch.  Limits: 1..1024 requests
+ * and at most 32 distinct grids per call; beyond them the call fails with
+ * PDF_E_RANGE before touching the GPU.  descs is HOST memory read during the
+ * call; x, q2, out are DEVICE pointers used by the launch on `stream`.  The
+ * first call on a device looks up the array's device address once, with that
+ * device current; make that first call before any stream capture.  Every call
+ * shares the one array and overwrites it (the ticket is reset on each call):
+ * calls that overlap on the GPU (different streams) race; serialise them.
+ * Asynchronous on `stream`. */
+int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_desc, pdfgpu_stream_t stream);
+
 /* Fused parton-luminosity workload (PDFFlow Sec. 3.1-3.2: event kinematics,
  * two xfxQ2 calls, luminosity formed from the products).  Per event e:
  *   ln x1 = ln_tau/2 + y, ln x2 = ln_tau/2 - y, ln Q^2 = ln_tau + ln_s;

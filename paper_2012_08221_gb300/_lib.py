@@ -59,6 +59,7 @@ SIGNATURES = {
     "pdf_batch_run": [c_batch, _VP],
     "pdf_batch_info": [c_batch, _I, _I, _I, _I, C.POINTER(C.c_float)],
     "pdf_batch_free": [c_batch],
+    "pdf_batch_run_noalloc": [C.POINTER(BatchDesc), C.c_int32, _VP],
     "pdf_lumi": [c_grid, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_double, C.c_int64,
                  _VP, _VP, _VP, _VP],
     "pdf_lumi_backward": [c_grid, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_double, C.c_int64,

@@ -13,10 +13,12 @@
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -452,5 +454,113 @@ extern "C" int pdf_batch_info(pdfgpu_batch_t b, int32_t *block, int32_t *qpt, in
     if (stage) *stage = b->shape.stage;
     if (ctas) *ctas = b->ctas;
     if (ms) *ms = b->tuned_ms;
+    return PDF_OK;
+}
+
+// ------------------------------------------------ allocation-free variant
+//
+// The same persistent kernel, launched once per call with a fixed shape
+// (256 threads, 2 points per thread), whose scratch -- the tile ticket and
+// the request and grid tables -- lives in one file-scope device array instead
+// of memory allocated per batch.  Nothing here calls cudaMalloc or cudaFree.
+
+namespace {
+
+constexpr int kNoAllocMaxRequests = 1024;
+constexpr int kNoAllocMaxGrids = 32;
+
+struct NoAllocScratch {
+    unsigned long long ticket;
+    unsigned long long pad[31];              // keeps the tables 256-byte aligned
+    GridDev grids[kNoAllocMaxGrids];
+    BatchReq reqs[kNoAllocMaxRequests];
+};
+
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_dev_addr[kNoAllocDevices];   // device address of the array, per device
+NoAllocScratch g_noalloc_host;               // host staging, static (no heap use)
+
+}  // namespace
+
+// About 85 KB per device that loads the library, held until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_desc,
+                                     pdfgpu_stream_t stream)
+{
+    clear_error();
+    if (!descs) return fail(PDF_E_ARG, "null request list");
+    if (n_desc < 1 || n_desc > kNoAllocMaxRequests)
+        return fail(PDF_E_RANGE, "pdf_batch_run_noalloc takes 1 to 1024 requests; got " +
+                                     std::to_string(n_desc));
+    int dev = 0;
+    PDF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocDevices) return fail(PDF_E_RANGE, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocScratch &H = g_noalloc_host;
+    int ngrids = 0;
+    pdfgpu_grid_t handles[kNoAllocMaxGrids];
+    int out_stride = 1;
+    const int block = 256, qpt = 2;
+    const int64_t tile = (int64_t)block * qpt;
+    int64_t ntiles = 0;
+    for (int i = 0; i < n_desc; ++i) {
+        const pdfgpu_batch_desc &D = descs[i];
+        int rc = check_grid(D.grid, true);
+        if (rc) return rc;
+        if (D.grid->device != dev) return fail(PDF_E_ARG, "request grid lives on another device");
+        if (D.member < 0 || D.member >= D.grid->d.nmem || D.n_pid < 1 || D.n_pid > kMaxReqPids ||
+            D.n < 0 || (D.n > 0 && (!D.x || !D.q2 || !D.out)))
+            return fail(PDF_E_ARG, "bad request " + std::to_string(i));
+        int gi = -1;
+        for (int k = 0; k < ngrids; ++k)
+            if (handles[k] == D.grid) gi = k;
+        if (gi < 0) {
+            if (ngrids == kNoAllocMaxGrids)
+                return fail(PDF_E_RANGE, "pdf_batch_run_noalloc takes at most 32 distinct grids");
+            gi = ngrids++;
+            handles[gi] = D.grid;
+            H.grids[gi] = D.grid->d;
+        }
+        Cols cols;
+        rc = resolve_cols(D.grid, D.pids, D.n_pid, &cols);
+        if (rc) return rc;
+        BatchReq &r = H.reqs[i];
+        r.grid = gi;
+        r.member = D.member;
+        r.npid = D.n_pid;
+        for (int a = 0; a < kMaxReqPids; ++a) r.cols[a] = a < D.n_pid ? cols.c[a] : -1;
+        r.x = D.x;
+        r.q2 = D.q2;
+        r.out = D.out;
+        r.n = D.n;
+        r.tile0 = ntiles;
+        ntiles += (D.n + tile - 1) / tile;
+        out_stride = std::max(out_stride, (int)D.n_pid);
+    }
+    H.ticket = 0;                      // the array keeps the previous call's ticket
+    if (!g_noalloc_dev_addr[dev]) {
+        // once per device, with that device current
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the batch scratch");
+        g_noalloc_dev_addr[dev] = p;
+    }
+    NoAllocScratch *S = reinterpret_cast<NoAllocScratch *>(g_noalloc_dev_addr[dev]);
+    cudaStream_t st = (cudaStream_t)stream;
+    // header + grid table + the used part of the request table; a copy from
+    // pageable memory returns once the source has been staged, so the static
+    // host buffer may be refilled by the next call
+    size_t bytes = offsetof(NoAllocScratch, reqs) + (size_t)n_desc * sizeof(BatchReq);
+    PDF_CUDA(cudaMemcpyAsync(S, &H, bytes, cudaMemcpyHostToDevice, st));
+    if (ntiles == 0) return PDF_OK;
+    KernelFn k = kernel_for(Shape{block, qpt, 0});
+    size_t smem = (size_t)block * out_stride * sizeof(double);
+    int sms = 0;
+    PDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int ctas = sms * occupancy((const void *)k, block, smem);
+    k<<<ctas, block, smem, st>>>(S->grids, S->reqs, n_desc, ntiles, &S->ticket, out_stride);
+    PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }

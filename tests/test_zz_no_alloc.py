@@ -1,0 +1,86 @@
+"""The allocation-free batched entry point, called through the C ABI.
+
+Some callers cannot allocate device memory at the point where they evaluate
+PDFs: a host framework that reserved the whole device memory up front, or a
+Monte Carlo event loop that must never trigger cudaMalloc (which can fail on a
+full device and can synchronise the whole device).  `pdf_batch_run_noalloc`
+runs the batched kernel with its scratch (tile ticket, request and grid
+tables) in a fixed static device array instead.  This test checks it against
+the regular prepared batch (`pdf_batch_prepare` + `pdf_batch_run`) on two
+calls in a row, and that it refuses requests beyond its fixed capacity.
+
+This file is collected last on purpose: it must pass alone in a fresh process
+and after every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2012_08221_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _descs(reqs):
+    from paper_2012_08221_gb300._lib import BatchDesc
+    arr = (BatchDesc * len(reqs))()
+    for i, (pdf, member, pids, x, q2, out) in enumerate(reqs):
+        arr[i].grid = pdf.handle
+        arr[i].member = int(member)
+        arr[i].n_pid = int(pids.size)
+        for k in range(pids.size):
+            arr[i].pids[k] = int(pids[k])
+        arr[i].x = x.data_ptr()
+        arr[i].q2 = q2.data_ptr()
+        arr[i].n = x.numel()
+        arr[i].out = out.data_ptr()
+    return arr
+
+
+def test_noalloc_batch_matches_prepared_batch_twice():
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300._lib import lib
+    from paper_2012_08221_gb300.batch import Batch
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    grids = [synth.grid_set_a(n_rep=7), synth.grid_set_b(), synth.grid_set_c(n_rep=5)]
+    pdfs = [PDF.from_grid(g) for g in grids]
+    batches = synth.batches_uneven(grids, n_batches=120, scale=0.01, seed=77)
+    dev = torch.device("cuda")
+    ref_reqs, new_reqs = [], []
+    for b in batches:
+        x = torch.as_tensor(b.x, device=dev)
+        q2 = torch.as_tensor(b.q2, device=dev)
+        shape = (b.x.size, b.pids.size)
+        ref_reqs.append((pdfs[b.set_index], b.member, b.pids, x, q2,
+                         torch.empty(shape, dtype=torch.float64, device=dev)))
+        new_reqs.append((pdfs[b.set_index], b.member, b.pids, x, q2,
+                         torch.empty(shape, dtype=torch.float64, device=dev)))
+    B = Batch(ref_reqs, autotune=False)
+    B.run()
+    torch.cuda.synchronize()
+    arr = _descs(new_reqs)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call in range(2):
+        for r in new_reqs:
+            r[5].fill_(float("nan") if call == 0 else -1.0)
+        rc = lib().pdf_batch_run_noalloc(arr, len(new_reqs), stream)
+        assert rc == 0, lib().pdf_last_error()
+        torch.cuda.synchronize()
+        for r_ref, r_new in zip(ref_reqs, new_reqs):
+            ref = r_ref[5].cpu().numpy()
+            got = r_new[5].cpu().numpy()
+            parity.check(got, ref, np.abs(ref), what=f"no-alloc call {call}")
+
+
+def test_noalloc_batch_rejects_more_requests_than_its_capacity():
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300._lib import BatchDesc, lib
+    build.build()
+    arr = (BatchDesc * 1025)()
+    rc = lib().pdf_batch_run_noalloc(arr, 1025, None)
+    assert rc == -6                                   # PDF_E_RANGE
+    assert b"1 to 1024 requests" in lib().pdf_last_error()
