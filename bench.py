@@ -158,25 +158,24 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
-def source_hash():
+def source_hash(files):
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2012_08221_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel, units):
     """DRAM bytes (read + write) per launch of `kernel` over `units` points,
     scaled from the committed ncu capture's bytes per point, if that capture
-    was taken on the current kernel sources (else None)."""
+    was taken on the current sources of the kernel (else None)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
     except (OSError, ValueError):
         return None
     e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(e.get("files", [])):
         return None
     return e["dram_bytes_per_unit"] * units
 
