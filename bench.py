@@ -180,6 +180,23 @@ def measured_traffic(kernel, units):
     return e["dram_bytes_per_unit"] * units
 
 
+def reduce_max(v, world, device):
+    """Max of a float over all ranks (identity for one rank)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Replicas: every rank processes `units_per_rank`; the job's rate is all
+    ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -222,11 +239,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     def max_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, dev)
 
     peak = fp64_peak()                              # FLOP/s, burst
     stream = torch.cuda.current_stream(dev)
@@ -278,7 +291,7 @@ def main():
     clocks.start()
     ms, k_ms = timed(step, args.steps, args.warmup, kstep)
     evals = npts * g.n_flav
-    value = world * evals / (ms * 1e-3)
+    value = whole_job_rate(evals, world, ms)
     flops_launch = npts * work.xfxq2_point_flops(g.n_flav)
     bytes_launch = npts * work.xfxq2_point_bytes(g.n_flav)
     achieved = flops_launch / (k_ms * 1e-3)

@@ -453,6 +453,7 @@ extern "C" int pdf_free_grid(pdfgpu_grid_t g)
     cudaDeviceSynchronize();
     for (void *p : g->blocks) cudaFree(p);
     if (g->partials) cudaFree(g->partials);
+    if (g->lumi_scratch) cudaFree(g->lumi_scratch);
     for (int s = 0; s < 3; ++s) {
         for (int k = 0; k < 3; ++k)
             if (g->stage[s][k]) cudaFree(g->stage[s][k]);

@@ -119,17 +119,152 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
     if (threadIdx.x == 0) *L = red[0] * inv_n;
 }
 
-// dL/dv for L = (1/n) sum_e sum_a f_a(x1) f_{-a}(x2), times `scale`:
-//   d/dv[.][b] gets W(x1) f_{-b}(x2) + W(x2) f_{-b}(x1).
-__global__ void __launch_bounds__(kBlock) k_lumi_bwd(GridDev g, Cols anti, int member,
+// ---------------------------------------------------------------- adjoint
+//
+// dL/dv for L = (1/n) sum_e sum_a f_a(x1) f_{-a}(x2), times dL:
+//   dL/dv[row][knot][b] = scale sum over partons p of all events of
+//                         Wq_j(p) Wx_i(p) f_{-b}(other parton)
+// over each parton's 4x4 stencil.  Instead of 16 x F global atomics per
+// parton, partons are grouped by grid cell and accumulated in registers:
+//   1. k_lumi_rec: per event the two partons' F values (the partner factors)
+//      and, per parton, its cell key, local coordinates and range flags;
+//      a histogram of the keys;
+//   2. k_scan: bin offsets;  3. k_scatter: parton ids in cell order;
+//   4. k_lumi_accum: each warp walks a run of cell-sorted partons in batches
+//      of 32 (one parton per lane computes its 16 stencil weights into shared
+//      memory), every lane owns fixed (stencil slot, flavour) outputs and
+//      accumulates 7 FMAs per parton; accumulators go to the gradient with one
+//      atomic per output when the cell changes.
+// Events are processed in chunks so that the scratch stays bounded.
+
+constexpr int kAccWarps = 4;
+constexpr int kSegment = 1024;        // partons per warp
+constexpr int kMaxSmemBins = 12 * 1024;
+
+__global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
                                                      const double *__restrict__ ln_tau,
                                                      const double *__restrict__ y,
                                                      const uint8_t *__restrict__ flags,
                                                      const double *__restrict__ ln_mu2,
                                                      const double *__restrict__ ln_x1, double ln_s,
-                                                     int64_t n, double scale,
-                                                     double *__restrict__ gval)
+                                                     int64_t e0, int m, int *__restrict__ key,
+                                                     double *__restrict__ tx, double *__restrict__ tq,
+                                                     uint8_t *__restrict__ fin, double *__restrict__ P,
+                                                     int *__restrict__ hist, int nbins)
 {
+    extern __shared__ int shist[];
+    const bool sh = nbins <= kMaxSmemBins;
+    if (sh) {
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x) shist[k] = 0;
+        __syncthreads();
+    }
+    const int F = g.nflav;
+    const size_t cell_stride = (size_t)F * 16;
+    const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        Event E = event(e0 + i, ln_tau, y, flags, ln_mu2, ln_x1, ln_s);
+        if (E.bad) {
+            key[2 * i] = -1;
+            key[2 * i + 1] = -1;
+            continue;
+        }
+        Axis Q = axis_w(g, E.w);
+        Axis X1 = axis_u(g, E.u1);
+        Axis X2 = axis_u(g, E.u2);
+        const double *c1 = cm + ((size_t)Q.cell * g.nxc + X1.cell) * cell_stride;
+        const double *c2 = cm + ((size_t)Q.cell * g.nxc + X2.cell) * cell_stride;
+        double *p1 = P + (size_t)i * 2 * F;
+        double *p2 = p1 + F;
+        for (int a = 0; a < F; ++a) {
+            p1[a] = patch(c1 + a * 16, X1, Q);
+            p2[a] = patch(c2 + a * 16, X2, Q);
+        }
+        int k1 = Q.cell * g.nxc + X1.cell, k2 = Q.cell * g.nxc + X2.cell;
+        key[2 * i] = k1;
+        key[2 * i + 1] = k2;
+        tx[2 * i] = X1.t;
+        tx[2 * i + 1] = X2.t;
+        tq[i] = Q.t;
+        fin[2 * i] = (uint8_t)(Q.in | (X1.in << 1));
+        fin[2 * i + 1] = (uint8_t)(Q.in | (X2.in << 1));
+        if (sh) {
+            atomicAdd(&shist[k1], 1);
+            atomicAdd(&shist[k2], 1);
+        } else {
+            atomicAdd(&hist[k1], 1);
+            atomicAdd(&hist[k2], 1);
+        }
+    }
+    if (sh) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+            if (shist[k]) atomicAdd(&hist[k], shist[k]);
+    }
+}
+
+// Exclusive scan of hist[0..nbins) into offs and cursor; offs[nbins] = total.
+__global__ void k_scan(const int *__restrict__ hist, int nbins, int *__restrict__ offs,
+                       int *__restrict__ cursor)
+{
+    __shared__ int part[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nbins; base += blockDim.x) {
+        int k = base + threadIdx.x;
+        int v = k < nbins ? hist[k] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            int t = (int)threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+            __syncthreads();
+            part[threadIdx.x] += t;
+            __syncthreads();
+        }
+        int excl = carry + part[threadIdx.x] - v;
+        if (k < nbins) {
+            offs[k] = excl;
+            cursor[k] = excl;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) offs[nbins] = carry;
+}
+
+__global__ void k_scatter(const int *__restrict__ key, int nrec, int *__restrict__ cursor,
+                          int *__restrict__ perm)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += gridDim.x * blockDim.x) {
+        int k = key[r];
+        if (k >= 0) perm[atomicAdd(&cursor[k], 1)] = r;
+    }
+}
+
+// Rebuild an axis from its stored local coordinate (t and range flag).
+__device__ __forceinline__ Axis axis_from(int cell, double t, bool in)
+{
+    Axis A;
+    A.cell = cell;
+    A.in = in;
+    make_basis(A, t);
+    return A;
+}
+
+__global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols anti,
+                                                               const int *__restrict__ perm,
+                                                               const int *__restrict__ offs, int nbins,
+                                                               const int *__restrict__ key,
+                                                               const double *__restrict__ tx,
+                                                               const double *__restrict__ tq,
+                                                               const uint8_t *__restrict__ fin,
+                                                               const double *__restrict__ P, double scale,
+                                                               double *__restrict__ gval)
+{
+    __shared__ double sW[kAccWarps][32][17];
+    __shared__ double sP[kAccWarps][32][17];
+    __shared__ int sK[kAccWarps][32];
     __shared__ signed char santi[PDF_MAX_PIDS];
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -137,58 +272,74 @@ __global__ void __launch_bounds__(kBlock) k_lumi_bwd(GridDev g, Cols anti, int m
     }
     __syncthreads();
     const int F = g.nflav;
-    const size_t cell_stride = (size_t)F * 16;
-    const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        Event E = event(e, ln_tau, y, flags, ln_mu2, ln_x1, ln_s);
-        if (E.bad) continue;
-        Axis Q = axis_w(g, E.w);
-        Axis X1 = axis_u(g, E.u1);
-        Axis X2 = axis_u(g, E.u2);
-        const double *c1 = cm + ((size_t)Q.cell * g.nxc + X1.cell) * cell_stride;
-        const double *c2 = cm + ((size_t)Q.cell * g.nxc + X2.cell) * cell_stride;
-        double P1[kMaxLumiFlav], P2[kMaxLumiFlav];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nvalid = offs[nbins];
+    const int64_t gw = (int64_t)blockIdx.x * kAccWarps + wid;
+    const int64_t beg = gw * kSegment;
+    if (beg >= nvalid) return;
+    const int end = (int)min((int64_t)nvalid, beg + kSegment);
+    // this lane's outputs: stencil slot s (fixed) and flavours b_k = (lane >> 4) + 2k
+    const int s = lane & 15, j = s >> 2, i = s & 3;
+    int bk[7], ak[7];
 #pragma unroll
-        for (int a = 0; a < kMaxLumiFlav; ++a) {
-            P1[a] = a < F ? patch(c1 + a * 16, X1, Q) : 0.0;
-            P2[a] = a < F ? patch(c2 + a * 16, X2, Q) : 0.0;
-        }
-        double Wq[4], Wx1[4], Wx2[4];
-        stencil_weights(g.mq + (size_t)Q.cell * 16, Q, Wq);
-        stencil_weights(g.mx + (size_t)X1.cell * 16, X1, Wx1);
-        stencil_weights(g.mx + (size_t)X2.cell * 16, X2, Wx2);
-        int qmask = g.qmask[Q.cell];
-        int r0 = g.qrow[Q.cell] - 1;
-        int k1 = X1.cell - 1, k2 = X2.cell - 1;
-#pragma unroll
-        for (int b = 0; b < kMaxLumiFlav; ++b) {
-            if (b >= F) break;
-            int ab = santi[b];
-            if (ab < 0) continue;
-            double o2 = 0.0, o1 = 0.0;
-#pragma unroll
-            for (int a = 0; a < kMaxLumiFlav; ++a)
-                if (a == ab) {
-                    o2 = P2[a];
-                    o1 = P1[a];
-                }
-            double G1 = scale * o2, G2 = scale * o1;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (!((qmask >> j) & 1)) continue;
-                double *rowp = gval + ((size_t)(r0 + j) * g.nx) * F + b;
-                double g1 = G1 * Wq[j], g2 = G2 * Wq[j];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    int kk = k1 + k;
-                    if (kk >= 0 && kk < g.nx) atomicAdd(rowp + (size_t)kk * F, g1 * Wx1[k]);
-                    kk = k2 + k;
-                    if (kk >= 0 && kk < g.nx) atomicAdd(rowp + (size_t)kk * F, g2 * Wx2[k]);
-                }
-            }
-        }
+    for (int k = 0; k < 7; ++k) {
+        bk[k] = (lane >> 4) + 2 * k;
+        ak[k] = bk[k] < F ? (int)santi[bk[k]] : -1;
     }
+    double acc[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc[k] = 0.0;
+    int cur = -1;
+    auto flush = [&](int cell) {
+        int qc = cell / g.nxc, xc = cell - qc * g.nxc;
+        int row = g.qrow[qc] - 1 + j, col = xc - 1 + i;
+        bool ok = ((g.qmask[qc] >> j) & 1) && col >= 0 && col < g.nx;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+            if (ok && ak[k] >= 0 && (dbits(acc[k]) << 1))
+                atomicAdd(gval + ((size_t)row * g.nx + col) * F + bk[k], scale * acc[k]);
+            acc[k] = 0.0;
+        }
+    };
+    for (int p = (int)beg; p < end; p += 32) {
+        // one parton per lane: stencil weights and the partner's values
+        int r = p + lane;
+        int kr = -1;
+        if (r < end) {
+            int rec = perm[r];
+            int e = rec >> 1, side = rec & 1;
+            kr = key[rec];
+            int qc = kr / g.nxc, xc = kr - qc * g.nxc;
+            uint8_t f = fin[rec];
+            Axis Q = axis_from(qc, tq[e], f & 1);
+            Axis X = axis_from(xc, tx[rec], (f >> 1) & 1);
+            double Wq[4], Wx[4];
+            stencil_weights(g.mq + (size_t)qc * 16, Q, Wq);
+            stencil_weights(g.mx + (size_t)xc * 16, X, Wx);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) sW[wid][lane][jj * 4 + ii] = Wq[jj] * Wx[ii];
+            const double *po = P + (size_t)e * 2 * F + (size_t)(1 - side) * F;
+            for (int a = 0; a < F; ++a) sP[wid][lane][a] = po[a];
+        }
+        sK[wid][lane] = kr;
+        __syncwarp();
+        const int nb = min(32, end - p);
+        for (int q = 0; q < nb; ++q) {
+            int kq = sK[wid][q];
+            if (kq != cur) {
+                if (cur >= 0) flush(cur);
+                cur = kq;
+            }
+            double wv = sW[wid][q][s];
+#pragma unroll
+            for (int k = 0; k < 7; ++k)
+                if (ak[k] >= 0) acc[k] = fma(wv, sP[wid][q][ak[k]], acc[k]);
+        }
+        __syncwarp();
+    }
+    if (cur >= 0) flush(cur);
 }
 
 int lumi_common(pdfgpu_grid *g, int32_t member, const double *ln_tau, const double *y,
@@ -253,9 +404,60 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     if (rc) return rc;
     if (!grad_values) return fail(PDF_E_ARG, "null grad_values");
     if (n == 0) return PDF_OK;
-    int grid = wave_grid(g, (const void *)k_lumi_bwd, kBlock, 0, n);
-    k_lumi_bwd<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2,
-                                                          ln_x1, ln_s, n, dL / (double)n, grad_values);
-    PDF_CUDA(cudaGetLastError());
+    cudaStream_t st = (cudaStream_t)stream;
+    const int F = g->d.nflav;
+    const int nbins = g->d.nqc * g->d.nxc;
+    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 23);
+    // scratch layout per chunk of m events
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t bP = al((size_t)chunk * 2 * F * sizeof(double));
+    const size_t btq = al((size_t)chunk * sizeof(double));
+    const size_t btx = al((size_t)chunk * 2 * sizeof(double));
+    const size_t bkey = al((size_t)chunk * 2 * sizeof(int));
+    const size_t bfin = al((size_t)chunk * 2);
+    const size_t bperm = bkey;
+    const size_t bbins = al((size_t)(nbins + 1) * sizeof(int));
+    const size_t need = bP + btq + btx + bkey + bfin + bperm + 3 * bbins;
+    if (g->lumi_scratch_bytes < need) {
+        if (g->lumi_scratch) cudaFree(g->lumi_scratch);
+        g->lumi_scratch = nullptr;
+        g->lumi_scratch_bytes = 0;
+        if (cudaMalloc(&g->lumi_scratch, need) != cudaSuccess)
+            return fail(PDF_E_NOMEM, "luminosity adjoint scratch allocation failed");
+        g->lumi_scratch_bytes = need;
+    }
+    char *base = (char *)g->lumi_scratch;
+    double *P = (double *)base;
+    double *tq = (double *)(base += bP);
+    double *tx = (double *)(base += btq);
+    int *key = (int *)(base += btx);
+    uint8_t *fin = (uint8_t *)(base += bkey);
+    int *perm = (int *)(base += bfin);
+    int *hist = (int *)(base += bperm);
+    int *offs = (int *)(base += bbins);
+    int *cursor = (int *)(base += bbins);
+    const double scale = dL / (double)n;
+    size_t hsmem = nbins <= kMaxSmemBins ? (size_t)nbins * sizeof(int) : 0;
+    if (hsmem > 48 * 1024)
+        PDF_CUDA(cudaFuncSetAttribute((const void *)k_lumi_rec, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)hsmem));
+    for (int64_t e0 = 0; e0 < n; e0 += chunk) {
+        const int m = (int)std::min(chunk, n - e0);
+        PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
+        int grid = wave_grid(g, (const void *)k_lumi_rec, kBlock, hsmem, m);
+        k_lumi_rec<<<grid, kBlock, hsmem, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, e0, m,
+                                                key, tx, tq, fin, P, hist, nbins);
+        PDF_CUDA(cudaGetLastError());
+        k_scan<<<1, 1024, 0, st>>>(hist, nbins, offs, cursor);
+        PDF_CUDA(cudaGetLastError());
+        int gs = wave_grid(g, (const void *)k_scatter, kBlock, 0, 2 * (int64_t)m);
+        k_scatter<<<gs, kBlock, 0, st>>>(key, 2 * m, cursor, perm);
+        PDF_CUDA(cudaGetLastError());
+        int64_t warps = (2 * (int64_t)m + kSegment - 1) / kSegment;
+        int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
+        k_lumi_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin, P,
+                                                        scale, grad_values);
+        PDF_CUDA(cudaGetLastError());
+    }
     return PDF_OK;
 }

@@ -23,6 +23,9 @@ struct pdfgpu_grid {
     // scratch for the luminosity reduction (block partial sums)
     double *partials = nullptr;
     int partials_cap = 0;
+    // scratch of the luminosity adjoint (event records, cell-sorted order)
+    void *lumi_scratch = nullptr;
+    size_t lumi_scratch_bytes = 0;
     // staging for the host-buffer entry point
     std::mutex host_mu;
     cudaStream_t hs[3] = {nullptr, nullptr, nullptr};

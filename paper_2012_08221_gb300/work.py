@@ -65,10 +65,12 @@ LUMI_EVENT_BYTES = 8 + 8 + 1 + 16      # ln tau, y, flags in; lum, alpha_s out
 
 
 def lumi_bwd_event_flops(n_flav: int) -> int:
-    """Recompute 2 F patches and the coordinates, stencil weights of 3 axes
-    (3 x 12 FMA), then per flavour and parton 2 multiplies for the scaled
-    partner value and 4 + 16 multiplies for the 16 cell contributions."""
-    return 4 + 3 * AXIS_FLOPS + 2 * PATCH_FLOPS * n_flav + 3 * 24 + 2 * n_flav * (1 + 4 + 16)
+    """Adjoint of one event, as the kernels organise it: recompute the
+    kinematics, 3 axes and the 2 F patch values (the partner factors), then
+    per parton the stencil weights of its two axes (2 x 12 FMA), their 16
+    products, and 16 F FMAs into the cell's accumulators."""
+    per_parton = 2 * 12 * 2 + 16 + 16 * n_flav * 2
+    return 4 + 3 * AXIS_FLOPS + 2 * PATCH_FLOPS * n_flav + 2 * per_parton
 
 
 LUMI_BWD_EVENT_BYTES = 8 + 8 + 1
