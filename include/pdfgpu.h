@@ -214,19 +214,29 @@ int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_desc, pdfgpu
  *   *L = (1/n) sum_e lum[e], summed in a fixed order (deterministic).
  * Inputs DEVICE [n]: ln_tau, y, flags (uint8); ln_mu2, ln_x1 may be NULL when
  * no flag uses them.  Outputs DEVICE: lum [n] or NULL, alphas [n] or NULL
- * (NULL also when the grid has no alpha_s), L one double.  Uses library-owned
+ * (NULL also when the grid has no alpha_s), L one double, and save_p
+ * [n][2][n_flav] or NULL: the two partons' x*f values that have a partner
+ * flavour, kept for pdf_lumi_backward.  An event with ln x > 0 or a
+ * non-finite input gives NaN and sets PDF_S_DOMAIN.  Uses library-owned
  * scratch of the grid handle for the block partial sums: calls on the same
- * grid must not overlap in time. */
+ * grid must not overlap in time.  Luminosity supports at most 16 flavours. */
 int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double *y,
              const uint8_t *flags, const double *ln_mu2, const double *ln_x1, double ln_s,
-             int64_t n, double *lum, double *alphas, double *L, pdfgpu_stream_t stream);
+             int64_t n, double *lum, double *alphas, double *L, double *save_p,
+             pdfgpu_stream_t stream);
 
 /* dL/dvalues of `member` for L of pdf_lumi, times the HOST scalar dL:
- * grad_values DEVICE [n_rows][n_x][n_flav], ACCUMULATED (+=). */
+ * grad_values DEVICE [n_rows][n_x][n_flav], ACCUMULATED (+=) with FP64
+ * atomics (summation order not fixed).  saved_p: the save_p array of the
+ * forward call on the same events and values (DEVICE, read only), or NULL to
+ * recompute those values.  Events with a domain error add nothing.  Uses
+ * library-owned scratch of the grid handle (allocated on first use, about
+ * 0.3 KB per event for up to 8.4e6 events per chunk, or 40 B per event when
+ * saved_p is given): calls on the same grid must not overlap in time. */
 int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double *y,
                       const uint8_t *flags, const double *ln_mu2, const double *ln_x1,
-                      double ln_s, int64_t n, double dL, double *grad_values,
-                      pdfgpu_stream_t stream);
+                      double ln_s, int64_t n, double dL, const double *saved_p,
+                      double *grad_values, pdfgpu_stream_t stream);
 
 /* Read and clear the grid's status word (PDF_S_* bits).  Synchronises
  * `stream` first. */

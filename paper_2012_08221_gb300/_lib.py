@@ -61,9 +61,9 @@ SIGNATURES = {
     "pdf_batch_free": [c_batch],
     "pdf_batch_run_noalloc": [C.POINTER(BatchDesc), C.c_int32, _VP],
     "pdf_lumi": [c_grid, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_double, C.c_int64,
-                 _VP, _VP, _VP, _VP],
+                 _VP, _VP, _VP, _VP, _VP],
     "pdf_lumi_backward": [c_grid, C.c_int32, _VP, _VP, _VP, _VP, _VP, C.c_double, C.c_int64,
-                          C.c_double, _VP, _VP],
+                          C.c_double, _VP, _VP, _VP],
     "pdf_get_status": [c_grid, _VP, C.POINTER(C.c_uint32)],
     "pdf_probe_fp64_peak": [_D],
     "pdf_debug_log": [c_grid, _VP, C.c_int64, _VP, _VP],

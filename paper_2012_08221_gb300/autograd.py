@@ -54,12 +54,15 @@ def xfxQ2_pw(pdf: PDF, values, pid, x, q2, member: int = 0):
 
 class LumiFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, values, pdf: PDF, events, member: int):
+    def forward(ctx, values, pdf: PDF, events, member: int, save: bool):
         from .lumi import luminosity
         pdf.bind_values(values)
-        L, lum, a_s = luminosity(pdf, events, member, want_lum=False, want_alphas=False)
+        saved = None
+        if save:
+            saved = torch.empty((events.n, 2, pdf.n_flav), dtype=torch.float64, device=pdf.device)
+        L, lum, a_s = luminosity(pdf, events, member, want_lum=False, want_alphas=False, save_p=saved)
         ctx.save_for_backward(values)
-        ctx.pdf, ctx.events, ctx.member = pdf, events, member
+        ctx.pdf, ctx.events, ctx.member, ctx.saved = pdf, events, member, saved
         return L
 
     @staticmethod
@@ -70,10 +73,13 @@ class LumiFn(torch.autograd.Function):
         pdf.bind_values(values)
         gvals = torch.zeros_like(values)
         gslice = gvals[ctx.member] if values.dim() == 4 else gvals
-        luminosity_backward(pdf, ctx.events, float(gL.item()), gslice, ctx.member)
-        return gvals, None, None, None
+        luminosity_backward(pdf, ctx.events, float(gL.item()), gslice, ctx.member, saved_p=ctx.saved)
+        ctx.saved = None
+        return gvals, None, None, None, None
 
 
-def lumi(pdf: PDF, values, events, member: int = 0):
-    """Differentiable luminosity L(values) of the event sample."""
-    return LumiFn.apply(values, pdf, events, member)
+def lumi(pdf: PDF, values, events, member: int = 0, save: bool = True):
+    """Differentiable luminosity L(values) of the event sample.  ``save``
+    keeps the partner factors of the forward pass (16 F bytes per event) so
+    that the backward pass does not recompute them."""
+    return LumiFn.apply(values, pdf, events, member, save)

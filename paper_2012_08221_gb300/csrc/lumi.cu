@@ -48,6 +48,7 @@ __device__ __forceinline__ Event event(int64_t e, const double *ln_tau, const do
     return E;
 }
 
+template <bool SAVE>
 __global__ void __launch_bounds__(kBlock) k_lumi(GridDev g, Cols anti, int member,
                                                  const double *__restrict__ ln_tau,
                                                  const double *__restrict__ y,
@@ -55,7 +56,8 @@ __global__ void __launch_bounds__(kBlock) k_lumi(GridDev g, Cols anti, int membe
                                                  const double *__restrict__ ln_mu2,
                                                  const double *__restrict__ ln_x1, double ln_s,
                                                  int64_t n, double *__restrict__ lum,
-                                                 double *__restrict__ as, double *__restrict__ partials)
+                                                 double *__restrict__ as, double *__restrict__ partials,
+                                                 double *__restrict__ save_p)
 {
     __shared__ signed char santi[PDF_MAX_PIDS];
     __shared__ double red[kBlock / 32];
@@ -83,6 +85,12 @@ __global__ void __launch_bounds__(kBlock) k_lumi(GridDev g, Cols anti, int membe
             double p1 = patch(c1 + a * 16, X1, Q);
             double p2 = patch(c2 + b * 16, X2, Q);
             s = fma(p1, p2, s);
+            if (SAVE) {
+                // the partner factors the adjoint needs: [event][parton][flavour]
+                double *pe = save_p + (size_t)e * 2 * g.nflav;
+                pe[a] = p1;
+                pe[g.nflav + b] = p2;
+            }
         }
         if (E.bad) s = qnan();
         if (lum) lum[e] = s;
@@ -141,6 +149,7 @@ constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;        // partons per warp
 constexpr int kMaxSmemBins = 12 * 1024;
 
+template <bool PATCHES>
 __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
                                                      const double *__restrict__ ln_tau,
                                                      const double *__restrict__ y,
@@ -173,11 +182,13 @@ __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
         Axis X2 = axis_u(g, E.u2);
         const double *c1 = cm + ((size_t)Q.cell * g.nxc + X1.cell) * cell_stride;
         const double *c2 = cm + ((size_t)Q.cell * g.nxc + X2.cell) * cell_stride;
-        double *p1 = P + (size_t)i * 2 * F;
-        double *p2 = p1 + F;
-        for (int a = 0; a < F; ++a) {
-            p1[a] = patch(c1 + a * 16, X1, Q);
-            p2[a] = patch(c2 + a * 16, X2, Q);
+        if (PATCHES) {
+            double *p1 = P + (size_t)i * 2 * F;
+            double *p2 = p1 + F;
+            for (int a = 0; a < F; ++a) {
+                p1[a] = patch(c1 + a * 16, X1, Q);
+                p2[a] = patch(c2 + a * 16, X2, Q);
+            }
         }
         int k1 = Q.cell * g.nxc + X1.cell, k2 = Q.cell * g.nxc + X2.cell;
         key[2 * i] = k1;
@@ -364,7 +375,8 @@ int lumi_common(pdfgpu_grid *g, int32_t member, const double *ln_tau, const doub
 
 extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double *y,
                         const uint8_t *flags, const double *ln_mu2, const double *ln_x1, double ln_s,
-                        int64_t n, double *lum, double *alphas, double *L, pdfgpu_stream_t stream)
+                        int64_t n, double *lum, double *alphas, double *L, double *save_p,
+                        pdfgpu_stream_t stream)
 {
     clear_error();
     Cols anti;
@@ -377,7 +389,8 @@ extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, c
         return PDF_OK;
     }
     if (alphas && !g->has_alphas) alphas = nullptr;
-    int grid = wave_grid(g, (const void *)k_lumi, kBlock, 0, n);
+    const void *kern = save_p ? (const void *)k_lumi<true> : (const void *)k_lumi<false>;
+    int grid = wave_grid(g, kern, kBlock, 0, n);
     if (g->partials_cap < grid) {
         if (g->partials) cudaFree(g->partials);
         g->partials = nullptr;
@@ -385,8 +398,12 @@ extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, c
         PDF_CUDA(cudaMalloc(&g->partials, (size_t)grid * sizeof(double)));
         g->partials_cap = grid;
     }
-    k_lumi<<<grid, kBlock, 0, s>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, n, lum,
-                                   alphas, g->partials);
+    if (save_p)
+        k_lumi<true><<<grid, kBlock, 0, s>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, n, lum,
+                                             alphas, g->partials, save_p);
+    else
+        k_lumi<false><<<grid, kBlock, 0, s>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, n,
+                                              lum, alphas, g->partials, nullptr);
     PDF_CUDA(cudaGetLastError());
     k_lumi_final<<<1, 256, 0, s>>>(g->partials, grid, 1.0 / (double)n, L);
     PDF_CUDA(cudaGetLastError());
@@ -395,8 +412,8 @@ extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, c
 
 extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double *y,
                                  const uint8_t *flags, const double *ln_mu2, const double *ln_x1,
-                                 double ln_s, int64_t n, double dL, double *grad_values,
-                                 pdfgpu_stream_t stream)
+                                 double ln_s, int64_t n, double dL, const double *saved_p,
+                                 double *grad_values, pdfgpu_stream_t stream)
 {
     clear_error();
     Cols anti;
@@ -410,7 +427,7 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 23);
     // scratch layout per chunk of m events
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t bP = al((size_t)chunk * 2 * F * sizeof(double));
+    const size_t bP = saved_p ? 0 : al((size_t)chunk * 2 * F * sizeof(double));
     const size_t btq = al((size_t)chunk * sizeof(double));
     const size_t btx = al((size_t)chunk * 2 * sizeof(double));
     const size_t bkey = al((size_t)chunk * 2 * sizeof(int));
@@ -427,7 +444,7 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
         g->lumi_scratch_bytes = need;
     }
     char *base = (char *)g->lumi_scratch;
-    double *P = (double *)base;
+    double *P = saved_p ? nullptr : (double *)base;
     double *tq = (double *)(base += bP);
     double *tx = (double *)(base += btq);
     int *key = (int *)(base += btx);
@@ -438,15 +455,20 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     int *cursor = (int *)(base += bbins);
     const double scale = dL / (double)n;
     size_t hsmem = nbins <= kMaxSmemBins ? (size_t)nbins * sizeof(int) : 0;
+    const void *krec = saved_p ? (const void *)k_lumi_rec<false> : (const void *)k_lumi_rec<true>;
     if (hsmem > 48 * 1024)
-        PDF_CUDA(cudaFuncSetAttribute((const void *)k_lumi_rec, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)hsmem));
+        PDF_CUDA(cudaFuncSetAttribute(krec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
     for (int64_t e0 = 0; e0 < n; e0 += chunk) {
         const int m = (int)std::min(chunk, n - e0);
         PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
-        int grid = wave_grid(g, (const void *)k_lumi_rec, kBlock, hsmem, m);
-        k_lumi_rec<<<grid, kBlock, hsmem, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, e0, m,
-                                                key, tx, tq, fin, P, hist, nbins);
+        int grid = wave_grid(g, krec, kBlock, hsmem, m);
+        const double *Pc = saved_p ? saved_p + (size_t)e0 * 2 * F : P;
+        if (saved_p)
+            k_lumi_rec<false><<<grid, kBlock, hsmem, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
+                                                           e0, m, key, tx, tq, fin, nullptr, hist, nbins);
+        else
+            k_lumi_rec<true><<<grid, kBlock, hsmem, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
+                                                          e0, m, key, tx, tq, fin, P, hist, nbins);
         PDF_CUDA(cudaGetLastError());
         k_scan<<<1, 1024, 0, st>>>(hist, nbins, offs, cursor);
         PDF_CUDA(cudaGetLastError());
@@ -455,7 +477,7 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
         PDF_CUDA(cudaGetLastError());
         int64_t warps = (2 * (int64_t)m + kSegment - 1) / kSegment;
         int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
-        k_lumi_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin, P,
+        k_lumi_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin, Pc,
                                                         scale, grad_values);
         PDF_CUDA(cudaGetLastError());
     }

@@ -38,8 +38,11 @@ class DeviceEvents:
                    d(ev.ln_mu2, torch.float64), d(ev.ln_x1, torch.float64), float(ev.ln_s))
 
 
-def luminosity(pdf: PDF, ev: DeviceEvents, member=0, want_lum=True, want_alphas=True, out=None):
-    """Returns (L as a 0-d device tensor, lum[n] or None, alpha_s[n] or None)."""
+def luminosity(pdf: PDF, ev: DeviceEvents, member=0, want_lum=True, want_alphas=True, out=None,
+               save_p=None):
+    """Returns (L as a 0-d device tensor, lum[n] or None, alpha_s[n] or None).
+    ``save_p``: optional float64 device tensor [n][2][n_flav] that receives the
+    partner factors for ``luminosity_backward``."""
     dev = pdf.device
     n = ev.n
     lum = torch.empty(n, dtype=torch.float64, device=dev) if want_lum else None
@@ -47,13 +50,16 @@ def luminosity(pdf: PDF, ev: DeviceEvents, member=0, want_lum=True, want_alphas=
     L = out if out is not None else torch.empty((), dtype=torch.float64, device=dev)
     check("pdf_lumi", lib().pdf_lumi(pdf.handle, int(member), _ptr(ev.ln_tau), _ptr(ev.y),
                                      _ptr(ev.flags), _ptr(ev.ln_mu2), _ptr(ev.ln_x1), ev.ln_s, n,
-                                     _ptr(lum), _ptr(a_s), _ptr(L), _stream(dev)))
+                                     _ptr(lum), _ptr(a_s), _ptr(L), _ptr(save_p), _stream(dev)))
     return L, lum, a_s
 
 
-def luminosity_backward(pdf: PDF, ev: DeviceEvents, dL: float, grad_values: torch.Tensor, member=0):
-    """Accumulate dL/dvalues * dL into ``grad_values`` ([rows][n_x][n_flav])."""
+def luminosity_backward(pdf: PDF, ev: DeviceEvents, dL: float, grad_values: torch.Tensor, member=0,
+                        saved_p=None):
+    """Accumulate dL/dvalues * dL into ``grad_values`` ([rows][n_x][n_flav]);
+    ``saved_p`` from the forward call skips recomputing the partner factors."""
     check("pdf_lumi_backward", lib().pdf_lumi_backward(
         pdf.handle, int(member), _ptr(ev.ln_tau), _ptr(ev.y), _ptr(ev.flags), _ptr(ev.ln_mu2),
-        _ptr(ev.ln_x1), ev.ln_s, ev.n, C.c_double(dL), _ptr(grad_values), _stream(pdf.device)))
+        _ptr(ev.ln_x1), ev.ln_s, ev.n, C.c_double(dL), _ptr(saved_p), _ptr(grad_values),
+        _stream(pdf.device)))
     return grad_values

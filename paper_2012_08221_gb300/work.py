@@ -64,13 +64,15 @@ def lumi_event_flops(n_flav: int) -> int:
 LUMI_EVENT_BYTES = 8 + 8 + 1 + 16      # ln tau, y, flags in; lum, alpha_s out
 
 
-def lumi_bwd_event_flops(n_flav: int) -> int:
-    """Adjoint of one event, as the kernels organise it: recompute the
-    kinematics, 3 axes and the 2 F patch values (the partner factors), then
-    per parton the stencil weights of its two axes (2 x 12 FMA), their 16
-    products, and 16 F FMAs into the cell's accumulators."""
+def lumi_bwd_event_flops(n_flav: int, saved: bool = False) -> int:
+    """Adjoint of one event, as the kernels organise it: the kinematics and
+    3 axes, the 2 F patch values (the partner factors; skipped when the
+    forward pass saved them), then per parton the stencil weights of its two
+    axes (2 x 12 FMA), their 16 products, and 16 F FMAs into the cell's
+    accumulators."""
     per_parton = 2 * 12 * 2 + 16 + 16 * n_flav * 2
-    return 4 + 3 * AXIS_FLOPS + 2 * PATCH_FLOPS * n_flav + 2 * per_parton
+    patches = 0 if saved else 2 * PATCH_FLOPS * n_flav
+    return 4 + 3 * AXIS_FLOPS + patches + 2 * per_parton
 
 
 LUMI_BWD_EVENT_BYTES = 8 + 8 + 1

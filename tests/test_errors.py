@@ -76,7 +76,7 @@ def test_null_arguments(L):
     assert L.pdf_free_grid(None) == -1
     assert L.pdf_batch_run(None, None) == -1
     assert L.pdf_batch_free(None) == -1
-    assert L.pdf_lumi(None, 0, None, None, None, None, None, 0.0, 0, None, None, None, None) == -1
+    assert L.pdf_lumi(None, 0, None, None, None, None, None, 0.0, 0, None, None, None, None, None) == -1
 
 
 def test_error_message_is_per_call(L):

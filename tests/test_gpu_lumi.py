@@ -87,6 +87,23 @@ def test_luminosity_gradient_against_oracle(lhc):
     assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
 
 
+def test_saved_partner_factors_give_the_same_gradient(lhc):
+    """The backward pass from the forward's saved partner factors equals the
+    one that recomputes them (up to the summation order of the atomics)."""
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
+    g, pdf, o = lhc
+    ev = DeviceEvents.from_host(synth.events_lhc(50_003, seed=95))
+    P = torch.empty((ev.n, 2, g.n_flav), dtype=torch.float64, device="cuda")
+    L1, lum1, _ = luminosity(pdf, ev, save_p=P)
+    L0, lum0, _ = luminosity(pdf, ev)
+    assert torch.equal(lum0, lum1) and torch.equal(L0, L1)
+    ga = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    gb = torch.zeros_like(ga)
+    luminosity_backward(pdf, ev, 2.0, ga)
+    luminosity_backward(pdf, ev, 2.0, gb, saved_p=P)
+    assert torch.allclose(ga, gb, rtol=1e-12, atol=1e-15 * float(ga.abs().max()))
+
+
 def test_luminosity_autograd(lhc):
     from paper_2012_08221_gb300.autograd import lumi
     from paper_2012_08221_gb300.lumi import DeviceEvents
