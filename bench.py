@@ -127,6 +127,59 @@ def cpu_oracle_rate(points, cores, budget_s=10.0, chunk=200_000, max_points=None
     return done * g.n_flav / dt, done, dt
 
 
+def _timed_rate(fn, units):
+    t0 = time.perf_counter()
+    fn()
+    return units / (time.perf_counter() - t0)
+
+
+def forms_cpu_baselines(cores):
+    """The oracle on bounded samples of each additional form (a few seconds
+    each): rates in the unit of the form's GPU value."""
+    import numpy as np
+
+    from oracle.oracle import OracleGrid, set_threads
+    from paper_2012_08221_gb300 import synth
+    set_threads(cores)
+    out = {}
+    gs = synth.grid_small(seed=1003, pids=synth.PIDS_13)
+    o3 = OracleGrid.from_synth(gs)
+    pid, x, q2, w = synth.queries_pointwise(20_000)
+
+    def fb():
+        o3.xfxq2_pw(pid, x, q2)
+        o3.grad_pw(pid, x, q2)
+        o3.dgrid_pw(pid, x, q2, w)
+    out["fwd_bwd"] = {"value": _timed_rate(fb, x.size), "unit": "evals/s (fwd+bwd)", "cores": cores,
+                      "kind": "oracle", "sample": "20000 points of the pointwise workload "
+                      "(grid gradient summed serially)"}
+    grids = [synth.grid_set_a(), synth.grid_set_b(), synth.grid_set_c()]
+    ogs = [OracleGrid.from_synth(gg) for gg in grids]
+    reqs = synth.batches_uneven(grids, n_batches=400)
+    done, evals, t0 = 0, 0, time.perf_counter()
+    for b in reqs:
+        m = min(b.x.size, 20_000)
+        ogs[b.set_index].xfxq2_batch(b.pids, b.x[:m], b.q2[:m], member=b.member)
+        evals += m * b.pids.size
+        done += 1
+        if time.perf_counter() - t0 > 5.0:
+            break
+    out["batched"] = {"value": evals / (time.perf_counter() - t0), "unit": "evals/s", "cores": cores,
+                      "kind": "oracle", "sample": f"first <= 20000 points of the first {done} requests"}
+    g5 = synth.grid_nnpdf(seeds=(1005, 1006, 1007))
+    o5 = OracleGrid.from_synth(g5)
+    ev = synth.events_lhc(40_000)
+    r_f = _timed_rate(lambda: o5.lumi(ev), ev.ln_tau.size * 2 * g5.n_flav)
+    sub = synth.Events(ev.ln_tau[:2000], ev.y[:2000], ev.flags[:2000], ev.ln_mu2[:2000], ev.ln_x1[:2000],
+                       ev.ln_s)
+    r_b = _timed_rate(lambda: (o5.lumi(sub), o5.lumi_dgrid(sub)), 2000 * 2 * g5.n_flav)
+    out["lumi"] = {"fwd": {"value": r_f, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                           "sample": "40000 events"},
+                   "fwd_bwd": {"value": r_b, "unit": "evals/s (fwd+bwd)", "cores": cores, "kind": "oracle",
+                               "sample": "2000 events (grid gradient summed serially)"}}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -439,6 +492,14 @@ def main():
         rate, done, dt = cpu_oracle_rate((x, q2), cores, budget_s=10.0)
         cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
                "sample": f"first {done} points of the 1e7-point workload x 13 flavours ({dt:.1f} s)"}
+        if forms:
+            fcpu = forms_cpu_baselines(cores)
+            for k in forms:
+                if k in fcpu and k != "lumi":
+                    forms[k]["cpu_baseline"] = fcpu[k]
+            if "lumi" in forms:
+                forms["lumi"]["fwd"]["cpu_baseline"] = fcpu["lumi"]["fwd"]
+                forms["lumi"]["fwd_bwd"]["cpu_baseline"] = fcpu["lumi"]["fwd_bwd"]
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,

@@ -31,7 +31,8 @@
  *     documented otherwise.
  *   - Per-element domain errors do not fail a call: x <= 0, x > 1, Q^2 <= 0,
  *     Q^2 infinite or any NaN input gives NaN for every requested flavour and
- *     sets PDF_S_DOMAIN in the grid's status word.  A pid absent from the grid
+ *     sets PDF_S_DOMAIN in the grid's status word (PDF_S_RANGE for points
+ *     outside the knot range of a grid loaded with PDF_EXTRAP_ERROR).  A pid absent from the grid
  *     gives 0 (pid 21 and pid 0 both mean the gluon).  n == 0 is a no-op.
  *   - The output is x*f, not f (the paper's luminosity divides by x1*x2).
  */
@@ -60,7 +61,34 @@ enum {
 
 /* Status bits accumulated by kernels in the grid's device status word. */
 enum {
-    PDF_S_DOMAIN = 1u     /* some input x / Q^2 was out of the domain (output NaN)   */
+    PDF_S_DOMAIN = 1u,    /* some input x / Q^2 was out of the domain (output NaN)   */
+    PDF_S_RANGE = 2u      /* some input was outside the knot range of a grid loaded
+                             with PDF_EXTRAP_ERROR (output NaN)                      */
+};
+
+/* Interpolation kind of a grid (pdfgpu_grid_desc.interp).  The paper keeps
+ * LHAPDF's interpolators without printing them; the default is the
+ * log-bicubic one described at the top of this file.
+ *   LOGBICUBIC               Hermite cubics with finite-difference slopes
+ *   LOGBILINEAR              straight lines between the interval's two knots
+ *                            on both axes (ln x, ln Q^2)
+ *   LOGBICUBIC_SMALL_LINEAR  log-bicubic, but straight lines along any axis
+ *                            or Q subgrid that has fewer than 4 knots       */
+enum {
+    PDF_INTERP_LOGBICUBIC = 0,
+    PDF_INTERP_LOGBILINEAR = 1,
+    PDF_INTERP_LOGBICUBIC_SMALL_LINEAR = 2
+};
+
+/* Extrapolation outside the knot range (pdfgpu_grid_desc.extrap):
+ *   LINEAR  continue linearly in ln x / ln Q^2 from the two edge knots
+ *   FREEZE  the value at the nearest edge of the grid (zero derivative
+ *           across the edge)
+ *   ERROR   NaN and the PDF_S_RANGE status bit                            */
+enum {
+    PDF_EXTRAP_LINEAR = 0,
+    PDF_EXTRAP_FREEZE = 1,
+    PDF_EXTRAP_ERROR = 2
 };
 
 #define PDF_MAX_PIDS 64   /* flavours per matrix-form call                  */
@@ -75,7 +103,11 @@ enum {
  *   pids    [n_flav]       PDG ids, distinct; 0 or 21 is the gluon
  *   values  [n_members][sum n_q][n_x][n_flav]  x*f at the knots (row-major),
  *                          or NULL: bind later with pdf_bind_values
- *   alphas  [sum n_q]      alpha_s at the Q knots, or NULL (no alpha_s)      */
+ *   alphas  [sum n_q]      alpha_s at the Q knots, or NULL (no alpha_s)
+ *   interp                 PDF_INTERP_* (0: log-bicubic); alpha_s follows the
+ *                          same kind along ln Q^2
+ *   extrap                 PDF_EXTRAP_* (0: linear continuation), also for
+ *                          alpha_s                                           */
 typedef struct {
     int32_t n_x;
     const double *x_knots;
@@ -87,6 +119,8 @@ typedef struct {
     int32_t n_members;
     const double *values;
     const double *alphas;
+    int32_t interp;
+    int32_t extrap;
 } pdfgpu_grid_desc;
 
 /* Validate a grid description, upload it and build the interpolation tables

@@ -97,18 +97,34 @@ def linear_1d(z0, z1, g0, g1, v):
     return g0 + (v - z0) * slope, slope
 
 
-class ExactGrid:
-    """values[s][j][k]: subgrid s, local Q row j, x knot k (one flavour)."""
+def line_1d(z, g, v):
+    """Straight line between the two knots of the interval containing v."""
+    k = _interval(z, v)
+    return linear_1d(z[k], z[k + 1], g[k], g[k + 1], v)
 
-    def __init__(self, U, W_sub, values_sub):
+
+class ExactGrid:
+    """values[s][j][k]: subgrid s, local Q row j, x knot k (one flavour).
+
+    interp: 0 cubic on both axes, 1 straight lines on both axes, 2 cubic but
+    straight lines on an axis or subgrid with fewer than 4 knots.
+    extrap: 0 linear continuation, 1 frozen at the edge (u, w clamped)."""
+
+    def __init__(self, U, W_sub, values_sub, interp=0, extrap=0):
         self.U = [_fr(v) for v in U]
         self.W = [[_fr(v) for v in Ws] for Ws in W_sub]
         self.V = [[[_fr(v) for v in row] for row in sub] for sub in values_sub]
+        self.interp, self.extrap = interp, extrap
+
+    def _lin(self, n):
+        return self.interp == 1 or (self.interp == 2 and n < 4)
 
     def _row_u(self, s, j, u, column=None):
         row = self.V[s][j]
         if column is not None:
             return row[column], Fr(0)
+        if self._lin(len(self.U)):
+            return line_1d(self.U, row, u)
         return interp_1d(self.U, row, u)
 
     def _w_step(self, u, w, column=None):
@@ -128,13 +144,23 @@ class ExactGrid:
         rows = [self._row_u(s, j, u, column) for j in range(len(W[s]))]
         R = [r[0] for r in rows]
         dR = [r[1] for r in rows]
-        v, dw = interp_1d(W[s], R, w)
-        du, _ = interp_1d(W[s], dR, w)
+        one_d = line_1d if self._lin(len(W[s])) else interp_1d
+        v, dw = one_d(W[s], R, w)
+        du, _ = one_d(W[s], dR, w)
         return v, du, dw
 
     def eval(self, u, w):
         """Exact (value, d/du, d/dw) at log coordinates (u, w)."""
         u, w = _fr(u), _fr(w)
+        U = self.U
+        if self.extrap == 1:
+            lo, hi = self.W[0][0], self.W[-1][-1]
+            cu, cw = min(max(u, U[0]), U[-1]), min(max(w, lo), hi)
+            v, du, dw = self._eval_in(cu, cw)
+            return v, (du if cu == u else Fr(0)), (dw if cw == w else Fr(0))
+        return self._eval_in(u, w)
+
+    def _eval_in(self, u, w):
         U = self.U
         if u < U[0] or u > U[-1]:
             k0 = 0 if u < U[0] else len(U) - 2

@@ -49,6 +49,7 @@ class _Grid(C.Structure):
         ("alphas", C.POINTER(C.c_double)),
         ("U", C.POINTER(C.c_double)), ("W", C.POINTER(C.c_double)),
         ("row0", C.POINTER(C.c_int)), ("rows", C.c_int),
+        ("interp", C.c_int), ("extrap", C.c_int),
     ]
 
 
@@ -127,7 +128,7 @@ class OracleGrid:
     duplicated), pids, values ``[members][rows][n_x][n_flav]`` and alpha_s
     knot values ``[rows]`` (or None)."""
 
-    def __init__(self, x_knots, n_q, q_knots, pids, values, alphas=None):
+    def __init__(self, x_knots, n_q, q_knots, pids, values, alphas=None, interp=0, extrap=0):
         self.x_knots = _f64(x_knots)
         self.n_q = _i32(n_q)
         self.q_knots = _f64(q_knots)
@@ -154,6 +155,9 @@ class OracleGrid:
         g.U = _d(self.U)
         g.W = _d(self.W)
         g.row0 = _i(self.row0)
+        g.interp = int(interp)
+        g.extrap = int(extrap)
+        self.interp, self.extrap = int(interp), int(extrap)
         self._g = g
         rc = lib().orc_init(C.byref(g))
         if rc != 0:
@@ -161,8 +165,9 @@ class OracleGrid:
         assert self.values.shape[1:] == (g.rows, g.n_x, g.n_flav), "values shape"
 
     @classmethod
-    def from_synth(cls, grid):
-        return cls(grid.x_knots, grid.n_q, grid.q_knots, grid.pids, grid.values, grid.alphas)
+    def from_synth(cls, grid, interp=0, extrap=0):
+        return cls(grid.x_knots, grid.n_q, grid.q_knots, grid.pids, grid.values, grid.alphas,
+                   interp, extrap)
 
     @property
     def ptr(self):

@@ -38,6 +38,11 @@
  *   8. Derivatives: d/du and d/dw of the same piecewise polynomial; the
  *      derivative with respect to one grid value is the interpolation of the
  *      indicator grid of that value (the result is linear in the values).
+ *   Variants (grid options): log-bilinear interpolation (straight lines
+ *   between the two interval knots on both axes), or log-bicubic with
+ *   straight lines on any axis or subgrid of fewer than 4 knots; outside the
+ *   grid, the value frozen at the nearest edge (u and w clamped into the
+ *   knot range, zero derivative across the edge), or NaN.
  *
  * Built with -O2 -ffp-contract=off (no fused multiply-add contraction, no
  * fast-math), parallelised over points with OpenMP in the batch drivers only.
@@ -63,6 +68,10 @@ typedef struct {
     double *W;               /* [rows]  ln (Q_r * Q_r)                     */
     int *row0;               /* [n_sub] first row of each subgrid         */
     int rows;
+    int interp;              /* 0 log-bicubic, 1 log-bilinear, 2 log-bicubic
+                                with linear axes that have fewer than 4 knots */
+    int extrap;              /* outside the grid: 0 linear continuation,
+                                1 freeze at the edge, 2 NaN                */
 } orc_grid;
 
 int orc_init(orc_grid *g)
@@ -147,6 +156,14 @@ static double xrow(const acc_t *a, int row, const xsel_t *xs, double *du)
         return val(a, row, xs->column);
     }
     int n = g->n_x, k = interval(g->U, n, xs->u);
+    if (g->interp == 1 || (g->interp == 2 && n < 4)) {
+        /* straight line between the interval's two knots */
+        double g0 = val(a, row, k), g1 = val(a, row, k + 1);
+        double dz = g->U[k + 1] - g->U[k];
+        double t = (xs->u - g->U[k]) / dz;
+        if (du) *du = (g1 - g0) / dz;
+        return (1.0 - t) * g0 + t * g1;
+    }
     double gm = k > 0 ? val(a, row, k - 1) : 0.0;
     double g0 = val(a, row, k), g1 = val(a, row, k + 1);
     double gp = k + 2 < n ? val(a, row, k + 2) : 0.0;
@@ -164,6 +181,11 @@ static double wdir(const acc_t *a, const xsel_t *xs, double w, double *dw, doubl
     const orc_grid *g = a->g;
     const double *W = g->W;
     int last = g->rows - 1;
+    int frozen = 0;
+    if ((w < W[0] || w > W[last]) && g->extrap == 1) {
+        w = w < W[0] ? W[0] : W[last];
+        frozen = 1;
+    }
     if (w < W[0] || w > W[last]) {
         /* step 6 in w: the two edge rows of the lowest or highest subgrid */
         int r0 = w < W[0] ? 0 : last - 1;
@@ -181,6 +203,16 @@ static double wdir(const acc_t *a, const xsel_t *xs, double w, double *dw, doubl
     int n = g->n_q[s], r0 = g->row0[s];
     const double *Ws = W + r0;
     int k = interval(Ws, n, w);
+    if (g->interp == 1 || (g->interp == 2 && n < 4)) {
+        /* straight line between the interval's two rows */
+        double du0, du1;
+        double B0 = xrow(a, r0 + k, xs, &du0), B1 = xrow(a, r0 + k + 1, xs, &du1);
+        double dz = Ws[k + 1] - Ws[k];
+        double t = (w - Ws[k]) / dz;
+        if (dw) *dw = frozen ? 0.0 : (B1 - B0) / dz;
+        if (du) *du = (1.0 - t) * du0 + t * du1;
+        return (1.0 - t) * B0 + t * B1;
+    }
     double R[4] = {0, 0, 0, 0}, D[4] = {0, 0, 0, 0};
     for (int j = -1; j <= 2; ++j) {
         int kk = k + j;
@@ -192,6 +224,7 @@ static double wdir(const acc_t *a, const xsel_t *xs, double w, double *dw, doubl
     double dz = Ws[k + 1] - Ws[k];
     double t = (w - Ws[k]) / dz;
     double value = hermite(t, dz, R[1], R[2], d0, d1, dw);
+    if (frozen && dw) *dw = 0.0;
     if (du) {
         /* the same w-Hermite applied to the u-derivatives of the rows */
         double e0 = fd_deriv(k, n, Ws, D[0], D[1], D[2]);
@@ -207,6 +240,13 @@ static double eval_uw(const acc_t *a, double u, double w, double *du, double *dw
     const orc_grid *g = a->g;
     const double *U = g->U;
     int n = g->n_x;
+    if ((u < U[0] || u > U[n - 1]) && g->extrap == 1) {
+        /* frozen at the edge: clamp u, no derivative across the edge */
+        xsel_t xs = {-1, u < U[0] ? U[0] : U[n - 1]};
+        double v = wdir(a, &xs, w, dw, du);
+        if (du) *du = 0.0;
+        return v;
+    }
     if (u < U[0] || u > U[n - 1]) {
         /* step 6 in u: A_k = w-interpolation of the two edge columns */
         int k0 = u < U[0] ? 0 : n - 2;
@@ -257,6 +297,11 @@ double orc_xfxq2_uw(const orc_grid *g, int member, int pid, double u, double w,
         if (dw) *dw = NAN;
         return NAN;
     }
+    if (g->extrap == 2 && (u < g->U[0] || u > g->U[g->n_x - 1] || w < g->W[0] || w > g->W[g->rows - 1])) {
+        if (du) *du = NAN;
+        if (dw) *dw = NAN;
+        return NAN;
+    }
     int col = pid_column(g, pid);
     if (col < 0) return 0.0;
     acc_t a = member_acc(g, member, col);
@@ -287,6 +332,7 @@ double orc_xfxq2_grad(const orc_grid *g, int member, int pid, double x, double q
 double orc_alphas_w(const orc_grid *g, double w)
 {
     if (!g->alphas || !(w > -INFINITY && w < INFINITY)) return NAN;
+    if (g->extrap == 2 && (w < g->W[0] || w > g->W[g->rows - 1])) return NAN;
     acc_t a;
     a.g = g;
     a.base = g->alphas;

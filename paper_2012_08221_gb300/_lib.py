@@ -24,6 +24,9 @@ _VP = C.c_void_p
 
 PDF_MAX_PIDS = 64
 PDF_S_DOMAIN = 1
+PDF_S_RANGE = 2
+INTERP = {"logbicubic": 0, "logbilinear": 1, "logbicubic_small_linear": 2}
+EXTRAP = {"linear": 0, "freeze": 1, "error": 2}
 ERRORS = {-1: "PDF_E_ARG", -2: "PDF_E_DESC", -3: "PDF_E_CUDA", -4: "PDF_E_UNBOUND",
           -5: "PDF_E_NOMEM", -6: "PDF_E_RANGE"}
 
@@ -32,7 +35,8 @@ class GridDesc(C.Structure):
     _fields_ = [("n_x", C.c_int32), ("x_knots", _D),
                 ("n_sub", C.c_int32), ("n_q", _I), ("q_knots", _D),
                 ("n_flav", C.c_int32), ("pids", _I),
-                ("n_members", C.c_int32), ("values", _D), ("alphas", _D)]
+                ("n_members", C.c_int32), ("values", _D), ("alphas", _D),
+                ("interp", C.c_int32), ("extrap", C.c_int32)]
 
 
 class BatchDesc(C.Structure):

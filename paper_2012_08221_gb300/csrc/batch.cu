@@ -132,6 +132,9 @@ __global__ void k_batch(const GridDev *__restrict__ grids, const BatchReq *__res
             double u, w;
             Axis X = axis_x(g, xi, &u);
             Axis Q = axis_q2(g, qi, &w);
+            const bool oor = live && out_of_range(g, X, Q);
+            flag_status(g, oor, PDF_S_RANGE);
+            bad |= oor;
             const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
             double *srow = sout + threadIdx.x * npid;
             for (int a = 0; a < npid; ++a) {

@@ -61,8 +61,17 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
         double u, w;
         Axis X = axis_x(g, xi, &u);
         Axis Q = axis_q2(g, qi, &w);
+        if (out_of_range(g, X, Q)) {
+            if (gx) gx[i] = qnan();
+            if (gq) gq[i] = qnan();
+            continue;
+        }
+        // derivative bases: (0, 1, 2t, 3t^2) inside; outside (0, 1, 1, 1) for
+        // the linear continuation, and no derivative across a frozen edge
         double dx2 = X.in ? 2.0 * X.t : 1.0, dx3 = X.in ? 3.0 * X.t * X.t : 1.0;
         double dq2 = Q.in ? 2.0 * Q.t : 1.0, dq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
+        const bool fzx = !X.in && g.extrap == PDF_EXTRAP_FREEZE;
+        const bool fzq = !Q.in && g.extrap == PDF_EXTRAP_FREEZE;
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
         double Wx[4], Wq[4];
         int qmask = 0, r0 = 0, k0 = 0;
@@ -81,6 +90,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
             double ga = PW ? gout[i] : gout[i * npid + a];
             double dtx, dtq;
             patch_d(cell + col * 16, X, Q, dx2, dx3, dq2, dq3, &dtx, &dtq);
+            if (fzx) dtx = 0.0;
+            if (fzq) dtq = 0.0;
             sx = fma(ga, dtx, sx);
             sq = fma(ga, dtq, sq);
             if (gval) {

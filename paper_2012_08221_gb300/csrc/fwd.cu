@@ -4,6 +4,7 @@
 // PDFFlow Sec. 2.1: the query is a flavour set plus equal-length arrays of x
 // and Q; the answer is one interpolated value per point and flavour.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -50,6 +51,9 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         double u, w;
         Axis X = axis_x(g, xi, &u);
         Axis Q = axis_q2(g, qi, &w);
+        const bool oor = live && out_of_range(g, X, Q);
+        flag_status(g, oor, PDF_S_RANGE);
+        bad |= oor;
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
         double *srow = sout + threadIdx.x * npid;
         for (int a = 0; a < npid; ++a) {
@@ -87,6 +91,9 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
         double u, w;
         Axis X = axis_x(g, xi, &u);
         Axis Q = axis_q2(g, qi, &w);
+        const bool oor = out_of_range(g, X, Q);
+        flag_status(g, oor, PDF_S_RANGE);
+        bad |= oor;
         double v = 0.0;
         if (col >= 0) v = patch(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
         out[i] = bad ? qnan() : v;
@@ -106,6 +113,9 @@ __global__ void __launch_bounds__(kBlock) k_alphas(GridDev g, const double *__re
         if (bad) qi = 10.0;
         double w;
         Axis Q = axis_q2(g, qi, &w);
+        const bool oor = g.extrap == PDF_EXTRAP_ERROR && !Q.in;
+        flag_status(g, oor, PDF_S_RANGE);
+        bad |= oor;
         const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
         double2 a01 = __ldg(A), a23 = __ldg(A + 1);
         double v = fma(Q.b3, a23.y, fma(Q.b2, a23.x, fma(Q.t, a01.y, a01.x)));
@@ -234,7 +244,15 @@ extern "C" int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, 
     if (n == 0) return PDF_OK;
     if (!x || !q2 || !out) return fail(PDF_E_ARG, "null array");
     std::lock_guard<std::mutex> lock(g->host_mu);
-    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 21);
+    // points per chunk: small enough that the pipeline fills quickly (the
+    // device-to-host copy of the outputs is the bound), large enough to fill
+    // the GPU; $PDFGPU_HOST_CHUNK overrides it
+    static const int64_t chunk_pts = [] {
+        const char *e = getenv("PDFGPU_HOST_CHUNK");
+        long long v = e ? atoll(e) : 0;
+        return (int64_t)(v >= 4096 ? v : (1 << 18));
+    }();
+    const int64_t chunk = std::min<int64_t>(n, chunk_pts);
     if (g->stage_pts < chunk || g->stage_pid < n_pid) {
         for (int s = 0; s < 3; ++s)
             for (int k = 0; k < 3; ++k) {

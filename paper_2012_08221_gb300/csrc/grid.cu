@@ -103,9 +103,17 @@ static void make_log_tables(std::vector<LogEntry> &tab, std::vector<double2> &et
 //   dz_k D_{k+1} = q0 g_k     + q1 g_{k+1} + q2 g_{k+2}
 // (one-sided secant at the first/last knot, mean of the secants inside),
 // assembled into M[m][i]: monomial coefficient m of the interval cubic in
-// t = (z - z_k)/dz_k from stencil value i (i <-> knot k-1+i).
-static void cell_matrix(const double *z, int n, int k, double M[16])
+// t = (z - z_k)/dz_k from stencil value i (i <-> knot k-1+i).  With `linear`
+// the interval polynomial is the straight line between its two knots.
+static void cell_matrix(const double *z, int n, int k, double M[16], bool linear)
 {
+    if (linear) {
+        // straight line between the interval's two knots: c0 = g_k, c1 = g_{k+1} - g_k
+        const double m[16] = {0.0, 1.0, 0.0, 0.0, 0.0, -1.0, 1.0, 0.0,
+                              0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        memcpy(M, m, sizeof(m));
+        return;
+    }
     double dz = z[k + 1] - z[k];
     double p0, p1, p2, q0, q1, q2;
     if (k == 0) {
@@ -231,6 +239,10 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     if (D.n_sub < 1 || !D.n_q || !D.q_knots) return fail(PDF_E_DESC, "need at least 1 Q subgrid");
     if (D.n_flav < 1 || D.n_flav > PDF_MAX_FLAV || !D.pids) return fail(PDF_E_DESC, "bad flavour count");
     if (D.n_members < 1) return fail(PDF_E_DESC, "need at least 1 member");
+    if (D.interp < PDF_INTERP_LOGBICUBIC || D.interp > PDF_INTERP_LOGBICUBIC_SMALL_LINEAR)
+        return fail(PDF_E_DESC, "unknown interpolation kind");
+    if (D.extrap < PDF_EXTRAP_LINEAR || D.extrap > PDF_EXTRAP_ERROR)
+        return fail(PDF_E_DESC, "unknown extrapolation mode");
     for (int k = 0; k < D.n_x; ++k) {
         double x = D.x_knots[k];
         if (!(x > 0.0 && x <= 1.0)) return fail(PDF_E_DESC, "x knot outside (0, 1]");
@@ -295,6 +307,8 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
         }
 
     // x cells
+    const bool x_linear = D.interp == PDF_INTERP_LOGBILINEAR ||
+                          (D.interp == PDF_INTERP_LOGBICUBIC_SMALL_LINEAR && nx < 4);
     std::vector<uint64_t> xbits(nxc);
     std::vector<int64_t> ukey(nxc);
     std::vector<double2> xcell(nxc);
@@ -303,7 +317,7 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
         xbits[k] = dbits(D.x_knots[k]);
         ukey[k] = dkey(g->U[k]);
         xcell[k] = make_double2(g->U[k], 1.0 / (g->U[k + 1] - g->U[k]));
-        cell_matrix(g->U.data(), nx, k, &mx[(size_t)k * 16]);
+        cell_matrix(g->U.data(), nx, k, &mx[(size_t)k * 16], x_linear);
     }
     // Q cells, subgrid by subgrid
     std::vector<uint64_t> qbits;
@@ -325,7 +339,9 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
                 wkey.push_back(dkey(Ws[j]));
                 qcell.push_back(make_double2(Ws[j], 1.0 / (Ws[j + 1] - Ws[j])));
                 double M[16];
-                cell_matrix(Ws, n, j, M);
+                const bool q_linear = D.interp == PDF_INTERP_LOGBILINEAR ||
+                                      (D.interp == PDF_INTERP_LOGBICUBIC_SMALL_LINEAR && n < 4);
+                cell_matrix(Ws, n, j, M, q_linear);
                 mq.insert(mq.end(), M, M + 16);
                 qrow.push_back(r0 + j);
                 int mask = 0x6 | (j > 0 ? 0x1 : 0) | (j + 2 <= n - 1 ? 0x8 : 0);
@@ -366,6 +382,7 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     d.uhi = dkey(g->U[nx - 1]);
     d.wlo = dkey(g->W[0]);
     d.whi = dkey(g->W[rows - 1]);
+    d.extrap = D.extrap;
 
     TRY(dev_upload(g, xbits.data(), xbits.size(), &d.xbits));
     TRY(dev_upload(g, ukey.data(), ukey.size(), &d.ukey));

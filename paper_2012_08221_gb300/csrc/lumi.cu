@@ -76,6 +76,9 @@ __global__ void __launch_bounds__(kBlock) k_lumi(GridDev g, Cols anti, int membe
         Axis Q = axis_w(g, E.w);
         Axis X1 = axis_u(g, E.u1);
         Axis X2 = axis_u(g, E.u2);
+        const bool oor = !E.bad && (out_of_range(g, X1, Q) || out_of_range(g, X2, Q));
+        flag_status(g, oor, PDF_S_RANGE);
+        E.bad |= oor;
         const double *c1 = cm + ((size_t)Q.cell * g.nxc + X1.cell) * cell_stride;
         const double *c2 = cm + ((size_t)Q.cell * g.nxc + X2.cell) * cell_stride;
         double s = 0.0;
@@ -180,6 +183,11 @@ __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
         Axis Q = axis_w(g, E.w);
         Axis X1 = axis_u(g, E.u1);
         Axis X2 = axis_u(g, E.u2);
+        if (out_of_range(g, X1, Q) || out_of_range(g, X2, Q)) {
+            key[2 * i] = -1;
+            key[2 * i + 1] = -1;
+            continue;
+        }
         const double *c1 = cm + ((size_t)Q.cell * g.nxc + X1.cell) * cell_stride;
         const double *c2 = cm + ((size_t)Q.cell * g.nxc + X2.cell) * cell_stride;
         if (PATCHES) {
@@ -253,13 +261,16 @@ __global__ void k_scatter(const int *__restrict__ key, int nrec, int *__restrict
     }
 }
 
-// Rebuild an axis from its stored local coordinate (t and range flag).
+// Rebuild an axis from its stored local coordinate (t and range flag).  The
+// stored t is the effective one (0 or 1 when frozen at an edge), for which
+// the outside basis (1, t, t, t) and weights (1 - t, t) are the right ones.
 __device__ __forceinline__ Axis axis_from(int cell, double t, bool in)
 {
     Axis A;
     A.cell = cell;
     A.in = in;
-    make_basis(A, t);
+    A.below = false;
+    make_basis(A, t, PDF_EXTRAP_LINEAR);
     return A;
 }
 

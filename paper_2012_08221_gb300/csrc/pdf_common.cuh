@@ -123,6 +123,7 @@ struct GridDev {
     const int *qmask;        // [nqc] bit i (0..3): stencil row i-1 exists
     const signed char *pidmap;  // [129] column of pid in [-64, 64], -1 absent
     uint32_t *status;
+    int extrap;              // PDF_EXTRAP_*
 };
 
 // Largest cell c in [0, ncell) whose lower key is <= key (0 below the grid).
@@ -143,10 +144,17 @@ struct Axis {
     int cell;
     double t, b2, b3;     // basis (1, t, b2, b3)
     bool in;              // inside the knot range
+    bool below;           // below the first knot
 };
 
-__device__ __forceinline__ void make_basis(Axis &A, double t)
+// Basis of the patch polynomial along one axis.  Inside the knot range
+// (1, t, t^2, t^3).  Outside: linear continuation (1, t, t, t), i.e.
+// P(0) + t (P(1) - P(0)); frozen at the edge, t becomes 0 (below) or 1
+// (above), the edge knot of the edge cell.  The error mode is handled by the
+// caller (the point is flagged, the basis does not matter).
+__device__ __forceinline__ void make_basis(Axis &A, double t, int extrap)
 {
+    if (!A.in && extrap == PDF_EXTRAP_FREEZE) t = A.below ? 0.0 : 1.0;
     A.t = t;
     double t2 = t * t;
     double t3 = t2 * t;
@@ -175,9 +183,10 @@ __device__ __forceinline__ Axis axis_x(const GridDev &g, double x, double *u)
     Axis A;
     A.cell = find_cell<uint64_t>(g.xbits, g.nxc, g.xstep, b);
     A.in = (b >= g.xlo) & (b <= g.xhi);
+    A.below = b < g.xlo;
     double uu = dlog(g, x);
     double2 c = g.xcell[A.cell];
-    make_basis(A, (uu - c.x) * c.y);
+    make_basis(A, (uu - c.x) * c.y, g.extrap);
     *u = uu;
     return A;
 }
@@ -189,8 +198,9 @@ __device__ __forceinline__ Axis axis_u(const GridDev &g, double u)
     Axis A;
     A.cell = find_cell<int64_t>(g.ukey, g.nxc, g.xstep, k);
     A.in = (k >= g.ulo) & (k <= g.uhi);
+    A.below = k < g.ulo;
     double2 c = g.xcell[A.cell];
-    make_basis(A, (u - c.x) * c.y);
+    make_basis(A, (u - c.x) * c.y, g.extrap);
     return A;
 }
 
@@ -200,9 +210,10 @@ __device__ __forceinline__ Axis axis_q2(const GridDev &g, double q2, double *w)
     Axis A;
     A.cell = find_cell<uint64_t>(g.qbits, g.nqc, g.qstep, b);
     A.in = (b >= g.qlo) & (b <= g.qhi);
+    A.below = b < g.qlo;
     double ww = dlog(g, q2);
     double2 c = g.qcell[A.cell];
-    make_basis(A, (ww - c.x) * c.y);
+    make_basis(A, (ww - c.x) * c.y, g.extrap);
     *w = ww;
     return A;
 }
@@ -213,8 +224,9 @@ __device__ __forceinline__ Axis axis_w(const GridDev &g, double w)
     Axis A;
     A.cell = find_cell<int64_t>(g.wkey, g.nqc, g.qstep, k);
     A.in = (k >= g.wlo) & (k <= g.whi);
+    A.below = k < g.wlo;
     double2 c = g.qcell[A.cell];
-    make_basis(A, (w - c.x) * c.y);
+    make_basis(A, (w - c.x) * c.y, g.extrap);
     return A;
 }
 
@@ -232,6 +244,8 @@ __device__ __forceinline__ double patch(const double *__restrict__ C, const Axis
 }
 
 // Patch value and its derivatives with respect to tx and tq.
+// (1, dx2, dx3) and (1, dq2, dq3) are the derivative bases of the two axes:
+// (1, 2t, 3t^2) inside the knot range, (1, 1, 1) for the linear continuation.
 __device__ __forceinline__ void patch_d(const double *__restrict__ C, const Axis &X, const Axis &Q,
                                         double dx2, double dx3, double dq2, double dq3,
                                         double *dtx, double *dtq)
@@ -270,10 +284,16 @@ __device__ __forceinline__ void stencil_weights(const double *__restrict__ M, co
     }
 }
 
-__device__ __forceinline__ void flag_status(const GridDev &g, bool bad)
+__device__ __forceinline__ void flag_status(const GridDev &g, bool bad, unsigned bit = PDF_S_DOMAIN)
 {
     unsigned m = __ballot_sync(__activemask(), bad);
-    if (m && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(g.status, (unsigned)PDF_S_DOMAIN);
+    if (m && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(g.status, bit);
+}
+
+// Outside the knot range of a grid that asks for NaN there.
+__device__ __forceinline__ bool out_of_range(const GridDev &g, const Axis &X, const Axis &Q)
+{
+    return g.extrap == PDF_EXTRAP_ERROR && !(X.in && Q.in);
 }
 
 __device__ __forceinline__ int pid_col(const GridDev &g, int pid)

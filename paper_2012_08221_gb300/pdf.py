@@ -14,9 +14,9 @@ import ctypes as C
 import numpy as np
 import torch
 
-from ._lib import GridDesc, PDF_S_DOMAIN, check, lib
+from ._lib import EXTRAP, INTERP, PDF_S_DOMAIN, PDF_S_RANGE, GridDesc, check, lib
 
-__all__ = ["PDF", "mkPDF", "PDF_S_DOMAIN"]
+__all__ = ["PDF", "mkPDF", "PDF_S_DOMAIN", "PDF_S_RANGE"]
 
 
 def _stream(device=None):
@@ -45,9 +45,13 @@ class PDF:
 
     ``values`` is ``[members][rows][n_x][n_flav]`` (or ``[rows][n_x][n_flav]``)
     of x*f on the knots; Q knots are in GeV with duplicated thresholds.
+    ``interp``: "logbicubic" (default), "logbilinear" or
+    "logbicubic_small_linear"; ``extrap``: "linear" (default), "freeze" or
+    "error" (see include/pdfgpu.h).
     """
 
-    def __init__(self, x_knots, n_q, q_knots, pids, values=None, alphas=None, device="cuda:0"):
+    def __init__(self, x_knots, n_q, q_knots, pids, values=None, alphas=None, device="cuda:0",
+                 interp="logbicubic", extrap="linear"):
         self.device = torch.device(device)
         torch.cuda.set_device(self.device)
         self._x = np.ascontiguousarray(x_knots, dtype=np.float64)
@@ -72,6 +76,9 @@ class PDF:
         desc.n_members = self.n_members
         desc.values = v.ctypes.data_as(C.POINTER(C.c_double)) if v is not None else None
         desc.alphas = a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+        desc.interp = INTERP[interp] if isinstance(interp, str) else int(interp)
+        desc.extrap = EXTRAP[extrap] if isinstance(extrap, str) else int(extrap)
+        self.interp, self.extrap = desc.interp, desc.extrap
         h = C.c_void_p()
         check("pdf_load_grid", lib().pdf_load_grid(C.byref(desc), C.byref(h)))
         self.handle = h
@@ -82,10 +89,10 @@ class PDF:
         self.has_alphas = a is not None
 
     @classmethod
-    def from_grid(cls, grid, device="cuda:0", with_values=True):
+    def from_grid(cls, grid, device="cuda:0", with_values=True, interp="logbicubic", extrap="linear"):
         """From a ``synth.Grid`` (or any object with the same fields)."""
         return cls(grid.x_knots, grid.n_q, grid.q_knots, grid.pids,
-                   grid.values if with_values else None, grid.alphas, device)
+                   grid.values if with_values else None, grid.alphas, device, interp, extrap)
 
     # ------------------------------------------------------------ lifetime
     def close(self):

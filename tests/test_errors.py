@@ -14,7 +14,7 @@ def L():
     return _lib.lib()
 
 
-def _desc(x, nq, q, pids, nmem=1):
+def _desc(x, nq, q, pids, nmem=1, interp=0, extrap=0):
     keep = [np.ascontiguousarray(x, np.float64), np.ascontiguousarray(nq, np.int32),
             np.ascontiguousarray(q, np.float64), np.ascontiguousarray(pids, np.int32)]
     d = _lib.GridDesc()
@@ -28,6 +28,8 @@ def _desc(x, nq, q, pids, nmem=1):
     d.n_members = nmem
     d.values = None
     d.alphas = None
+    d.interp = interp
+    d.extrap = extrap
     return d, keep
 
 
@@ -62,6 +64,11 @@ def test_malformed_descriptions(L, args, code, needle):
     rc, msg = _load(L, *args)
     assert rc == code
     assert needle in msg
+
+
+def test_unknown_modes(L):
+    assert _load(L, X, NQ, Q, P, interp=3)[0] == -2
+    assert _load(L, X, NQ, Q, P, extrap=-1)[0] == -2
 
 
 def test_zero_members(L):
