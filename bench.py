@@ -267,6 +267,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="points of the headline workload (smaller only for profiling captures)")
+    ap.add_argument("--lumi-events", type=int, default=100_000_000,
+                    help="events of the luminosity form (smaller only for profiling captures)")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="size factor of the batched form's requests (smaller only for profiling)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -406,7 +410,7 @@ def main():
         reqs = []
         ev4 = 0
         fl4 = 0
-        for b in synth.batches_uneven(grids):
+        for b in synth.batches_uneven(grids, scale=args.batch_scale):
             xb, qb = torch.as_tensor(b.x, device=dev), torch.as_tensor(b.q2, device=dev)
             ob = torch.empty((b.x.size, b.pids.size), dtype=torch.float64, device=dev)
             reqs.append((pdfs[b.set_index], b.member, b.pids, xb, qb, ob))
@@ -427,7 +431,7 @@ def main():
         from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
         g5 = synth.grid_nnpdf(seeds=(1005, 1006, 1007))
         p5 = PDF.from_grid(g5, device=dev)
-        n5 = 100_000_000
+        n5 = args.lumi_events
         ev = DeviceEvents.from_host(synth.events_lhc(n5), device=dev)
         LUM = torch.empty(n5, dtype=torch.float64, device=dev)
         L5 = torch.empty((), dtype=torch.float64, device=dev)
@@ -453,7 +457,7 @@ def main():
         ms5r, _ = timed(step5r, 2, args.warmup)
         ev5 = n5 * 2 * g5.n_flav
         forms["lumi"] = {
-            "workload": "1e8 events at sqrt(s) = 13 TeV (5% low tail), x1 and x2 over 13 flavours, "
+            "workload": f"{n5:.0e} events at sqrt(s) = 13 TeV (5% low tail), x1 and x2 over 13 flavours, "
                         "luminosity sum_a f_a(x1) f_-a(x2) and alpha_s per event, L = mean",
             "fwd": {"value": world * ev5 / (ms5 * 1e-3), "unit": "evals/s", "ms_per_step": ms5,
                     "fp64_frac": n5 * work.lumi_event_flops(g5.n_flav) / (ms5 * 1e-3) / peak},
