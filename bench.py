@@ -263,12 +263,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="all", help="comma list of fwdbwd,batched,lumi or all/none")
+    ap.add_argument("--forms", default="all", help="comma list of fwdbwd,batched,lumi,vegas or all/none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="points of the headline workload (smaller only for profiling captures)")
     ap.add_argument("--lumi-events", type=int, default=100_000_000,
                     help="events of the luminosity form (smaller only for profiling captures)")
+    ap.add_argument("--vegas-points", type=int, default=10_000_000,
+                    help="points per VEGAS iteration")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="size factor of the batched form's requests (smaller only for profiling)")
     args = ap.parse_args()
@@ -363,7 +365,7 @@ def main():
                 "kernel_ms": k_ms}
 
     forms = {}
-    want = set(["fwdbwd", "batched", "lumi"] if args.forms == "all" else
+    want = set(["fwdbwd", "batched", "lumi", "vegas"] if args.forms == "all" else
                ([] if args.forms == "none" else args.forms.split(",")))
 
     # --------------------------------------------------- forward + backward
@@ -472,6 +474,34 @@ def main():
                                                      work.lumi_bwd_event_flops(g5.n_flav))
                                   / (ms5r * 1e-3) / peak}}
         del ev, LUM, SAVE
+    # ------------------------------------------------------- VEGAS integration
+    if "vegas" in want:
+        from paper_2012_08221_gb300.vegas import VegasLumi
+        gv = synth.grid_nnpdf()
+        pv = PDF.from_grid(gv, device=dev)
+        n_it, n_pts = 5, args.vegas_points
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2006)
+        U = [torch.rand((n_pts, 2), generator=gen, dtype=torch.float64, device=dev) for _ in range(n_it)]
+        ln_tau_min, ln_s = math.log(1e-6), 2 * math.log(13000.0)
+        res = {}
+
+        def step6():
+            res["r"] = VegasLumi(pv, ln_tau_min, ln_s, n_bins=50).integrate(n_iter=n_it, n_per_iter=n_pts,
+                                                                              uniforms=U)
+
+        ms6, _ = timed(step6, 2, 1)
+        r = res["r"]
+        pts = n_it * n_pts
+        forms["vegas"] = {
+            "workload": f"VEGAS integral of the parton luminosity over (ln tau, y), tau > 1e-6, sqrt(s) = 13 TeV; "
+                        f"{n_it} adapting iterations x {n_pts} points, 50 bins per dimension",
+            "value": world * pts * 2 * gv.n_flav / (ms6 * 1e-3), "unit": "evals/s",
+            "points_per_s": world * pts / (ms6 * 1e-3), "ms_per_step": ms6,
+            "fp64_frac": pts * work.vegas_point_flops(gv.n_flav) / (ms6 * 1e-3) / peak,
+            "integral": r.integral, "error": r.error, "chi2_dof": r.chi2_dof}
+        del U
+
     clk = clocks.stop()
 
     # ----------------------------------------------------------- end to end

@@ -272,6 +272,52 @@ int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *ln_tau, con
                       double ln_s, int64_t n, double dL, const double *saved_p,
                       double *grad_values, pdfgpu_stream_t stream);
 
+/* Adaptive Monte Carlo integration of the parton luminosity (PDFFlow Sec.
+ * 3.1: VegasFlow importance sampling around an integrand that calls the
+ * PDFs; the matrix element is 1 here):
+ *   I = int_0^1 dr1 dr2 F(r1, r2),  ln tau = (1 - r1) ln_tau_min,
+ *   y = (2 r2 - 1)(-ln tau / 2),  ln x1,2 = ln tau / 2 +- y,
+ *   ln Q^2 = ln tau + ln_s,  F = (-ln_tau_min)(-ln tau) sum_a xf_a(x1) xf_-a(x2),
+ * sampled through the VEGAS map (Lepage, J. Comput. Phys. 27 (1978) 192):
+ * per dimension n_bins bins with edges 0 = e_0 < ... < e_n = 1; a uniform v
+ * falls in bin i = floor(v n) and maps to r = e_i + (v n - i)(e_{i+1} - e_i)
+ * with Jacobian n (e_{i+1} - e_i).
+ * pdf_vegas_lumi_iteration evaluates one iteration:
+ *   edges DEVICE [2][n_bins + 1], v DEVICE [n][2] uniforms in [0, 1),
+ *   sums DEVICE [2 + 2 n_bins] (overwritten): sum w, sum w^2, then per bin
+ *   the sum of w^2 for dimension 0 and for dimension 1, w = F(r) x Jacobian.
+ * 2 <= n_bins <= 1024, ln_tau_min < 0.  Uses the grid handle's scratch for
+ * block partial sums (calls on one grid must not overlap).  Asynchronous.
+ * pdf_vegas_refine moves one dimension's HOST edges [n_bins + 1] from its
+ * HOST per-bin sums of w^2: smoothing with the neighbours, damping
+ * r_i = ((1 - d_i) / ln(1 / d_i))^alpha (d_i normalised), and new edges that
+ * give every bin an equal share of sum r_i.  Host only. */
+int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double ln_tau_min, double ln_s,
+                             int32_t n_bins, const double *edges, const double *v, int64_t n,
+                             double *sums, pdfgpu_stream_t stream);
+int pdf_vegas_refine(const double *bin_w2, int32_t n_bins, double alpha, double *edges);
+
+/* LHAPDF grid files (PDFFlow Sec. 1 and 4 keep the community "lhagrid1"
+ * format and folder layout).  HOST only: no GPU call is made.
+ * pdf_lhapdf_open reads members [first_member, first_member + n_members) of
+ * the set in folder `set_dir` (files <name>/<name>.info and
+ * <name>_<mmmm>.dat, <name> = the folder's last path component).  In a member
+ * file, after the header line "---", each Q subgrid block is: a line of x
+ * knots, a line of Q knots (GeV), a line of PDG ids, then n_x * n_q lines of
+ * x*f values (x knot outer, Q knot inner), closed by "---".  All subgrids must
+ * share the x knots and flavours; all members must share the knots.
+ * AlphaS_Qs / AlphaS_Vals of the .info file are used when the Q list equals
+ * the grid's Q knots.  Errors: PDF_E_ARG (missing file), PDF_E_DESC
+ * (malformed), PDF_E_RANGE (members beyond NumMembers).
+ * pdf_lhapdf_desc fills a description (interp and extrap 0) whose arrays
+ * belong to the handle and stay valid until pdf_lhapdf_close; pass it to
+ * pdf_load_grid. */
+typedef struct pdfgpu_lhapdf *pdfgpu_lhapdf_t;
+int pdf_lhapdf_open(const char *set_dir, int32_t first_member, int32_t n_members,
+                    pdfgpu_lhapdf_t *out);
+int pdf_lhapdf_desc(pdfgpu_lhapdf_t h, pdfgpu_grid_desc *desc);
+int pdf_lhapdf_close(pdfgpu_lhapdf_t h);
+
 /* Read and clear the grid's status word (PDF_S_* bits).  Synchronises
  * `stream` first. */
 int pdf_get_status(pdfgpu_grid_t g, pdfgpu_stream_t stream, uint32_t *bits);

@@ -91,6 +91,9 @@ def lib():
             L.orc_lumi_batch.restype = C.c_double
             L.orc_lumi_dgrid.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
                                          C.c_int64, _D, C.c_int]
+            L.orc_vegas_sums.argtypes = [_G, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
+                                         C.c_int64, _D]
+            L.orc_vegas_refine.argtypes = [_D, C.c_int, C.c_double, _D]
             _lib = L
     return _lib
 
@@ -267,3 +270,23 @@ class OracleGrid:
                              fl.ctypes.data_as(C.POINTER(C.c_ubyte)), _d(lm), _d(lx),
                              float(ev.ln_s), n, _d(grad), int(absval))
         return grad
+
+
+def vegas_refine(bin_w2, alpha, edges):
+    """New edges (one dimension) from per-bin sums of w^2 (Lepage's rule)."""
+    b = _f64(bin_w2)
+    e = _f64(edges).copy()
+    lib().orc_vegas_refine(_d(b), b.size, float(alpha), _d(e))
+    return e
+
+
+def vegas_sums(grid: "OracleGrid", member, ln_tau_min, ln_s, edges, v):
+    """Sums of one VEGAS iteration of the luminosity integral (see the C
+    file): [sum w, sum w^2, per-bin w^2 of dimension 0, of dimension 1]."""
+    e = _f64(edges)
+    n_bins = e.shape[1] - 1
+    v = _f64(v)
+    out = np.empty(2 + 2 * n_bins)
+    lib().orc_vegas_sums(grid.ptr, member, float(ln_tau_min), float(ln_s), n_bins, _d(e), _d(v),
+                         v.shape[0], _d(out))
+    return out

@@ -567,3 +567,99 @@ void orc_lumi_dgrid(const orc_grid *g, int member, const double *ln_tau, const d
         }
     }
 }
+
+/* ------------------------------------------ adaptive Monte Carlo (VEGAS) */
+/*
+ * The Monte Carlo use of the paper (Sec. 3.1: VegasFlow importance sampling
+ * around an integrand that calls the PDFs; matrix element set to 1 here):
+ *
+ *   I = int_0^1 dr1 dr2 F(r1, r2),
+ *   ln tau = (1 - r1) ln tau_min,  y = (2 r2 - 1)(-ln tau / 2),
+ *   ln x1,2 = ln tau / 2 +- y,  ln Q^2 = ln tau + ln s,
+ *   F = (-ln tau_min)(-ln tau) sum_a xf_a(x1) xf_{-a}(x2)
+ *
+ * (the Jacobian of (ln tau, y) -> (r1, r2) times the luminosity), sampled
+ * through the VEGAS map of Lepage (J. Comput. Phys. 27 (1978) 192): per
+ * dimension n_bins bins with edges e_0 = 0 < ... < e_n = 1; a uniform v
+ * falls in bin i = floor(v n) at fraction d = v n - i, is mapped to
+ * r = e_i + d (e_{i+1} - e_i), with Jacobian n (e_{i+1} - e_i).
+ */
+
+/* Sums of one iteration: out[0] = sum w, out[1] = sum w^2, then for each of
+ * the two dimensions the sum of w^2 over the points in each bin, where
+ * w = F(r) J(v) is the weight of the point drawn with uniforms v[i][0..1]. */
+void orc_vegas_sums(const orc_grid *g, int member, double ln_tau_min, double ln_s, int n_bins,
+                    const double *edges, const double *v, int64_t n, double *out)
+{
+    for (int k = 0; k < 2 + 2 * n_bins; ++k) out[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double r[2], jac = 1.0;
+        int bin[2];
+        for (int d = 0; d < 2; ++d) {
+            const double *e = edges + (size_t)d * (n_bins + 1);
+            double vn = v[2 * i + d] * n_bins;
+            int b = (int)vn;
+            if (b > n_bins - 1) b = n_bins - 1;
+            double frac = vn - b;
+            double width = e[b + 1] - e[b];
+            r[d] = e[b] + frac * width;
+            jac *= n_bins * width;
+            bin[d] = b;
+        }
+        double ln_tau = (1.0 - r[0]) * ln_tau_min;
+        double h = 0.5 * ln_tau;
+        double y = (2.0 * r[1] - 1.0) * (-h);
+        double u1 = h + y, u2 = h - y, w = ln_tau + ln_s;
+        double lum = 0.0;
+        for (int a = 0; a < g->n_flav; ++a) {
+            int pa = g->pids[a];
+            lum += orc_xfxq2_uw(g, member, pa, u1, w, NULL, NULL) *
+                   orc_xfxq2_uw(g, member, -pa, u2, w, NULL, NULL);
+        }
+        double f = (-ln_tau_min) * (-ln_tau) * lum;
+        double wt = f * jac;
+        out[0] += wt;
+        out[1] += wt * wt;
+        out[2 + bin[0]] += wt * wt;
+        out[2 + n_bins + bin[1]] += wt * wt;
+    }
+}
+
+/* One refinement of one dimension's edges from its per-bin sums of w^2
+ * (Lepage's rule): smooth the sums with their neighbours, damp them as
+ * r_i = ((1 - d_i) / ln(1 / d_i))^alpha with d_i the normalised smoothed sum,
+ * and place the new edges so that every new bin holds an equal share of
+ * sum r_i, the old bins' shares spread uniformly over their widths. */
+void orc_vegas_refine(const double *bin_w2, int n_bins, double alpha, double *edges)
+{
+    double d[4096], r[4096], e_old[4097];
+    if (n_bins < 2 || n_bins > 4096) return;
+    d[0] = 0.5 * (bin_w2[0] + bin_w2[1]);
+    for (int i = 1; i < n_bins - 1; ++i) d[i] = (bin_w2[i - 1] + bin_w2[i] + bin_w2[i + 1]) / 3.0;
+    d[n_bins - 1] = 0.5 * (bin_w2[n_bins - 2] + bin_w2[n_bins - 1]);
+    double dsum = 0.0;
+    for (int i = 0; i < n_bins; ++i) dsum += d[i];
+    if (!(dsum > 0.0)) return;
+    double rsum = 0.0;
+    for (int i = 0; i < n_bins; ++i) {
+        double di = d[i] / dsum;
+        r[i] = (di > 0.0 && di < 1.0) ? pow((1.0 - di) / log(1.0 / di), alpha) : 0.0;
+        rsum += r[i];
+    }
+    if (!(rsum > 0.0)) return;
+    for (int i = 0; i <= n_bins; ++i) e_old[i] = edges[i];
+    double per_bin = rsum / n_bins, acc = 0.0;
+    int k = 0;
+    for (int j = 1; j < n_bins; ++j) {
+        double target = j * per_bin;
+        while (acc + r[k] <= target) {
+            acc += r[k];
+            ++k;
+        }
+        /* the new edge lies in old bin k, at the fraction of its share still needed */
+        double frac = (target - acc) / r[k];
+        edges[j] = e_old[k] + frac * (e_old[k + 1] - e_old[k]);
+    }
+    edges[0] = 0.0;
+    edges[n_bins] = 1.0;
+}

@@ -1,0 +1,80 @@
+"""VEGAS integration of the parton luminosity on the GPU (PDFFlow Sec. 3.1:
+VegasFlow-style importance sampling around the PDF calls).
+
+Each iteration draws uniforms (a torch generator on the device, or arrays the
+caller passes), evaluates the integrand through the VEGAS map in one kernel
+(`pdf_vegas_lumi_iteration`), and refines the two dimensions' grids on the
+host (`pdf_vegas_refine`).  Iterations are combined with weights 1/sigma^2.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from ._lib import check, lib
+from .pdf import PDF, _ptr, _stream
+
+
+@dataclass
+class VegasResult:
+    integral: float
+    error: float
+    chi2_dof: float
+    iterations: list = field(default_factory=list)   # (estimate, error) per iteration
+    edges: np.ndarray | None = None
+
+
+class VegasLumi:
+    def __init__(self, pdf: PDF, ln_tau_min: float, ln_s: float, n_bins: int = 50, alpha: float = 1.5,
+                 member: int = 0):
+        self.pdf, self.member = pdf, member
+        self.ln_tau_min, self.ln_s = float(ln_tau_min), float(ln_s)
+        self.n_bins, self.alpha = int(n_bins), float(alpha)
+        self.edges = np.tile(np.linspace(0.0, 1.0, self.n_bins + 1), (2, 1))
+        self._sums = torch.empty(2 + 2 * self.n_bins, dtype=torch.float64, device=pdf.device)
+
+    def iteration(self, v: torch.Tensor, refine: bool = True):
+        """One iteration on the uniforms ``v`` ([n][2] float64 on the device).
+        Returns (estimate, error, raw sums)."""
+        dev = self.pdf.device
+        v = v.to(device=dev, dtype=torch.float64).contiguous()
+        n = v.shape[0]
+        e = torch.as_tensor(self.edges, device=dev)
+        check("pdf_vegas_lumi_iteration", lib().pdf_vegas_lumi_iteration(
+            self.pdf.handle, self.member, self.ln_tau_min, self.ln_s, self.n_bins, _ptr(e), _ptr(v), n,
+            _ptr(self._sums), _stream(dev)))
+        s = self._sums.cpu().numpy()
+        mean = s[0] / n
+        var = max(s[1] / n - mean * mean, 0.0) / max(n - 1, 1)
+        if refine:
+            for d in range(2):
+                b = np.ascontiguousarray(s[2 + d * self.n_bins: 2 + (d + 1) * self.n_bins])
+                ed = np.ascontiguousarray(self.edges[d])
+                check("pdf_vegas_refine", lib().pdf_vegas_refine(
+                    b.ctypes.data_as(C.POINTER(C.c_double)), self.n_bins, self.alpha,
+                    ed.ctypes.data_as(C.POINTER(C.c_double))))
+                self.edges[d] = ed
+        return mean, math.sqrt(var), s
+
+    def integrate(self, n_iter: int = 5, n_per_iter: int = 1_000_000, seed: int = 0,
+                  uniforms=None, warmup: int = 0) -> VegasResult:
+        """``warmup`` iterations adapt the grid and are not averaged."""
+        gen = torch.Generator(device=self.pdf.device)
+        gen.manual_seed(seed)
+        ests = []
+        for it in range(warmup + n_iter):
+            v = uniforms[it] if uniforms is not None else torch.rand(
+                (n_per_iter, 2), generator=gen, dtype=torch.float64, device=self.pdf.device)
+            est, err, _ = self.iteration(v)
+            if it >= warmup:
+                ests.append((est, err))
+        w = np.array([1.0 / max(e, 1e-300) ** 2 for _, e in ests])
+        vals = np.array([m for m, _ in ests])
+        integral = float(np.sum(w * vals) / np.sum(w))
+        error = float(1.0 / math.sqrt(np.sum(w)))
+        chi2 = float(np.sum(w * (vals - integral) ** 2) / max(len(ests) - 1, 1))
+        return VegasResult(integral, error, chi2, ests, self.edges.copy())

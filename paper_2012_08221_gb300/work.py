@@ -76,3 +76,11 @@ def lumi_bwd_event_flops(n_flav: int, saved: bool = False) -> int:
 
 
 LUMI_BWD_EVENT_BYTES = 8 + 8 + 1
+
+
+def vegas_point_flops(n_flav: int) -> int:
+    """One VEGAS point of the luminosity integral: the map of 2 dimensions
+    (multiply, subtract, FMA, width difference, Jacobian multiply: 6 each),
+    the kinematics (5), 3 axes, 2 F patches and F FMAs for the luminosity, the
+    weight (3 multiplies) and its sums (add, FMA)."""
+    return 2 * 6 + 5 + 3 * AXIS_FLOPS + 2 * PATCH_FLOPS * n_flav + 2 * n_flav + 3 + 3
