@@ -58,44 +58,56 @@ _I = C.POINTER(C.c_int)
 _G = C.POINTER(_Grid)
 
 
+def load_library(path):
+    """A handle on an oracle shared object with every prototype declared."""
+    L = C.CDLL(path)
+    _declare(L)
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             L = C.CDLL(build())
-            L.orc_init.argtypes = [_G]
-            L.orc_init.restype = C.c_int
-            L.orc_xfxq2.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double]
-            L.orc_xfxq2.restype = C.c_double
-            L.orc_xfxq2_uw.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double, _D, _D]
-            L.orc_xfxq2_uw.restype = C.c_double
-            L.orc_xfxq2_grad.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double, _D, _D]
-            L.orc_xfxq2_grad.restype = C.c_double
-            L.orc_alphas.argtypes = [_G, C.c_double]
-            L.orc_alphas.restype = C.c_double
-            L.orc_alphas_w.argtypes = [_G, C.c_double]
-            L.orc_alphas_w.restype = C.c_double
-            L.orc_cell_weight_uw.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double]
-            L.orc_cell_weight_uw.restype = C.c_double
-            L.orc_xfxq2_batch.argtypes = [_G, C.c_int, _I, C.c_int, _D, _D, C.c_int64, _D]
-            L.orc_xfxq2_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D]
-            L.orc_alphas_batch.argtypes = [_G, _D, C.c_int64, _D]
-            L.orc_grad_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D, _D]
-            L.orc_kappa_batch.argtypes = [_G, C.c_int, _I, C.c_int, C.c_int, _D, _D,
-                                          C.c_int64, _D]
-            L.orc_dgrid_pw.argtypes = [_G, _I, _D, _D, _D, C.c_int64, _D, C.c_int]
-            L.orc_dgrid_batch.argtypes = [_G, _I, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_int]
-            U8 = C.POINTER(C.c_ubyte)
-            L.orc_lumi_batch.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
-                                         C.c_int64, _D, _D]
-            L.orc_lumi_batch.restype = C.c_double
-            L.orc_lumi_dgrid.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
-                                         C.c_int64, _D, C.c_int]
-            L.orc_vegas_sums.argtypes = [_G, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
-                                         C.c_int64, _D]
-            L.orc_vegas_refine.argtypes = [_D, C.c_int, C.c_double, _D]
+            _declare(L)
             _lib = L
     return _lib
+
+
+def _declare(L):
+    """Argument and result types of every oracle entry point."""
+    L.orc_init.argtypes = [_G]
+    L.orc_init.restype = C.c_int
+    L.orc_xfxq2.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double]
+    L.orc_xfxq2.restype = C.c_double
+    L.orc_xfxq2_uw.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double, _D, _D]
+    L.orc_xfxq2_uw.restype = C.c_double
+    L.orc_xfxq2_grad.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double, _D, _D]
+    L.orc_xfxq2_grad.restype = C.c_double
+    L.orc_alphas.argtypes = [_G, C.c_double]
+    L.orc_alphas.restype = C.c_double
+    L.orc_alphas_w.argtypes = [_G, C.c_double]
+    L.orc_alphas_w.restype = C.c_double
+    L.orc_cell_weight_uw.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double]
+    L.orc_cell_weight_uw.restype = C.c_double
+    L.orc_xfxq2_batch.argtypes = [_G, C.c_int, _I, C.c_int, _D, _D, C.c_int64, _D]
+    L.orc_xfxq2_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D]
+    L.orc_alphas_batch.argtypes = [_G, _D, C.c_int64, _D]
+    L.orc_grad_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D, _D]
+    L.orc_kappa_batch.argtypes = [_G, C.c_int, _I, C.c_int, C.c_int, _D, _D,
+                                  C.c_int64, _D]
+    L.orc_dgrid_pw.argtypes = [_G, _I, _D, _D, _D, C.c_int64, _D, C.c_int]
+    L.orc_dgrid_batch.argtypes = [_G, _I, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_int]
+    U8 = C.POINTER(C.c_ubyte)
+    L.orc_lumi_batch.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
+                                 C.c_int64, _D, _D]
+    L.orc_lumi_batch.restype = C.c_double
+    L.orc_lumi_dgrid.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
+                                 C.c_int64, _D, C.c_int]
+    L.orc_vegas_sums.argtypes = [_G, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
+                                 C.c_int64, _D]
+    L.orc_vegas_refine.argtypes = [_D, C.c_int, C.c_double, _D]
 
 
 def _d(a):

@@ -1,0 +1,118 @@
+"""The pins are strong enough to catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a copy of ``oracle/pdf_oracle.c`` (a dropped
+or flipped term, a wrong index, a wrong tie-break...), builds it into a
+separate shared object on the CPU, and runs a compact set of the pins against
+it: at least one must fail.  The unmodified oracle passes all of them."""
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle.oracle as O
+from oracle.bruteforce import ExactGrid
+from paper_2012_08221_gb300 import synth
+from tests.tinygrids import fill, tiny_two_sub
+
+SRC = os.path.join(os.path.dirname(O.__file__), "pdf_oracle.c")
+
+MUTANTS = {
+    "hermite h10 sign": ("double h10 = t3 - 2.0 * t2 + t;", "double h10 = t3 - 2.0 * t2 - t;"),
+    "hermite h01 coefficient": ("double h01 = -2.0 * t3 + 3.0 * t2;", "double h01 = -2.0 * t3 + 2.0 * t2;"),
+    "hermite derivative dropped": ("return h00 * g0 + h10 * dz * d0 + h01 * g1 + h11 * dz * d1;",
+                                   "return h00 * g0 + h10 * dz * d0 + h01 * g1;"),
+    "interior slope one-sided": (
+        "return 0.5 * ((gp - g0) / (z[k + 1] - z[k]) + (g0 - gm) / (z[k] - z[k - 1]));",
+        "return (gp - g0) / (z[k + 1] - z[k]);"),
+    "first-knot slope zero": ("if (k == 0) return (gp - g0) / (z[1] - z[0]);", "if (k == 0) return 0.0;"),
+    "last-knot slope transposed": ("if (k == n - 1) return (g0 - gm) / (z[n - 1] - z[n - 2]);",
+                                   "if (k == n - 1) return (gm - g0) / (z[n - 1] - z[n - 2]);"),
+    "threshold to lower subgrid": ("        if (W[g->row0[j]] <= w) s = j;\n    int n = g->n_q[s], r0 = g->row0[s];",
+                                   "        if (W[g->row0[j]] < w) s = j;\n    int n = g->n_q[s], r0 = g->row0[s];"),
+    "w extrapolation rows": ("int r0 = w < W[0] ? 0 : last - 1;", "int r0 = w < W[0] ? 1 : last - 1;"),
+    "u extrapolation columns": ("int k0 = u < U[0] ? 0 : n - 2;", "int k0 = u < U[0] ? 1 : n - 2;"),
+    "w-derivative sign": ("if (dw) *dw = (B1 - B0) / dz;\n        if (du)",
+                          "if (dw) *dw = (B0 - B1) / dz;\n        if (du)"),
+    "row stencil shifted": ("double gm = k > 0 ? val(a, row, k - 1) : 0.0;",
+                            "double gm = k > 1 ? val(a, row, k - 2) : 0.0;"),
+}
+
+
+def build_variant(tmp, text):
+    src = os.path.join(tmp, "orc.c")
+    with open(src, "w") as f:
+        f.write(text)
+    so = os.path.join(tmp, "liborc_variant.so")
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", src, "-o", so, "-lm"],
+                   check=True)
+    return O.load_library(so)
+
+
+def pin_failures():
+    """Names of the compact pins that fail with the currently loaded oracle."""
+    fails = []
+    # knot values, including thresholds, on a two-subgrid grid
+    g = tiny_two_sub(seed=41, dup_equal=False)
+    o = O.OracleGrid.from_synth(g)
+    starts = np.concatenate([[0], np.cumsum(g.n_q)[:-1]])
+    for r in range(g.n_rows):
+        row = r + 1 if any(r == s + n - 1 for s, n in zip(starts[:-1], g.n_q[:-1])) else r
+        for k in range(g.n_x):
+            if o.xfxq2(g.pids[0], g.x_knots[k], g.q_knots[r] ** 2) != g.values[0, row, k, 0]:
+                fails.append("knots")
+                break
+        if fails:
+            break
+    # log-bilinear data everywhere (inside and outside), with derivatives
+    gl = fill(synth.grid_small(), lambda U, W: 0.7 - 0.3 * U + 0.05 * W + 0.01 * U * W)
+    ol = O.OracleGrid.from_synth(gl)
+    rng = np.random.default_rng(42)
+    for u, w in zip(rng.uniform(-22, 0, 200), rng.uniform(-1, 22, 200)):
+        v, du, dw = ol.xfxq2_uw(0, u, w)
+        if (abs(v - (0.7 - 0.3 * u + 0.05 * w + 0.01 * u * w)) > 1e-12 or
+                abs(du - (-0.3 + 0.01 * w)) > 1e-11 or abs(dw - (0.05 + 0.01 * u)) > 1e-11):
+            fails.append("bilinear")
+            break
+    # quadratic in u: interior exact, first interval h^2 t (1-t)^2
+    gq = fill(synth.grid_small(), lambda U, W: U * U + 0 * W)
+    oq = O.OracleGrid.from_synth(gq)
+    U = np.log(gq.x_knots)
+    h = U[1] - U[0]
+    for k, t in [(0, 0.3), (10, 0.4), (30, 0.8)]:
+        u = U[k] + t * (U[k + 1] - U[k])
+        want = u * u + (h * h * t * (1 - t) ** 2 if k == 0 else 0.0)
+        if abs(oq.xfxq2_uw(0, u, math.log(50.0))[0] - want) > 1e-11 * (1 + u * u):
+            fails.append("quadratic")
+            break
+    # exact-rational brute force on the two-subgrid grid
+    Wsub = [o.W[0:3], o.W[3:6]]
+    ex = ExactGrid(o.U, Wsub, [g.values[0, 0:3, :, 0], g.values[0, 3:6, :, 0]])
+    for u, w in zip(rng.uniform(o.U[0] - 1, 0, 40), rng.uniform(o.W[0] - 1, o.W[-1] + 1, 40)):
+        if abs(o.xfxq2_uw(g.pids[0], u, w)[0] - float(ex.eval(u, w)[0])) > 1e-13:
+            fails.append("brute force")
+            break
+    return fails
+
+
+@pytest.fixture
+def swap_oracle():
+    saved = O._lib
+    yield
+    O._lib = saved
+
+
+def test_unmodified_oracle_passes_the_compact_pins():
+    assert pin_failures() == []
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path, swap_oracle):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    O._lib = build_variant(str(tmp_path), text.replace(old, new))
+    assert pin_failures(), f"no pin catches: {name}"
+    shutil.rmtree(tmp_path, ignore_errors=True)
