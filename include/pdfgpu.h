@@ -164,6 +164,12 @@ int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *
 int alphasQ2(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream);
 int alphasQ(pdfgpu_grid_t g, const double *q, int64_t n, double *out, pdfgpu_stream_t stream);
 
+/* alpha_s(Q^2) and its derivative d alpha_s / d Q^2 (the derivative of the
+ * same piecewise cubic in ln Q^2, divided by Q^2; zero across a frozen edge).
+ * q2, dq2 DEVICE [n]; out DEVICE [n] or NULL. */
+int alphasQ2_grad(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, double *dq2,
+                  pdfgpu_stream_t stream);
+
 /* End-to-end form of xfxQ2 for HOST buffers: x, q2 HOST [n], out HOST
  * [n][n_pid].  The library streams the points through device staging buffers
  * it owns (chunks overlapped on internal streams), and returns when `out` is

@@ -87,6 +87,8 @@ def _declare(L):
     L.orc_xfxq2_grad.restype = C.c_double
     L.orc_alphas.argtypes = [_G, C.c_double]
     L.orc_alphas.restype = C.c_double
+    L.orc_alphas_grad.argtypes = [_G, C.c_double, _D]
+    L.orc_alphas_grad.restype = C.c_double
     L.orc_alphas_w.argtypes = [_G, C.c_double]
     L.orc_alphas_w.restype = C.c_double
     L.orc_cell_weight_uw.argtypes = [_G, C.c_int, C.c_int, C.c_double, C.c_double]
@@ -206,6 +208,12 @@ class OracleGrid:
 
     def alphas_q2(self, q2):
         return lib().orc_alphas(self.ptr, float(q2))
+
+    def alphas_grad(self, q2):
+        """(alpha_s, d alpha_s / d Q^2) at one Q^2."""
+        d = C.c_double()
+        v = lib().orc_alphas_grad(self.ptr, float(q2), C.byref(d))
+        return v, d.value
 
     def alphas_w(self, w):
         return lib().orc_alphas_w(self.ptr, float(w))

@@ -343,6 +343,26 @@ double orc_alphas_w(const orc_grid *g, double w)
     return wdir(&a, &c, w, NULL, NULL);
 }
 
+/* alpha_s and d alpha_s / d Q^2 (chain rule through w = ln Q^2). */
+double orc_alphas_grad(const orc_grid *g, double q2, double *dq2)
+{
+    *dq2 = NAN;
+    if (bad_q2(q2) || !g->alphas) return NAN;
+    double w = log(q2);
+    if (g->extrap == 2 && (w < g->W[0] || w > g->W[g->rows - 1])) return NAN;
+    acc_t a;
+    a.g = g;
+    a.base = g->alphas;
+    a.stride_row = 1;
+    a.stride_k = 0;
+    a.ind_row = a.ind_k = -1;
+    xsel_t c = {0, 0.0};
+    double dw = 0.0;
+    double v = wdir(&a, &c, w, &dw, NULL);
+    *dq2 = dw / q2;
+    return v;
+}
+
 double orc_alphas(const orc_grid *g, double q2)
 {
     if (bad_q2(q2)) return NAN;

@@ -56,6 +56,7 @@ SIGNATURES = {
     "xfxQ2_pw": [c_grid, C.c_int32, _VP, _VP, _VP, C.c_int64, _VP, _VP],
     "alphasQ2": [c_grid, _VP, C.c_int64, _VP, _VP],
     "alphasQ": [c_grid, _VP, C.c_int64, _VP, _VP],
+    "alphasQ2_grad": [c_grid, _VP, C.c_int64, _VP, _VP, _VP],
     "xfxQ2_host": [c_grid, C.c_int32, _I, C.c_int32, _VP, _VP, C.c_int64, _VP],
     "xfxQ2_backward": [c_grid, C.c_int32, _VP, C.c_int32, C.c_int32, _VP, _VP, C.c_int64,
                        _VP, _VP, _VP, _VP, _VP],

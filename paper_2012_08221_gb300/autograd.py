@@ -52,6 +52,27 @@ def xfxQ2_pw(pdf: PDF, values, pid, x, q2, member: int = 0):
     return XfxQ2Fn.apply(values, x, q2, pdf, pid, member, True)
 
 
+class AlphasFn(torch.autograd.Function):
+    """alpha_s(Q^2) differentiable in Q^2 (alpha_s knots are not a parameter)."""
+
+    @staticmethod
+    def forward(ctx, q2, pdf: PDF):
+        ctx.save_for_backward(q2)
+        ctx.pdf = pdf
+        return pdf.alphasQ2(q2)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (q2,) = ctx.saved_tensors
+        _, d = ctx.pdf.alphasQ2_grad(q2, want_value=False)
+        return gout * d, None
+
+
+def alphasQ2(pdf: PDF, q2):
+    """Differentiable alpha_s(Q^2)."""
+    return AlphasFn.apply(q2, pdf)
+
+
 class LumiFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, values, pdf: PDF, events, member: int, save: bool):

@@ -17,9 +17,11 @@ namespace {
 constexpr int kBlock = 256;
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000000000000ll); }
 
-// One point per thread (grid-stride over blocks).  Results of a block are
-// staged in shared memory and written out as one contiguous, coalesced run
-// of npid * blockDim doubles (the output is [n][npid] row-major).
+// One point per thread; each warp takes 32 consecutive points at a time
+// (grid-stride over warps).  A warp's results are staged in its own slice of
+// shared memory and written out as one contiguous, coalesced run of 32 * npid
+// doubles (the output is [n][npid] row-major): only warp-level
+// synchronisation, no block barriers in the loop.
 template <bool Q_IS_Q>
 __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid, int member,
                                                   const double *__restrict__ x,
@@ -35,9 +37,11 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
     __syncthreads();
     const size_t cell_stride = (size_t)g.nflav * 16;
     const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = base + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double *wbuf = sout + (size_t)wid * 32 * npid;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5) * 32;
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wid) * 32; base < n; base += wstride) {
+        int64_t i = base + lane;
         bool live = i < n;
         double xi = live ? x[i] : 0.5;
         double qi = live ? q[i] : 10.0;
@@ -55,18 +59,18 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
-        double *srow = sout + threadIdx.x * npid;
+        double *srow = wbuf + lane * npid;
         for (int a = 0; a < npid; ++a) {
             int col = scol[a];
             double v = col >= 0 ? patch(cell + col * 16, X, Q) : 0.0;
             srow[a] = bad ? qnan() : v;
         }
-        __syncthreads();
-        int64_t rows = min((int64_t)blockDim.x, n - base);
-        int64_t cnt = rows * npid;
+        __syncwarp();
+        const int rows = (int)min((int64_t)32, n - base);
+        const int cnt = rows * npid;
         double *dst = out + base * npid;
-        for (int64_t k = threadIdx.x; k < cnt; k += blockDim.x) dst[k] = sout[k];
-        __syncthreads();
+        for (int k = lane; k < cnt; k += 32) dst[k] = wbuf[k];
+        __syncwarp();
     }
 }
 
@@ -120,6 +124,32 @@ __global__ void __launch_bounds__(kBlock) k_alphas(GridDev g, const double *__re
         double2 a01 = __ldg(A), a23 = __ldg(A + 1);
         double v = fma(Q.b3, a23.y, fma(Q.b2, a23.x, fma(Q.t, a01.y, a01.x)));
         out[i] = bad ? qnan() : v;
+    }
+}
+
+// alpha_s and d alpha_s / d Q^2 = (da/dtq) / dW / Q^2 (zero across a frozen edge).
+__global__ void __launch_bounds__(kBlock) k_alphas_grad(GridDev g, const double *__restrict__ q2, int64_t n,
+                                                        double *__restrict__ out, double *__restrict__ dq2)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double qi = q2[i];
+        bool bad = !q2_ok(dbits(qi));
+        flag_status(g, bad);
+        if (bad) qi = 10.0;
+        double w;
+        Axis Q = axis_q2(g, qi, &w);
+        const bool oor = g.extrap == PDF_EXTRAP_ERROR && !Q.in;
+        flag_status(g, oor, PDF_S_RANGE);
+        bad |= oor;
+        const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
+        double2 a01 = __ldg(A), a23 = __ldg(A + 1);
+        double v = fma(Q.b3, a23.y, fma(Q.b2, a23.x, fma(Q.t, a01.y, a01.x)));
+        double d2 = Q.in ? 2.0 * Q.t : 1.0, d3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
+        double dt = fma(d3, a23.y, fma(d2, a23.x, a01.y));
+        if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dt = 0.0;
+        if (out) out[i] = bad ? qnan() : v;
+        dq2[i] = bad ? qnan() : dt * g.qcell[Q.cell].y * __drcp_rn(qi);
     }
 }
 
@@ -213,6 +243,22 @@ extern "C" int alphasQ2(pdfgpu_grid_t g, const double *q2, int64_t n, double *ou
 extern "C" int alphasQ(pdfgpu_grid_t g, const double *q, int64_t n, double *out, pdfgpu_stream_t stream)
 {
     return launch_alphas(g, q, n, out, (cudaStream_t)stream, true);
+}
+
+extern "C" int alphasQ2_grad(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, double *dq2,
+                             pdfgpu_stream_t stream)
+{
+    clear_error();
+    int rc = check_grid(g, false);
+    if (rc) return rc;
+    if (!g->has_alphas) return fail(PDF_E_DESC, "grid has no alpha_s values");
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (n == 0) return PDF_OK;
+    if (!q2 || !dq2) return fail(PDF_E_ARG, "null array");
+    int grid = wave_grid(g, (const void *)k_alphas_grad, kBlock, 0, n);
+    k_alphas_grad<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, q2, n, out, dq2);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
 }
 
 extern "C" int pdf_debug_log(pdfgpu_grid_t g, const double *in, int64_t n, double *out,

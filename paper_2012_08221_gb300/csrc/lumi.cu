@@ -144,13 +144,14 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 //   4. k_lumi_accum: each warp walks a run of cell-sorted partons in batches
 //      of 32 (one parton per lane computes its 16 stencil weights into shared
 //      memory), every lane owns fixed (stencil slot, flavour) outputs and
-//      accumulates 7 FMAs per parton; accumulators go to the gradient with one
+//      accumulates up to 8 FMAs per parton; accumulators go to the gradient with one
 //      atomic per output when the cell changes.
 // Events are processed in chunks so that the scratch stays bounded.
 
 constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;        // partons per warp
 constexpr int kMaxSmemBins = 12 * 1024;
+constexpr int kOut = (kMaxLumiFlav + 1) / 2;   // outputs per lane: flavours lane/16 + 2k
 
 template <bool PATCHES>
 __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
@@ -302,22 +303,22 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
     const int end = (int)min((int64_t)nvalid, beg + kSegment);
     // this lane's outputs: stencil slot s (fixed) and flavours b_k = (lane >> 4) + 2k
     const int s = lane & 15, j = s >> 2, i = s & 3;
-    int bk[7], ak[7];
+    int bk[kOut], ak[kOut];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < kOut; ++k) {
         bk[k] = (lane >> 4) + 2 * k;
         ak[k] = bk[k] < F ? (int)santi[bk[k]] : -1;
     }
-    double acc[7];
+    double acc[kOut];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) acc[k] = 0.0;
+    for (int k = 0; k < kOut; ++k) acc[k] = 0.0;
     int cur = -1;
     auto flush = [&](int cell) {
         int qc = cell / g.nxc, xc = cell - qc * g.nxc;
         int row = g.qrow[qc] - 1 + j, col = xc - 1 + i;
         bool ok = ((g.qmask[qc] >> j) & 1) && col >= 0 && col < g.nx;
 #pragma unroll
-        for (int k = 0; k < 7; ++k) {
+        for (int k = 0; k < kOut; ++k) {
             if (ok && ak[k] >= 0 && (dbits(acc[k]) << 1))
                 atomicAdd(gval + ((size_t)row * g.nx + col) * F + bk[k], scale * acc[k]);
             acc[k] = 0.0;
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
             }
             double wv = sW[wid][q][s];
 #pragma unroll
-            for (int k = 0; k < 7; ++k)
+            for (int k = 0; k < kOut; ++k)
                 if (ak[k] >= 0) acc[k] = fma(wv, sP[wid][q][ak[k]], acc[k]);
         }
         __syncwarp();

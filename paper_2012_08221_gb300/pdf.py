@@ -180,6 +180,16 @@ class PDF:
         check(name, getattr(lib(), name)(self.handle, _ptr(q), n, _ptr(out), _stream(self.device)))
         return out
 
+    def alphasQ2_grad(self, q2, want_value=True):
+        """(alpha_s or None, d alpha_s / d Q^2) at each Q^2."""
+        q2 = _f64_cuda(q2, self.device)
+        n = q2.numel()
+        out = torch.empty(n, dtype=torch.float64, device=self.device) if want_value else None
+        d = torch.empty(n, dtype=torch.float64, device=self.device)
+        check("alphasQ2_grad", lib().alphasQ2_grad(self.handle, _ptr(q2), n, _ptr(out), _ptr(d),
+                                                   _stream(self.device)))
+        return out, d
+
     def xfxQ2_host(self, pids, x, q2, member=0, out=None):
         """End-to-end call on HOST arrays (CPU tensors, pinned for full copy
         speed); returns a CPU tensor ``[n][len(pids)]``."""

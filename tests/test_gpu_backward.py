@@ -181,3 +181,18 @@ def test_full_size_sum_rules(diffgrid):
     Ud, Wd = np.min(np.diff(U)), np.min(np.diff(np.log(g.q_knots ** 2)))
     _check(gx, w[idx] * rdx, np.abs(w[idx]) * 4 * kap / (Ud * x[idx]), "full dL/dx")
     _check(gq, w[idx] * rdq, np.abs(w[idx]) * 4 * kap / (Wd * q2[idx]), "full dL/dQ2")
+
+
+def test_alphas_derivative_and_autograd():
+    from paper_2012_08221_gb300.autograd import alphasQ2
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_nnpdf()
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    q2 = np.exp(np.random.default_rng(50).uniform(math.log(0.1), math.log(1e11), 5000))
+    v, d = pdf.alphasQ2_grad(cuda(q2))
+    ref = np.array([o.alphas_grad(q) for q in q2])
+    assert np.allclose(v.cpu().numpy(), ref[:, 0], rtol=1e-12, atol=0)
+    assert np.allclose(d.cpu().numpy(), ref[:, 1], rtol=1e-9, atol=1e-12 * np.max(np.abs(ref[:, 1])))
+    Q = cuda(q2[:6]).requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda z: alphasQ2(pdf, z), (Q,), eps=1e-6 * float(Q.min()),
+                                    atol=1e-9, rtol=1e-5)

@@ -104,6 +104,27 @@ def test_saved_partner_factors_give_the_same_gradient(lhc):
     assert torch.allclose(ga, gb, rtol=1e-12, atol=1e-15 * float(ga.abs().max()))
 
 
+def test_sixteen_flavours_with_an_unpaired_one(lhc):
+    """The widest luminosity grid (16 flavours: -7..7 and a photon, 22, with
+    no partner): forward and adjoint against the oracle."""
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
+    from paper_2012_08221_gb300.pdf import PDF
+    pids = np.concatenate([np.arange(-7, 8), [22]]).astype(np.int32)
+    g = synth.grid_small(seed=1008, pids=pids)
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    ev = synth.events_lhc(3000, seed=96)
+    dev = DeviceEvents.from_host(ev)
+    L, lum, _ = luminosity(pdf, dev)
+    Lr, lumr, _ = o.lumi(ev)
+    assert np.allclose(lum.cpu().numpy(), lumr, rtol=1e-11, atol=1e-13 * np.max(np.abs(lumr)))
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    luminosity_backward(pdf, dev, 1.0, gv)
+    ref = o.lumi_dgrid(ev)
+    kap = o.lumi_dgrid(ev, absval=True)
+    assert np.all(np.abs(gv.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kap) + 1e-300)
+    assert np.all(gv.cpu().numpy()[:, :, 15] == 0.0)        # the photon has no partner
+
+
 def test_luminosity_autograd(lhc):
     from paper_2012_08221_gb300.autograd import lumi
     from paper_2012_08221_gb300.lumi import DeviceEvents

@@ -383,3 +383,19 @@ def test_golden_tiny_exact_values():
     got = o.xfxq2_batch(g.pids, x, q2)
     assert np.max(np.abs(got - exp)) < 1e-14
     assert np.max(np.abs(o.alphas_batch(q2) - exp_as)) < 1e-15
+
+
+def test_alphas_derivative_against_central_differences(nnpdf):
+    o = orc(nnpdf)
+    W = np.log(nnpdf.q_knots ** 2)
+    rng = np.random.default_rng(60)
+    n_ok = 0
+    while n_ok < 200:
+        w = rng.uniform(W[0] - 2, W[-1] + 2)
+        if np.min(np.abs(W - w)) < 1e-5:
+            continue
+        q2, h = math.exp(w), 1e-7
+        v, d = o.alphas_grad(q2)
+        fd = (o.alphas_q2(q2 * (1 + h)) - o.alphas_q2(q2 * (1 - h))) / (2 * h * q2)
+        assert abs(d - fd) <= 1e-6 * (abs(d) + abs(v) / q2)
+        n_ok += 1
