@@ -115,11 +115,14 @@ __global__ void k_batch(const GridDev *__restrict__ grids, const BatchReq *__res
         const size_t cell_stride = (size_t)g.nflav * 16;
         const double *cm = g.coef + (size_t)sr.member * g.nqc * g.nxc * cell_stride;
         const int64_t p0 = (int64_t)(t - sr.tile0) * ((int64_t)blockDim.x * QPT);
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        double *wbuf = sout + (size_t)wid * 32 * out_stride;
 #pragma unroll 1
         for (int qq = 0; qq < QPT; ++qq) {
-            const int64_t base = p0 + (int64_t)qq * blockDim.x;
+            // this warp's 32 consecutive points of the tile
+            const int64_t base = p0 + (int64_t)qq * blockDim.x + 32 * wid;
             if (base >= n) break;
-            const int64_t i = base + threadIdx.x;
+            const int64_t i = base + lane;
             const bool live = i < n;
             double xi = live ? sr.x[i] : 0.5;
             double qi = live ? sr.q2[i] : 10.0;
@@ -136,18 +139,18 @@ __global__ void k_batch(const GridDev *__restrict__ grids, const BatchReq *__res
             flag_status(g, oor, PDF_S_RANGE);
             bad |= oor;
             const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
-            double *srow = sout + threadIdx.x * npid;
+            double *srow = wbuf + lane * npid;
             for (int a = 0; a < npid; ++a) {
                 int col = sr.cols[a];
                 double v = col >= 0 ? patch(cell + col * 16, X, Q) : 0.0;
                 srow[a] = bad ? qnan() : v;
             }
-            __syncthreads();
-            const int64_t rows = min((int64_t)blockDim.x, n - base);
-            const int64_t cnt = rows * npid;
+            __syncwarp();
+            const int rows = (int)min((int64_t)32, n - base);
+            const int cnt = rows * npid;
             double *dst = sr.out + base * npid;
-            for (int64_t k = threadIdx.x; k < cnt; k += blockDim.x) dst[k] = sout[k];
-            __syncthreads();
+            for (int k = lane; k < cnt; k += 32) dst[k] = wbuf[k];
+            __syncwarp();
         }
         __syncthreads();   // everyone is done with sr/s_tile before thread 0 refills them
     }

@@ -151,7 +151,8 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;        // partons per warp
 constexpr int kMaxSmemBins = 12 * 1024;
-constexpr int kOut = (kMaxLumiFlav + 1) / 2;   // outputs per lane: flavours lane/16 + 2k
+// outputs per lane (flavours lane/16 + 2k): 7 covers up to 14 flavours, 8 up to 16
+constexpr int kOutMax = (kMaxLumiFlav + 1) / 2;
 
 template <bool PATCHES>
 __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
@@ -275,6 +276,7 @@ __device__ __forceinline__ Axis axis_from(int cell, double t, bool in)
     return A;
 }
 
+template <int kOut>
 __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols anti,
                                                                const int *__restrict__ perm,
                                                                const int *__restrict__ offs, int nbins,
@@ -489,8 +491,12 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
         PDF_CUDA(cudaGetLastError());
         int64_t warps = (2 * (int64_t)m + kSegment - 1) / kSegment;
         int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
-        k_lumi_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin, Pc,
-                                                        scale, grad_values);
+        if (g->d.nflav <= 14)
+            k_lumi_accum<7><<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin,
+                                                               Pc, scale, grad_values);
+        else
+            k_lumi_accum<kOutMax><<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq,
+                                                                     fin, Pc, scale, grad_values);
         PDF_CUDA(cudaGetLastError());
     }
     return PDF_OK;
