@@ -45,10 +45,11 @@ def pw_bwd_point_flops() -> int:
     bases), derivative bases (2 multiplies per axis for 2t, 3t^2), patch
     value-derivatives (12 FMA for the x rows, 8 for their tx-derivatives,
     3 + 2 for the tq sums), 2 FMA for the weighted sums, stencil weights of
-    both axes (2 x 12 FMA), 4 + 16 multiplies for the 16 cell weights, and
-    the chain rule to x and Q^2 (2 x 2 multiplies and a reciprocal)."""
+    both axes (2 x 12 FMA), 4 + 16 multiplies for the 16 cell weights, the
+    16 adds that sum them into the gradient of the grid values, and the
+    chain rule to x and Q^2 (2 x 2 multiplies and a reciprocal)."""
     coords = 2 * LOG_FLOPS + 2 * AXIS_FLOPS
-    return coords + 4 + 2 * (12 + 8 + 3 + 2) + 4 + 2 * 2 * 12 + 20 + 2 * 2 + 2 * 4
+    return coords + 4 + 2 * (12 + 8 + 3 + 2) + 4 + 2 * 2 * 12 + 20 + 16 + 2 * 2 + 2 * 4
 
 
 PW_BWD_POINT_BYTES = 44                # grad_out, x, Q^2, pid in; dx, dQ^2 out
