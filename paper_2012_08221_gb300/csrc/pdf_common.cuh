@@ -230,16 +230,29 @@ __device__ __forceinline__ Axis axis_w(const GridDev &g, double w)
     return A;
 }
 
-// 16-coefficient patch contraction: 15 FP64 FMAs.
+// Four consecutive doubles in one 32-byte read-only load (sm_100 and later).
+// The address must be 32-byte aligned: every coefficient block and cell
+// matrix is 128 B long and starts at a multiple of 128 B from a cudaMalloc
+// base.
+struct D4 {
+    double x, y, z, w;
+};
+__device__ __forceinline__ D4 ld4(const double *p)
+{
+    D4 v;
+    asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(v.x), "=d"(v.y), "=d"(v.z), "=d"(v.w) : "l"(p));
+    return v;
+}
+
+// 16-coefficient patch contraction: 15 FP64 FMAs.  C[4n + m] multiplies
+// tx^m tq^n: row n of the block is one 32-byte load.
 __device__ __forceinline__ double patch(const double *__restrict__ C, const Axis &X, const Axis &Q)
 {
-    const double2 *C2 = reinterpret_cast<const double2 *>(C);
-    double2 c0 = __ldg(C2 + 0), c1 = __ldg(C2 + 1), c2 = __ldg(C2 + 2), c3 = __ldg(C2 + 3);
-    double2 c4 = __ldg(C2 + 4), c5 = __ldg(C2 + 5), c6 = __ldg(C2 + 6), c7 = __ldg(C2 + 7);
-    double i0 = fma(X.b3, c1.y, fma(X.b2, c1.x, fma(X.t, c0.y, c0.x)));
-    double i1 = fma(X.b3, c3.y, fma(X.b2, c3.x, fma(X.t, c2.y, c2.x)));
-    double i2 = fma(X.b3, c5.y, fma(X.b2, c5.x, fma(X.t, c4.y, c4.x)));
-    double i3 = fma(X.b3, c7.y, fma(X.b2, c7.x, fma(X.t, c6.y, c6.x)));
+    D4 r0 = ld4(C), r1 = ld4(C + 4), r2 = ld4(C + 8), r3 = ld4(C + 12);
+    double i0 = fma(X.b3, r0.w, fma(X.b2, r0.z, fma(X.t, r0.y, r0.x)));
+    double i1 = fma(X.b3, r1.w, fma(X.b2, r1.z, fma(X.t, r1.y, r1.x)));
+    double i2 = fma(X.b3, r2.w, fma(X.b2, r2.z, fma(X.t, r2.y, r2.x)));
+    double i3 = fma(X.b3, r3.w, fma(X.b2, r3.z, fma(X.t, r3.y, r3.x)));
     return fma(Q.b3, i3, fma(Q.b2, i2, fma(Q.t, i1, i0)));
 }
 
@@ -250,13 +263,12 @@ __device__ __forceinline__ void patch_d(const double *__restrict__ C, const Axis
                                         double dx2, double dx3, double dq2, double dq3,
                                         double *dtx, double *dtq)
 {
-    const double2 *C2 = reinterpret_cast<const double2 *>(C);
     double i[4], j[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
-        double2 a = __ldg(C2 + 2 * n), b = __ldg(C2 + 2 * n + 1);
-        i[n] = fma(X.b3, b.y, fma(X.b2, b.x, fma(X.t, a.y, a.x)));
-        j[n] = fma(dx3, b.y, fma(dx2, b.x, a.y));
+        D4 r = ld4(C + 4 * n);
+        i[n] = fma(X.b3, r.w, fma(X.b2, r.z, fma(X.t, r.y, r.x)));
+        j[n] = fma(dx3, r.w, fma(dx2, r.z, r.y));
     }
     *dtx = fma(Q.b3, j[3], fma(Q.b2, j[2], fma(Q.t, j[1], j[0])));
     *dtq = fma(dq3, i[3], fma(dq2, i[2], i[1]));
@@ -266,15 +278,11 @@ __device__ __forceinline__ void patch_d(const double *__restrict__ C, const Axis
 // outside the knot range the exact weights of the linear continuation.
 __device__ __forceinline__ void stencil_weights(const double *__restrict__ M, const Axis &A, double W[4])
 {
-    const double2 *M2 = reinterpret_cast<const double2 *>(M);
-    double2 r0a = __ldg(M2 + 0), r0b = __ldg(M2 + 1);
-    double2 r1a = __ldg(M2 + 2), r1b = __ldg(M2 + 3);
-    double2 r2a = __ldg(M2 + 4), r2b = __ldg(M2 + 5);
-    double2 r3a = __ldg(M2 + 6), r3b = __ldg(M2 + 7);
-    W[0] = fma(A.b3, r3a.x, fma(A.b2, r2a.x, fma(A.t, r1a.x, r0a.x)));
-    W[1] = fma(A.b3, r3a.y, fma(A.b2, r2a.y, fma(A.t, r1a.y, r0a.y)));
-    W[2] = fma(A.b3, r3b.x, fma(A.b2, r2b.x, fma(A.t, r1b.x, r0b.x)));
-    W[3] = fma(A.b3, r3b.y, fma(A.b2, r2b.y, fma(A.t, r1b.y, r0b.y)));
+    D4 r0 = ld4(M), r1 = ld4(M + 4), r2 = ld4(M + 8), r3 = ld4(M + 12);
+    W[0] = fma(A.b3, r3.x, fma(A.b2, r2.x, fma(A.t, r1.x, r0.x)));
+    W[1] = fma(A.b3, r3.y, fma(A.b2, r2.y, fma(A.t, r1.y, r0.y)));
+    W[2] = fma(A.b3, r3.z, fma(A.b2, r2.z, fma(A.t, r1.z, r0.z)));
+    W[3] = fma(A.b3, r3.w, fma(A.b2, r2.w, fma(A.t, r1.w, r0.w)));
     if (!A.in) {
         // linear continuation: exactly (1 - t, t) on the cell's two knots
         W[0] = 0.0;
