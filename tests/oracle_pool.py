@@ -1,0 +1,36 @@
+"""The oracle spread over the host cores, for full-size parity checks.
+
+Where the oracle sums over many points in one serial loop (the VEGAS sums),
+the points are split into chunks that spawned worker processes evaluate;
+the partial sums are added in chunk order.  Spawned, not forked: the parent
+already holds a CUDA context, which a forked child must not inherit."""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+
+import numpy as np
+
+
+def _vegas_chunk(args):
+    grid_factory, member, ln_tau_min, ln_s, edges, v = args
+    from oracle.oracle import OracleGrid, vegas_sums
+    from paper_2012_08221_gb300 import synth
+    o = OracleGrid.from_synth(getattr(synth, grid_factory)())
+    return vegas_sums(o, member, ln_tau_min, ln_s, edges, v)
+
+
+def workers(limit: int = 16) -> int:
+    return max(1, min(limit, len(os.sched_getaffinity(0))))
+
+
+def vegas_sums_parallel(grid_factory: str, member: int, ln_tau_min: float, ln_s: float,
+                        edges: np.ndarray, v: np.ndarray, n_workers: int | None = None) -> np.ndarray:
+    """``vegas_sums`` of the grid ``synth.<grid_factory>()`` over all of
+    ``v``, chunked over ``n_workers`` processes."""
+    n_workers = n_workers or workers()
+    chunks = np.array_split(np.ascontiguousarray(v), n_workers)
+    jobs = [(grid_factory, member, ln_tau_min, ln_s, edges, c) for c in chunks]
+    with mp.get_context("spawn").Pool(n_workers) as pool:
+        parts = pool.map(_vegas_chunk, jobs)
+    return np.sum(np.stack(parts), axis=0)

@@ -68,3 +68,27 @@ def test_constant_grid_integral_closed_form():
     exact = LN_TAU_MIN ** 2 * g.n_flav * 0.75 ** 2 / 2
     assert abs(res.integral - exact) < 4 * res.error
     assert res.error < 1e-3 * exact
+
+
+def test_full_size_iteration_sums(nn):
+    """One iteration at the benchmark's size and shape (1e7 points, 50 bins
+    per dimension) on adapted edges: every sum against the oracle, which
+    runs on the host cores in chunks (partial sums added in chunk order)."""
+    from paper_2012_08221_gb300.vegas import VegasLumi
+    from tests.oracle_pool import vegas_sums_parallel
+    g, pdf, o = nn
+    n_bins = 50
+    rng = np.random.default_rng(14)
+    # adapted edges from one small oracle iteration and the oracle's refinement
+    edges = np.tile(np.linspace(0.0, 1.0, n_bins + 1), (2, 1))
+    s0 = vegas_sums(o, 0, LN_TAU_MIN, LN_S, edges, rng.uniform(0, 1, (100_000, 2)))
+    for d in range(2):
+        edges[d] = vegas_refine(s0[2 + n_bins * d: 2 + n_bins * (d + 1)], 1.5, edges[d])
+    v = rng.uniform(0, 1, (10_000_000, 2))
+    ref = vegas_sums_parallel("grid_nnpdf", 0, LN_TAU_MIN, LN_S, edges, v)
+    vg = VegasLumi(pdf, LN_TAU_MIN, LN_S, n_bins=n_bins)
+    vg.edges = edges.copy()
+    _, _, s = vg.iteration(torch.as_tensor(v, device="cuda"), refine=False)
+    # 1e7 positive terms per sum, summed in different orders on the two sides
+    assert np.all(np.abs(s - ref) <= 1e-10 * np.abs(ref) + 1e-300), np.max(np.abs(s - ref) / np.abs(ref))
+    assert np.all(ref[2:] > 0.0)
