@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kBlock) k_alphas(GridDev g, const double *__re
         bad |= oor;
         const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
         double2 a01 = __ldg(A), a23 = __ldg(A + 1);
-        double v = fma(Q.b3, a23.y, fma(Q.b2, a23.x, fma(Q.t, a01.y, a01.x)));
+        double v = horner(Q, a01.x, a01.y, a23.x, a23.y);
         out[i] = bad ? qnan() : v;
     }
 }
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) k_alphas_grad(GridDev g, const double 
         bad |= oor;
         const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
         double2 a01 = __ldg(A), a23 = __ldg(A + 1);
-        double v = fma(Q.b3, a23.y, fma(Q.b2, a23.x, fma(Q.t, a01.y, a01.x)));
+        double v = horner(Q, a01.x, a01.y, a23.x, a23.y);
         double d2 = Q.in ? 2.0 * Q.t : 1.0, d3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
         double dt = fma(d3, a23.y, fma(d2, a23.x, a01.y));
         if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dt = 0.0;

@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_lumi(GridDev g, Cols anti, int me
         if (as) {
             const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
             double2 a01 = __ldg(A), a23 = __ldg(A + 1);
-            double v = fma(Q.b3, a23.y, fma(Q.b2, a23.x, fma(Q.t, a01.y, a01.x)));
+            double v = horner(Q, a01.x, a01.y, a23.x, a23.y);
             as[e] = E.bad ? qnan() : v;
         }
     }

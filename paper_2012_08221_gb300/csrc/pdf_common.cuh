@@ -143,6 +143,7 @@ __device__ __forceinline__ int find_cell(const K *keys, int ncell, int step, K k
 struct Axis {
     int cell;
     double t, b2, b3;     // basis (1, t, b2, b3)
+    double h;             // Horner factor: t inside, 1 outside
     bool in;              // inside the knot range
     bool below;           // below the first knot
 };
@@ -160,6 +161,14 @@ __device__ __forceinline__ void make_basis(Axis &A, double t, int extrap)
     double t3 = t2 * t;
     A.b2 = A.in ? t2 : t;
     A.b3 = A.in ? t3 : t;
+    A.h = A.in ? t : 1.0;
+}
+
+// c0 + c1 t + c2 b2 + c3 b3 by Horner's rule, c0 + t (c1 + h (c2 + h c3)):
+// 3 FMAs and no powers of t (outside, h = 1 gives c0 + t (c1 + c2 + c3)).
+__device__ __forceinline__ double horner(const Axis &A, double c0, double c1, double c2, double c3)
+{
+    return fma(A.t, fma(A.h, fma(A.h, c3, c2), c1), c0);
 }
 
 // Domain checks on bit patterns: x in (0, 1], Q^2 in (0, max finite].
@@ -244,16 +253,17 @@ __device__ __forceinline__ D4 ld4(const double *p)
     return v;
 }
 
-// 16-coefficient patch contraction: 15 FP64 FMAs.  C[4n + m] multiplies
-// tx^m tq^n: row n of the block is one 32-byte load.
+// 16-coefficient patch contraction: 15 FP64 FMAs (Horner along x in each
+// row, then along Q).  C[4n + m] multiplies tx^m tq^n: row n of the block is
+// one 32-byte load.
 __device__ __forceinline__ double patch(const double *__restrict__ C, const Axis &X, const Axis &Q)
 {
     D4 r0 = ld4(C), r1 = ld4(C + 4), r2 = ld4(C + 8), r3 = ld4(C + 12);
-    double i0 = fma(X.b3, r0.w, fma(X.b2, r0.z, fma(X.t, r0.y, r0.x)));
-    double i1 = fma(X.b3, r1.w, fma(X.b2, r1.z, fma(X.t, r1.y, r1.x)));
-    double i2 = fma(X.b3, r2.w, fma(X.b2, r2.z, fma(X.t, r2.y, r2.x)));
-    double i3 = fma(X.b3, r3.w, fma(X.b2, r3.z, fma(X.t, r3.y, r3.x)));
-    return fma(Q.b3, i3, fma(Q.b2, i2, fma(Q.t, i1, i0)));
+    double i0 = horner(X, r0.x, r0.y, r0.z, r0.w);
+    double i1 = horner(X, r1.x, r1.y, r1.z, r1.w);
+    double i2 = horner(X, r2.x, r2.y, r2.z, r2.w);
+    double i3 = horner(X, r3.x, r3.y, r3.z, r3.w);
+    return horner(Q, i0, i1, i2, i3);
 }
 
 // Patch value and its derivatives with respect to tx and tq.
