@@ -17,18 +17,35 @@ namespace {
 constexpr int kBlock = 256;
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000000000000ll); }
 
+// Bulk copy (TMA engine) of `bytes` from shared to global memory: both
+// addresses 16-byte aligned, bytes a multiple of 16.  The shared source may be
+// rewritten once bulk_wait_read() has returned in the issuing thread.
+__device__ __forceinline__ void bulk_store(double *dst, const double *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+                 "cp.async.bulk.commit_group;" ::"l"(dst),
+                 "r"((unsigned)__cvta_generic_to_shared(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Orders this thread's shared-memory writes before later bulk copies.
+__device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // One point per thread; each warp takes 32 consecutive points at a time
 // (grid-stride over warps).  A warp's results are staged in its own slice of
-// shared memory and written out as one contiguous, coalesced run of 32 * npid
-// doubles (the output is [n][npid] row-major): only warp-level
-// synchronisation, no block barriers in the loop.
+// shared memory and leave as one contiguous run of 32 * npid doubles (the
+// output is [n][npid] row-major): one bulk copy issued by lane 0 when the run
+// is 16-byte aligned and a multiple of 16 bytes long, else coalesced stores
+// by the whole warp.  Only warp-level synchronisation, no block barriers in
+// the loop.
 template <bool Q_IS_Q>
 __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid, int member,
                                                   const double *__restrict__ x,
                                                   const double *__restrict__ q,
                                                   int64_t n, double *__restrict__ out)
 {
-    extern __shared__ double sout[];
+    extern __shared__ __align__(16) double sout[];
     __shared__ signed char scol[PDF_MAX_PIDS];
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -60,18 +77,27 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         bad |= oor;
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
         double *srow = wbuf + lane * npid;
+        if (lane == 0) bulk_wait_read();      // the previous run has left the slice
+        __syncwarp();
         for (int a = 0; a < npid; ++a) {
             int col = scol[a];
             double v = col >= 0 ? patch(cell + col * 16, X, Q) : 0.0;
             srow[a] = bad ? qnan() : v;
         }
-        __syncwarp();
         const int rows = (int)min((int64_t)32, n - base);
         const int cnt = rows * npid;
         double *dst = out + base * npid;
-        for (int k = lane; k < cnt; k += 32) dst[k] = wbuf[k];
-        __syncwarp();
+        if (((reinterpret_cast<uintptr_t>(dst) | (uintptr_t)(cnt * 8)) & 15) == 0) {
+            fence_smem_to_async();
+            __syncwarp();
+            if (lane == 0) bulk_store(dst, wbuf, (unsigned)cnt * 8u);
+        } else {
+            __syncwarp();
+            for (int k = lane; k < cnt; k += 32) dst[k] = wbuf[k];
+            __syncwarp();
+        }
     }
+    if (lane == 0) bulk_wait_all();
 }
 
 __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
