@@ -172,8 +172,13 @@ int alphasQ2_grad(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, dou
 
 /* End-to-end form of xfxQ2 for HOST buffers: x, q2 HOST [n], out HOST
  * [n][n_pid].  The library streams the points through device staging buffers
- * it owns (chunks overlapped on internal streams), and returns when `out` is
- * complete (synchronous).  Pinned host memory gives full copy bandwidth. */
+ * it owns (chunks of 2^18 points, or $PDFGPU_HOST_CHUNK read at the first
+ * call, overlapped on three internal streams), and returns when `out` is
+ * complete (synchronous).  Pinned host memory gives full copy bandwidth;
+ * pageable memory works.  Calls on the same grid are serialised.  Domain
+ * errors as for xfxQ2 (NaN rows, status bits).  On a failure the copies
+ * already queued are drained before the call returns (nothing writes to
+ * `out` afterwards; `out` is then partly written). */
 int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                const double *x, const double *q2, int64_t n, double *out);
 

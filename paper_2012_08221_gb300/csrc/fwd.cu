@@ -344,17 +344,26 @@ extern "C" int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, 
     }
     for (int s = 0; s < 3; ++s)
         if (!g->hs[s]) PDF_CUDA(cudaStreamCreateWithFlags(&g->hs[s], cudaStreamNonBlocking));
+    // on any failure, copies already queued are drained before returning, so
+    // that none of them touches the caller's buffers after the call
+    auto drain = [&](int code) {
+        for (int s = 0; s < 3; ++s) cudaStreamSynchronize(g->hs[s]);
+        return code;
+    };
     int64_t nchunks = (n + chunk - 1) / chunk;
     for (int64_t c = 0; c < nchunks; ++c) {
         int s = (int)(c % 3);
         cudaStream_t st = g->hs[s];
         int64_t off = c * chunk, m = std::min(chunk, n - off);
-        PDF_CUDA(cudaMemcpyAsync(g->stage[s][0], x + off, m * sizeof(double), cudaMemcpyHostToDevice, st));
-        PDF_CUDA(cudaMemcpyAsync(g->stage[s][1], q2 + off, m * sizeof(double), cudaMemcpyHostToDevice, st));
+        cudaError_t e = cudaMemcpyAsync(g->stage[s][0], x + off, m * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->stage[s][1], q2 + off, m * sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return drain(cuda_fail(e, "host-to-device copy"));
         rc = launch_matrix(g, member, pids, n_pid, g->stage[s][0], g->stage[s][1], m, g->stage[s][2], st, false);
-        if (rc) return rc;
-        PDF_CUDA(cudaMemcpyAsync(out + off * n_pid, g->stage[s][2], m * n_pid * sizeof(double),
-                                 cudaMemcpyDeviceToHost, st));
+        if (rc) return drain(rc);
+        e = cudaMemcpyAsync(out + off * n_pid, g->stage[s][2], m * n_pid * sizeof(double), cudaMemcpyDeviceToHost,
+                            st);
+        if (e != cudaSuccess) return drain(cuda_fail(e, "device-to-host copy"));
     }
     for (int s = 0; s < 3; ++s) PDF_CUDA(cudaStreamSynchronize(g->hs[s]));
     return PDF_OK;

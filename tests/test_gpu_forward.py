@@ -65,6 +65,50 @@ def test_nnpdf_many_tiles_ragged_tail(nnpdf):
     parity.check(got, ref, kap, what="nnpdf xfxQ2")
 
 
+def test_output_alignment_and_odd_runs(nnpdf):
+    """Both exits of the staged output rows give the same values: the bulk
+    copy (16-byte aligned runs of a multiple of 16 bytes) and the warp-wide
+    stores (an output 8 bytes off a 16-byte boundary; the odd-length run of
+    the ragged last warp)."""
+    g, pdf, o = nnpdf
+    x, q2, _ = synth.queries_nnpdf(100_003, seed=31)
+    X, Q = cuda(x), cuda(q2)
+    for pids in (g.pids, g.pids[:3], g.pids[:1]):
+        k = len(pids)
+        aligned = pdf.xfxQ2(pids, X, Q)
+        assert aligned.data_ptr() % 16 == 0
+        buf = torch.empty(x.size * k + 1, dtype=torch.float64, device="cuda")
+        shifted = buf[1:].view(x.size, k)
+        assert shifted.data_ptr() % 16 == 8
+        pdf.xfxQ2(pids, X, Q, out=shifted)
+        assert torch.equal(aligned, shifted)
+        ref = o.xfxq2_batch(pids, x, q2)
+        parity.check(shifted.cpu().numpy(), ref, o.kappa(pids, x, q2), what=f"shifted output, {k} pids")
+
+
+def test_host_buffer_path(nnpdf):
+    """xfxQ2_host, the end-to-end entry point: several chunks through the
+    three staging slots and a ragged last chunk, pinned and pageable host
+    buffers; equal bit for bit to the device-resident call, and to the
+    oracle on a sample; a domain error gives a NaN row and the status bit."""
+    g, pdf, o = nnpdf
+    n = 3 * (1 << 18) + 12_345
+    x, q2, _ = synth.queries_nnpdf(n, seed=33)
+    x[7] = -1.0
+    dev = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu()
+    assert pdf.status() == 1
+    got = pdf.xfxQ2_host(g.pids, torch.as_tensor(x).pin_memory(), torch.as_tensor(q2).pin_memory())
+    assert torch.equal(got[8:], dev[8:]) and torch.equal(got[:7], dev[:7])
+    assert torch.isnan(got[7]).all()
+    assert pdf.status() == 1
+    two = pdf.xfxQ2_host(g.pids[:2], torch.as_tensor(x), torch.as_tensor(q2))
+    assert torch.equal(two[8:], dev[8:, :2])
+    assert pdf.status() == 1
+    idx = np.random.default_rng(33).choice(np.arange(8, n), 2000, replace=False)
+    ref = o.xfxq2_batch(g.pids, x[idx], q2[idx])
+    parity.check(got.numpy()[idx], ref, o.kappa(g.pids, x[idx], q2[idx]), what="xfxQ2_host")
+
+
 def test_nnpdf_full_size_sampled(nnpdf):
     """The full 1e7-point workload in one launch; 3000 sampled points are
     recomputed by the oracle."""
