@@ -41,6 +41,15 @@ MUTANTS = {
 }
 
 
+LUMI_MUTANTS = {
+    "luminosity pairs a with a": ("double f2 = orc_xfxq2_uw(g, member, -pa, u2, w, NULL, NULL);",
+                                  "double f2 = orc_xfxq2_uw(g, member, pa, u2, w, NULL, NULL);"),
+    "second parton's rapidity sign": ("*u2 = h - y;", "*u2 = h + y;"),
+    "tail replaces the wrong parton's x": ("if (flags & 2u) *u1 = ln_x1;", "if (flags & 2u) *u2 = ln_x1;"),
+    "factorisation scale ignores the tail": ("if (flags & 1u) *w = ln_mu2;", "if (flags & 1u) *w = ln_tau + ln_s;"),
+}
+
+
 def build_variant(tmp, text):
     src = os.path.join(tmp, "orc.c")
     with open(src, "w") as f:
@@ -115,4 +124,29 @@ def test_planted_mistake_is_caught(name, tmp_path, swap_oracle):
     assert text.count(old) == 1, f"mutation site not unique: {name}"
     O._lib = build_variant(str(tmp_path), text.replace(old, new))
     assert pin_failures(), f"no pin catches: {name}"
+    shutil.rmtree(tmp_path, ignore_errors=True)
+
+
+def lumi_pin_fails():
+    """The closed-form luminosity pin (flavour-dependent log-bilinear data)."""
+    from tests.closed_forms import bilinear_flavour_grid, luminosity
+    g, params = bilinear_flavour_grid(synth.grid_nnpdf())
+    o = O.OracleGrid.from_synth(g)
+    ev = synth.events_lhc(2000, seed=81, tail=0.3)
+    _, lum, _ = o.lumi(ev)
+    want, mag, _ = luminosity(g.pids, params, ev)
+    return not np.all(np.abs(lum - want) <= 1e-13 * mag + 1e-15)
+
+
+def test_unmodified_oracle_passes_the_luminosity_pin():
+    assert not lumi_pin_fails()
+
+
+@pytest.mark.parametrize("name", sorted(LUMI_MUTANTS))
+def test_planted_luminosity_mistake_is_caught(name, tmp_path, swap_oracle):
+    old, new = LUMI_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    O._lib = build_variant(str(tmp_path), text.replace(old, new))
+    assert lumi_pin_fails(), f"no pin catches: {name}"
     shutil.rmtree(tmp_path, ignore_errors=True)

@@ -354,6 +354,23 @@ def test_luminosity_constant_grid_closed_form(nnpdf):
     assert np.all(np.isfinite(a_s))
 
 
+def test_luminosity_flavour_pairing_and_kinematics_closed_form(nnpdf):
+    """Flavour-dependent log-bilinear data (reproduced exactly inside and
+    outside the grid) make every event's luminosity and alpha_s closed forms
+    of ln x1 = ln tau/2 + y, ln x2 = ln tau/2 - y, ln Q^2 = ln tau + ln s (the
+    injected tail included) and of the pairing a <-> -a (gluon with itself)."""
+    from tests.closed_forms import bilinear_flavour_grid, luminosity
+    g, params = bilinear_flavour_grid(nnpdf)
+    o = orc(g)
+    ev = synth.events_lhc(4000, seed=81, tail=0.3)
+    L, lum, a_s = o.lumi(ev)
+    want, mag, want_as = luminosity(g.pids, params, ev)
+    assert np.all(np.abs(lum - want) <= 1e-13 * mag + 1e-15)
+    assert abs(L - want.mean()) <= 1e-13 * mag.mean()
+    assert np.all(np.abs(a_s - want_as) <= 1e-15)
+    assert np.any(ev.flags & 1) and np.any(ev.flags & 2)
+
+
 def test_luminosity_gradient_central_difference():
     """L is quadratic in the values: a central difference is exact (up to
     rounding) and must equal the oracle's analytic grid gradient."""
