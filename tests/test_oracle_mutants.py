@@ -50,6 +50,14 @@ LUMI_MUTANTS = {
 }
 
 
+VEGAS_MUTANTS = {
+    "VEGAS Jacobian without the bin count": ("jac *= n_bins * width;", "jac *= width;"),
+    "VEGAS bin index off by one": ("int b = (int)vn;", "int b = (int)vn + 1;"),
+    "VEGAS tau mapped the other way": ("double ln_tau = (1.0 - r[0]) * ln_tau_min;",
+                                       "double ln_tau = r[0] * ln_tau_min;"),
+}
+
+
 def build_variant(tmp, text):
     src = os.path.join(tmp, "orc.c")
     with open(src, "w") as f:
@@ -149,4 +157,30 @@ def test_planted_luminosity_mistake_is_caught(name, tmp_path, swap_oracle):
     assert text.count(old) == 1, f"mutation site not unique: {name}"
     O._lib = build_variant(str(tmp_path), text.replace(old, new))
     assert lumi_pin_fails(), f"no pin catches: {name}"
+    shutil.rmtree(tmp_path, ignore_errors=True)
+
+
+def vegas_pins_fail():
+    """The two closed-form VEGAS pins: identity map sample by sample, and a
+    non-uniform map integrated exactly by a midpoint lattice."""
+    from tests import test_oracle_vegas as V
+    try:
+        V.test_identity_map_on_constant_grid_is_the_closed_form()
+        V.test_non_uniform_map_midpoint_rule_is_exact()
+    except AssertionError:
+        return True
+    return False
+
+
+def test_unmodified_oracle_passes_the_vegas_pins():
+    assert not vegas_pins_fail()
+
+
+@pytest.mark.parametrize("name", sorted(VEGAS_MUTANTS))
+def test_planted_vegas_mistake_is_caught(name, tmp_path, swap_oracle):
+    old, new = VEGAS_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    O._lib = build_variant(str(tmp_path), text.replace(old, new))
+    assert vegas_pins_fail(), f"no pin catches: {name}"
     shutil.rmtree(tmp_path, ignore_errors=True)

@@ -71,3 +71,26 @@ def test_adaptation_reduces_the_variance():
         for dmn in range(2):
             edges[dmn] = vegas_refine(s[2 + 30 * dmn: 32 + 30 * dmn], 1.5, edges[dmn])
     assert sig[-1] < 0.7 * sig[0]
+
+
+def test_non_uniform_map_midpoint_rule_is_exact():
+    """On a constant grid the integrand depends on r1 only, linearly, so
+    through any piecewise-linear map the weight w(v) = F(r(v)) J(v) is linear
+    in v inside every bin: a midpoint lattice with a whole number of points
+    per bin integrates it exactly.  With random non-uniform edges the mean
+    weight must equal the integral (ln tau_min)^2 n_pairs c^2 / 2, which pins
+    the bin index, the position inside the bin and the Jacobian."""
+    g = fill(synth.grid_nnpdf(), lambda U, W: 0.75 + 0 * U * W)
+    o = OracleGrid.from_synth(g)
+    nb = 20
+    rng = np.random.default_rng(4)
+    edges = np.stack([np.concatenate([[0.0], np.sort(rng.uniform(0, 1, nb - 1)), [1.0]]) for _ in range(2)])
+    N, M = 5 * nb, 3 * nb
+    v0 = (np.arange(N) + 0.5) / N
+    v1 = (np.arange(M) + 0.5) / M
+    v = np.stack(np.meshgrid(v0, v1, indexing="ij"), axis=-1).reshape(-1, 2)
+    s = vegas_sums(o, 0, LN_TAU_MIN, LN_S, edges, v)
+    per = LN_TAU_MIN ** 2 * g.n_flav * 0.75 ** 2
+    assert abs(s[0] / v.shape[0] - per / 2) <= 1e-12 * per
+    assert abs(s[2:2 + nb].sum() - s[1]) <= 1e-12 * s[1]
+    assert abs(s[2 + nb:].sum() - s[1]) <= 1e-12 * s[1]
