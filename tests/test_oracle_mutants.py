@@ -58,6 +58,16 @@ VEGAS_MUTANTS = {
 }
 
 
+GRAD_MUTANTS = {
+    "chain rule multiplies by x": ("*dx = du / x;", "*dx = du * x;"),
+    "alpha_s derivative left in ln Q^2": ("*dq2 = dw / q2;\n    return v;\n}\n\ndouble orc_alphas(",
+                                          "*dq2 = dw;\n    return v;\n}\n\ndouble orc_alphas("),
+    "indicator scan drops the last stencil knot": (
+        "*c1 = k + 3 > g->n_x - 1 ? g->n_x - 1 : k + 3;", "*c1 = k + 1 > g->n_x - 1 ? g->n_x - 1 : k + 1;"),
+    "grid gradient ignores the point weights": ("double t = gw[i] * wt;", "double t = wt;"),
+}
+
+
 def build_variant(tmp, text):
     src = os.path.join(tmp, "orc.c")
     with open(src, "w") as f:
@@ -183,4 +193,33 @@ def test_planted_vegas_mistake_is_caught(name, tmp_path, swap_oracle):
     assert text.count(old) == 1, f"mutation site not unique: {name}"
     O._lib = build_variant(str(tmp_path), text.replace(old, new))
     assert vegas_pins_fail(), f"no pin catches: {name}"
+    shutil.rmtree(tmp_path, ignore_errors=True)
+
+
+def gradient_pins_fail():
+    """The derivative pins: central differences of x*f and alpha_s, the
+    linear response of one grid value, and the full indicator scan."""
+    from tests import test_oracle_pins as P
+    small, nnpdf = synth.grid_small(), synth.grid_nnpdf()
+    try:
+        P.test_gradients_against_central_differences(small)
+        P.test_grid_gradient_is_linear_response(small)
+        P.test_alphas_derivative_against_central_differences(nnpdf)
+        P.test_window_holds_every_nonzero_weight()
+    except AssertionError:
+        return True
+    return False
+
+
+def test_unmodified_oracle_passes_the_gradient_pins():
+    assert not gradient_pins_fail()
+
+
+@pytest.mark.parametrize("name", sorted(GRAD_MUTANTS))
+def test_planted_gradient_mistake_is_caught(name, tmp_path, swap_oracle):
+    old, new = GRAD_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    O._lib = build_variant(str(tmp_path), text.replace(old, new))
+    assert gradient_pins_fail(), f"no pin catches: {name}"
     shutil.rmtree(tmp_path, ignore_errors=True)
