@@ -259,10 +259,18 @@ class PDF:
         return out
 
 
-def mkPDF(grid, device="cuda:0") -> PDF:
-    """Build a PDF object from an in-memory grid (PDFFlow Sec. 2.1 `mkPDF`;
-    the LHAPDF file loader is not part of this library)."""
-    return PDF.from_grid(grid, device)
+def mkPDF(grid, dirname=None, device="cuda:0", **kw) -> PDF:
+    """Build a PDF object (PDFFlow Sec. 2.1 `mkPDF`): from an in-memory grid,
+    or from member m of an LHAPDF lhagrid1 set named ``"<set>/<m>"`` inside
+    the folder ``dirname`` (``"<set>"`` alone means member 0).  Keyword
+    options (``interp``, ``extrap``) go to ``PDF.from_grid``."""
+    if isinstance(grid, str):
+        import os
+
+        from .lhapdf import load
+        name, _, member = grid.partition("/")
+        return load(os.path.join(dirname or ".", name), first_member=int(member or 0), device=device, **kw)
+    return PDF.from_grid(grid, device, **kw)
 
 
 def fp64_peak() -> float:
