@@ -257,7 +257,8 @@ static int configure(pdfgpu_batch *b, const Shape &s, cudaStream_t st)
                              cudaMemcpyHostToDevice, st));
     KernelFn k = kernel_for(s);
     size_t smem = shape_smem(b, s);
-    PDF_CUDA(cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int rc = allow_dynamic_smem((const void *)k, smem);
+    if (rc) return rc;
     b->ctas = b->sm_count * occupancy((const void *)k, s.block, smem);
     b->smem = smem;
     b->shape = s;
@@ -563,6 +564,8 @@ extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_d
     if (ntiles == 0) return PDF_OK;
     KernelFn k = kernel_for(Shape{block, qpt, 0});
     size_t smem = (size_t)block * out_stride * sizeof(double);
+    int rc = allow_dynamic_smem((const void *)k, smem);
+    if (rc) return rc;
     int sms = 0;
     PDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int ctas = sms * occupancy((const void *)k, block, smem);

@@ -129,7 +129,8 @@ int launch(pdfgpu_grid *g, const Cols &cols, int npid, int member, const int *pi
     size_t gbytes = (size_t)g->d.nrows * g->d.nx * g->d.nflav * sizeof(double);
     if (gval && gbytes <= kSmemGradMax) {
         const void *kern = (const void *)k_bwd<PW, true>;
-        PDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gbytes));
+        int rc = allow_dynamic_smem(kern, gbytes);
+        if (rc) return rc;
         int grid = wave_grid(g, kern, kBlock, gbytes, n);
         k_bwd<PW, true><<<grid, kBlock, gbytes, s>>>(g->d, cols, npid, member, pid, x, q2, n, gout, gx, gq, gval);
     } else {

@@ -17,21 +17,6 @@ namespace {
 constexpr int kBlock = 256;
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000000000000ll); }
 
-// Bulk copy (TMA engine) of `bytes` from shared to global memory: both
-// addresses 16-byte aligned, bytes a multiple of 16.  The shared source may be
-// rewritten once bulk_wait_read() has returned in the issuing thread.
-__device__ __forceinline__ void bulk_store(double *dst, const double *src, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
-                 "cp.async.bulk.commit_group;" ::"l"(dst),
-                 "r"((unsigned)__cvta_generic_to_shared(src)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// Orders this thread's shared-memory writes before later bulk copies.
-__device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // One point per thread; each warp takes 32 consecutive points at a time
 // (grid-stride over warps).  A warp's results are staged in its own slice of
 // shared memory and leave as one contiguous run of 32 * npid doubles (the
@@ -77,25 +62,14 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         bad |= oor;
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
         double *srow = wbuf + lane * npid;
-        if (lane == 0) bulk_wait_read();      // the previous run has left the slice
-        __syncwarp();
+        warp_run_reuse(lane);                 // the previous run has left the slice
         for (int a = 0; a < npid; ++a) {
             int col = scol[a];
             double v = col >= 0 ? patch(cell + col * 16, X, Q) : 0.0;
             srow[a] = bad ? qnan() : v;
         }
         const int rows = (int)min((int64_t)32, n - base);
-        const int cnt = rows * npid;
-        double *dst = out + base * npid;
-        if (((reinterpret_cast<uintptr_t>(dst) | (uintptr_t)(cnt * 8)) & 15) == 0) {
-            fence_smem_to_async();
-            __syncwarp();
-            if (lane == 0) bulk_store(dst, wbuf, (unsigned)cnt * 8u);
-        } else {
-            __syncwarp();
-            for (int k = lane; k < cnt; k += 32) dst[k] = wbuf[k];
-            __syncwarp();
-        }
+        warp_run_store(out + base * npid, wbuf, rows * npid, lane);
     }
     if (lane == 0) bulk_wait_all();
 }
@@ -202,7 +176,8 @@ int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n
     if (!x || !q || !out) return fail(PDF_E_ARG, "null array");
     size_t smem = (size_t)kBlock * n_pid * sizeof(double);
     const void *kern = q_is_q ? (const void *)k_xfxq2<true> : (const void *)k_xfxq2<false>;
-    if (smem > 48 * 1024) PDF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rc = allow_dynamic_smem(kern, smem);
+    if (rc) return rc;
     int grid = wave_grid(g, kern, kBlock, smem, n);
     if (q_is_q)
         k_xfxq2<true><<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out);

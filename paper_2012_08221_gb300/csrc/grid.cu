@@ -8,7 +8,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "pdf_internal.h"
@@ -38,6 +41,22 @@ int occupancy(const void *kernel, int block, size_t smem)
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) n = 1;
     return n < 1 ? 1 : n;
+}
+
+int allow_dynamic_smem(const void *kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return PDF_OK;    // the default limit, never lowered here
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> granted;
+    int dev = 0;
+    PDF_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &have = granted[{dev, kernel}];
+    if (bytes > have) {
+        PDF_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        have = bytes;
+    }
+    return PDF_OK;
 }
 
 int wave_grid(const pdfgpu_grid *g, const void *kernel, int block, size_t smem, int64_t items)

@@ -472,8 +472,8 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     const double scale = dL / (double)n;
     size_t hsmem = nbins <= kMaxSmemBins ? (size_t)nbins * sizeof(int) : 0;
     const void *krec = saved_p ? (const void *)k_lumi_rec<false> : (const void *)k_lumi_rec<true>;
-    if (hsmem > 48 * 1024)
-        PDF_CUDA(cudaFuncSetAttribute(krec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+    rc = allow_dynamic_smem(krec, hsmem);
+    if (rc) return rc;
     for (int64_t e0 = 0; e0 < n; e0 += chunk) {
         const int m = (int)std::min(chunk, n - e0);
         PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));

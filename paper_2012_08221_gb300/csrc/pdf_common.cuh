@@ -302,6 +302,44 @@ __device__ __forceinline__ void stencil_weights(const double *__restrict__ M, co
     }
 }
 
+// Bulk copy (TMA engine) of `bytes` from shared to global memory: both
+// addresses 16-byte aligned, bytes a multiple of 16.  The shared source may be
+// rewritten once bulk_wait_read() has returned in the issuing thread.
+__device__ __forceinline__ void bulk_store(double *dst, const double *src, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n\t"
+                 "cp.async.bulk.commit_group;" ::"l"(dst),
+                 "r"((unsigned)__cvta_generic_to_shared(src)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Orders this thread's shared-memory writes before later bulk copies.
+__device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// A warp's staged run of `cnt` doubles at `wbuf` (shared) goes to `dst`:
+// one bulk copy issued by lane 0 when both ends allow it, else coalesced
+// stores by the whole warp.  The caller has written wbuf (each lane its own
+// rows) and, before rewriting it, calls warp_run_reuse().
+__device__ __forceinline__ void warp_run_store(double *dst, const double *wbuf, int cnt, int lane)
+{
+    if (((reinterpret_cast<uintptr_t>(dst) | (uintptr_t)(cnt * 8)) & 15) == 0) {
+        fence_smem_to_async();
+        __syncwarp();
+        if (lane == 0) bulk_store(dst, wbuf, (unsigned)cnt * 8u);
+    } else {
+        __syncwarp();
+        for (int k = lane; k < cnt; k += 32) dst[k] = wbuf[k];
+        __syncwarp();
+    }
+}
+// The warp's staging slice may be rewritten after this returns.
+__device__ __forceinline__ void warp_run_reuse(int lane)
+{
+    if (lane == 0) bulk_wait_read();
+    __syncwarp();
+}
+
 __device__ __forceinline__ void flag_status(const GridDev &g, bool bad, unsigned bit = PDF_S_DOMAIN)
 {
     unsigned m = __ballot_sync(__activemask(), bad);

@@ -50,6 +50,11 @@ void clear_error();
 // Resident CTAs per SM for a kernel at a block size and dynamic smem.
 int occupancy(const void *kernel, int block, size_t smem);
 
+// Let `kernel` launch with `bytes` of dynamic shared memory on the current
+// device.  Raise-only and serialised: the limit of a kernel is never lowered
+// below what an earlier caller (a prepared batch, another thread) relies on.
+int allow_dynamic_smem(const void *kernel, size_t bytes);
+
 // Grid of a grid-stride launch: enough CTAs for n items, at most one wave.
 int wave_grid(const pdfgpu_grid *g, const void *kernel, int block, size_t smem, int64_t items);
 

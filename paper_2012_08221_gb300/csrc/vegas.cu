@@ -151,8 +151,8 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
     PDF_CUDA(cudaMemsetAsync(sums, 0, (2 + 2 * (size_t)n_bins) * sizeof(double), s));
     if (n == 0) return PDF_OK;
     size_t smem = 2 * (size_t)n_bins * sizeof(double);
-    if (smem > 48 * 1024)
-        PDF_CUDA(cudaFuncSetAttribute((const void *)k_vegas, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    rc = allow_dynamic_smem((const void *)k_vegas, smem);
+    if (rc) return rc;
     int grid = wave_grid(g, (const void *)k_vegas, kBlock, smem, n);
     if (g->partials_cap < 2 * grid) {
         if (g->partials) cudaFree(g->partials);

@@ -76,6 +76,35 @@ def test_noalloc_batch_matches_prepared_batch_twice():
             parity.check(got, ref, np.abs(ref), what=f"no-alloc call {call}")
 
 
+def test_noalloc_after_a_narrower_prepared_batch():
+    """A prepared batch of the same kernel shape whose output rows are
+    narrower (1 pid) must leave the no-alloc launch (3 pids, more shared
+    memory) free to run, in either order."""
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300._lib import lib
+    from paper_2012_08221_gb300.batch import Batch
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    g = synth.grid_nnpdf()
+    pdf = PDF.from_grid(g)
+    dev = torch.device("cuda")
+    x, q2, _ = synth.queries_nnpdf(70_001, seed=91)
+    X, Q = torch.as_tensor(x, device=dev), torch.as_tensor(q2, device=dev)
+    one = np.array([21], dtype=np.int32)
+    three = np.array([-2, 21, 2], dtype=np.int32)
+    narrow = [(pdf, 0, one, X, Q, torch.empty((x.size, 1), dtype=torch.float64, device=dev))]
+    wide = [(pdf, 0, three, X, Q, torch.empty((x.size, 3), dtype=torch.float64, device=dev))]
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    B = Batch(narrow, autotune=False)
+    for _ in range(2):
+        B.run()
+        rc = lib().pdf_batch_run_noalloc(_descs(wide), 1, stream)
+        assert rc == 0, lib().pdf_last_error()
+        torch.cuda.synchronize()
+        assert torch.equal(wide[0][5], pdf.xfxQ2(three, X, Q))
+        assert torch.equal(narrow[0][5], pdf.xfxQ2(one, X, Q))
+
+
 def test_noalloc_batch_rejects_more_requests_than_its_capacity():
     from paper_2012_08221_gb300 import build
     from paper_2012_08221_gb300._lib import BatchDesc, lib
