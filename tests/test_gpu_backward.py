@@ -152,8 +152,9 @@ def test_full_size_sum_rules(diffgrid):
     """Full 1e7 pointwise workload through autograd.  Exact sum rules of the
     grid gradient (the interpolation reproduces constants and functions
     linear in ln x): sum_cells dL/dv[.][a] = sum_{i: a_i = a} w_i and
-    sum_cells U_k dL/dv[.][k][a] = sum_{i: a_i = a} w_i ln x_i; plus sampled
-    dL/dx against the oracle."""
+    sum_cells U_k dL/dv[.][k][a] = sum_{i: a_i = a} w_i ln x_i; the whole grid
+    gradient against the oracle; sampled dL/dx and dL/dQ^2 against the
+    oracle."""
     from paper_2012_08221_gb300.autograd import xfxQ2_pw
     g, pdf, o = diffgrid
     pid, x, q2, w = synth.queries_pointwise()
@@ -173,6 +174,12 @@ def test_full_size_sum_rules(diffgrid):
         s1 = (G[:, :, a] * U[None, :]).sum()
         want1 = (w[m] * np.log(x[m])).sum()
         assert abs(s1 - want1) <= 1e-9 * np.abs(w[m] * np.log(x[m])).sum()
+    # the whole grid gradient against the oracle (run chunked on the host cores)
+    from tests.oracle_pool import dgrid_pw_parallel
+    spec = ("grid_small", {"seed": 1003, "pids": synth.PIDS_13})
+    ref = dgrid_pw_parallel(*spec, pid, x, q2, w)
+    mag = dgrid_pw_parallel(*spec, pid, x, q2, w, absval=True)
+    _check(G, ref, mag, "full-size grid gradient")
     idx = np.random.default_rng(6).choice(x.size, 2000, replace=False)
     rdx, rdq = o.grad_pw(pid[idx], x[idx], q2[idx])
     gx = X.grad[cuda(idx)].cpu().numpy()
