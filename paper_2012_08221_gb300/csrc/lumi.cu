@@ -143,18 +143,18 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 //      and, per parton, its cell key, local coordinates and range flags;
 //      a histogram of the keys;
 //   2. k_scan: bin offsets;  3. k_scatter: parton ids in cell order;
-//   4. k_lumi_accum: each warp walks a run of cell-sorted partons in batches
-//      of 32 (one parton per lane computes its 16 stencil weights into shared
-//      memory), every lane owns fixed (stencil slot, flavour) outputs and
-//      accumulates up to 8 FMAs per parton; accumulators go to the gradient with one
-//      atomic per output when the cell changes.
+//   4. k_lumi_accum: each half-warp walks half of a warp's run of cell-sorted
+//      partons in batches of 16 (one parton per lane computes its 16 stencil
+//      weights and paired partner factors into shared memory); lane s of a
+//      half owns stencil slot s of the current cell for all F flavours and
+//      adds F FMAs per parton (both halves busy: F/2 warp instructions per
+//      parton); accumulators go to the gradient with one atomic per output
+//      when the cell changes.
 // Events are processed in chunks so that the scratch stays bounded.
 
 constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;        // partons per warp
 constexpr int kMaxSmemBins = 12 * 1024;
-// outputs per lane (flavours lane/16 + 2k): 7 covers up to 14 flavours, 8 up to 16
-constexpr int kOutMax = (kMaxLumiFlav + 1) / 2;
 
 template <bool PATCHES>
 __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
@@ -278,7 +278,7 @@ __device__ __forceinline__ Axis axis_from(int cell, double t, bool in)
     return A;
 }
 
-template <int kOut>
+template <int kF>
 __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols anti,
                                                                const int *__restrict__ perm,
                                                                const int *__restrict__ offs, int nbins,
@@ -289,8 +289,11 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
                                                                const double *__restrict__ P, double scale,
                                                                double *__restrict__ gval)
 {
+    // per warp: 32 staged partons (16 per half-warp), their 16 stencil
+    // weights and their partner factors already paired: sP[.][b] is the
+    // partner parton's value of the flavour paired with b (0 if none)
     __shared__ double sW[kAccWarps][32][17];
-    __shared__ double sP[kAccWarps][32][17];
+    __shared__ double sP[kAccWarps][32][kF + 1];
     __shared__ int sK[kAccWarps][32];
     __shared__ signed char santi[PDF_MAX_PIDS];
     if (threadIdx.x == 0) {
@@ -301,36 +304,36 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
     const int F = g.nflav;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nvalid = offs[nbins];
-    const int64_t gw = (int64_t)blockIdx.x * kAccWarps + wid;
-    const int64_t beg = gw * kSegment;
-    if (beg >= nvalid) return;
-    const int end = (int)min((int64_t)nvalid, beg + kSegment);
-    // this lane's outputs: stencil slot s (fixed) and flavours b_k = (lane >> 4) + 2k
-    const int s = lane & 15, j = s >> 2, i = s & 3;
-    int bk[kOut], ak[kOut];
+    const int64_t wbeg = ((int64_t)blockIdx.x * kAccWarps + wid) * kSegment;
+    if (wbeg >= nvalid) return;
+    const int wend = (int)min((int64_t)nvalid, wbeg + kSegment);
+    // the two half-warps walk the two halves of the warp's segment; a lane
+    // owns stencil slot s of its half's current cell for every flavour
+    const int h = lane >> 4, s = lane & 15, j = s >> 2, i = s & 3;
+    const int half = (wend - (int)wbeg + 1) / 2;
+    const int beg = (int)wbeg + h * half;
+    const int end = h ? wend : (int)wbeg + half;
+    const int row0 = h * 16;
+    double acc[kF];
 #pragma unroll
-    for (int k = 0; k < kOut; ++k) {
-        bk[k] = (lane >> 4) + 2 * k;
-        ak[k] = bk[k] < F ? (int)santi[bk[k]] : -1;
-    }
-    double acc[kOut];
-#pragma unroll
-    for (int k = 0; k < kOut; ++k) acc[k] = 0.0;
+    for (int b = 0; b < kF; ++b) acc[b] = 0.0;
     int cur = -1;
     auto flush = [&](int cell) {
         int qc = cell / g.nxc, xc = cell - qc * g.nxc;
         int row = g.qrow[qc] - 1 + j, col = xc - 1 + i;
         bool ok = ((g.qmask[qc] >> j) & 1) && col >= 0 && col < g.nx;
 #pragma unroll
-        for (int k = 0; k < kOut; ++k) {
-            if (ok && ak[k] >= 0 && (dbits(acc[k]) << 1))
-                atomicAdd(gval + ((size_t)row * g.nx + col) * F + bk[k], scale * acc[k]);
-            acc[k] = 0.0;
+        for (int b = 0; b < kF; ++b) {
+            if (ok && b < F && santi[b] >= 0 && (dbits(acc[b]) << 1))
+                atomicAdd(gval + ((size_t)row * g.nx + col) * F + b, scale * acc[b]);
+            acc[b] = 0.0;
         }
     };
-    for (int p = (int)beg; p < end; p += 32) {
-        // one parton per lane: stencil weights and the partner's values
-        int r = p + lane;
+    const int steps = (half + 15) / 16;
+    for (int step = 0; step < steps; ++step) {
+        const int p = beg + step * 16;
+        // one parton per lane: stencil weights and the paired partner factors
+        int r = p + s;
         int kr = -1;
         if (r < end) {
             int rec = perm[r];
@@ -346,23 +349,28 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-                for (int ii = 0; ii < 4; ++ii) sW[wid][lane][jj * 4 + ii] = Wq[jj] * Wx[ii];
+                for (int ii = 0; ii < 4; ++ii) sW[wid][row0 + s][jj * 4 + ii] = Wq[jj] * Wx[ii];
             const double *po = P + (size_t)e * 2 * F + (size_t)(1 - side) * F;
-            for (int a = 0; a < F; ++a) sP[wid][lane][a] = po[a];
-        }
-        sK[wid][lane] = kr;
-        __syncwarp();
-        const int nb = min(32, end - p);
-        for (int q = 0; q < nb; ++q) {
-            int kq = sK[wid][q];
-            if (kq != cur) {
-                if (cur >= 0) flush(cur);
-                cur = kq;
+            for (int b = 0; b < F; ++b) {
+                int a = santi[b];
+                sP[wid][row0 + s][b] = a >= 0 ? po[a] : 0.0;
             }
-            double wv = sW[wid][q][s];
+        }
+        sK[wid][row0 + s] = kr;
+        __syncwarp();
+        const int nb = min(16, end - p);
+        for (int q = 0; q < 16; ++q) {
+            if (q < nb) {
+                int kq = sK[wid][row0 + q];
+                if (kq != cur) {
+                    if (cur >= 0) flush(cur);
+                    cur = kq;
+                }
+                double wv = sW[wid][row0 + q][s];
 #pragma unroll
-            for (int k = 0; k < kOut; ++k)
-                if (ak[k] >= 0) acc[k] = fma(wv, sP[wid][q][ak[k]], acc[k]);
+                for (int b = 0; b < kF; ++b)
+                    if (kF == kMaxLumiFlav ? b < F : true) acc[b] = fma(wv, sP[wid][row0 + q][b], acc[b]);
+            }
         }
         __syncwarp();
     }
@@ -493,12 +501,15 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
         PDF_CUDA(cudaGetLastError());
         int64_t warps = (2 * (int64_t)m + kSegment - 1) / kSegment;
         int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
-        if (g->d.nflav <= 14)
-            k_lumi_accum<7><<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin,
-                                                               Pc, scale, grad_values);
+        if (F == 13)
+            k_lumi_accum<13><<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin,
+                                                                Pc, scale, grad_values);
+        else if (F == 11)
+            k_lumi_accum<11><<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq, fin,
+                                                                Pc, scale, grad_values);
         else
-            k_lumi_accum<kOutMax><<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx, tq,
-                                                                     fin, Pc, scale, grad_values);
+            k_lumi_accum<kMaxLumiFlav><<<blocks, kAccWarps * 32, 0, st>>>(g->d, anti, perm, offs, nbins, key, tx,
+                                                                          tq, fin, Pc, scale, grad_values);
         PDF_CUDA(cudaGetLastError());
     }
     return PDF_OK;

@@ -57,12 +57,19 @@ def test_small_grid_full_workload(small):
 
 
 def test_nnpdf_many_tiles_ragged_tail(nnpdf):
+    """Also counts the outputs that a plain 1e-12 relative test (no kappa)
+    would reject: values that nearly cancel, where the two sides' rounding
+    orders differ on the scale of the terms, not of the result."""
     g, pdf, o = nnpdf
     x, q2, _ = synth.queries_nnpdf(300_001, seed=12)
     got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
     ref = o.xfxq2_batch(g.pids, x, q2)
     kap = o.kappa(g.pids, x, q2)
-    parity.check(got, ref, kap, what="nnpdf xfxQ2")
+    worst = parity.check(got, ref, kap, what="nnpdf xfxQ2")
+    strict = parity.strict_count(got, ref)
+    print(f"\nnnpdf xfxQ2: worst error / scale {worst:.2e}; "
+          f"plain 1e-12 relative test would reject {strict} of {ref.size}")
+    assert strict <= 1e-4 * ref.size
 
 
 def test_output_alignment_and_odd_runs(nnpdf):
