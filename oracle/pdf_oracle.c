@@ -34,7 +34,7 @@
  *      interpolated in w; in w from the first (last) two rows of the lowest
  *      (highest) subgrid, each first interpolated (or continued) in u.
  *   7. alpha_s: step 5 then steps 2-3 in w on the alpha_s knot values, and
- *      step 6's linear continuation at both ends.
+ *      step 6 at both ends (or the grid's extrapolation option below).
  *   8. Derivatives: d/du and d/dw of the same piecewise polynomial; the
  *      derivative with respect to one grid value is the interpolation of the
  *      indicator grid of that value (the result is linear in the values).
@@ -42,7 +42,14 @@
  *   between the two interval knots on both axes), or log-bicubic with
  *   straight lines on any axis or subgrid of fewer than 4 knots; outside the
  *   grid, the value frozen at the nearest edge (u and w clamped into the
- *   knot range, zero derivative across the edge), or NaN.
+ *   knot range, zero derivative across the edge), NaN, or an LHAPDF-style
+ *   continuation: from the same two values as step 6, y0 and y1 at the lower
+ *   and upper knot of the edge interval, with t the position in that interval
+ *   (t < 0 below the grid, t > 1 above), the power law y0^(1-t) y1^t in the
+ *   log coordinate when both values exceed 1e-3, else step 6's straight line
+ *   (sign-safe: no logarithm of a value that is not clearly positive).  The w
+ *   direction is continued first (per edge column when u is out of range
+ *   too), then u.
  *
  * Built with -O2 -ffp-contract=off (no fused multiply-add contraction, no
  * fast-math), parallelised over points with OpenMP in the batch drivers only.
@@ -71,7 +78,8 @@ typedef struct {
     int interp;              /* 0 log-bicubic, 1 log-bilinear, 2 log-bicubic
                                 with linear axes that have fewer than 4 knots */
     int extrap;              /* outside the grid: 0 linear continuation,
-                                1 freeze at the edge, 2 NaN                */
+                                1 freeze at the edge, 2 NaN, 3 power-law
+                                continuation (linear where not positive)   */
 } orc_grid;
 
 int orc_init(orc_grid *g)
@@ -141,6 +149,29 @@ static int interval(const double *z, int n, double v)
     return k;
 }
 
+/* Step 6 with option 3: continuation from y0 and y1, the values at the
+ * lower and upper knot of the edge interval of width dz, to the offset off
+ * from the lower knot (t = off / dz).  A power law y0^(1-t) y1^t when both
+ * values exceed CONT_MIN, else step 6's straight line (the same expression).
+ * *doff gets dy/d(off), *d0 and *d1 get dy/dy0 and dy/dy1. */
+#define CONT_MIN 1e-3
+static double cont(double y0, double y1, double off, double dz, double *doff, double *d0, double *d1)
+{
+    double t = off / dz;
+    if (y0 > CONT_MIN && y1 > CONT_MIN) {
+        double lr = log(y1 / y0);
+        double y = y0 * exp(t * lr);
+        *doff = y * lr / dz;
+        *d0 = y * (1.0 - t) / y0;
+        *d1 = y * t / y1;
+        return y;
+    }
+    *doff = (y1 - y0) / dz;
+    *d0 = 1.0 - t;
+    *d1 = t;
+    return y0 + off * (y1 - y0) / dz;
+}
+
 /* How one Q row is reduced to a number: Hermite in u, or one x column. */
 typedef struct {
     int column;    /* >= 0: take this x column as is                 */
@@ -193,6 +224,13 @@ static double wdir(const acc_t *a, const xsel_t *xs, double w, double *dw, doubl
         double B0 = xrow(a, r0, xs, &du0), B1 = xrow(a, r0 + 1, xs, &du1);
         double dz = W[r0 + 1] - W[r0];
         double t = (w - W[r0]) / dz;
+        if (g->extrap == 3) {
+            double doff, d0, d1;
+            double y = cont(B0, B1, w - W[r0], dz, &doff, &d0, &d1);
+            if (dw) *dw = doff;
+            if (du) *du = d0 * du0 + d1 * du1;
+            return y;
+        }
         if (dw) *dw = (B1 - B0) / dz;
         if (du) *du = du0 + t * (du1 - du0);
         return B0 + (w - W[r0]) * (B1 - B0) / dz;
@@ -254,6 +292,13 @@ static double eval_uw(const acc_t *a, double u, double w, double *du, double *dw
         double dw0, dw1;
         double A0 = wdir(a, &c0, w, &dw0, NULL), A1 = wdir(a, &c1, w, &dw1, NULL);
         double dz = U[k0 + 1] - U[k0];
+        if (g->extrap == 3) {
+            double doff, d0, d1;
+            double y = cont(A0, A1, u - U[k0], dz, &doff, &d0, &d1);
+            if (du) *du = doff;
+            if (dw) *dw = d0 * dw0 + d1 * dw1;
+            return y;
+        }
         if (du) *du = (A1 - A0) / dz;
         if (dw) *dw = dw0 + (u - U[k0]) / dz * (dw1 - dw0);
         return A0 + (u - U[k0]) * (A1 - A0) / dz;

@@ -68,6 +68,16 @@ GRAD_MUTANTS = {
 }
 
 
+CONT_MUTANTS = {
+    "continuation anchored at the wrong knot": ("double y = y0 * exp(t * lr);", "double y = y1 * exp(t * lr);"),
+    "continuation threshold on one value only": ("if (y0 > CONT_MIN && y1 > CONT_MIN) {",
+                                                 "if (y0 > CONT_MIN) {"),
+    "corners continued by a straight line in u": (
+        "double A0 = wdir(a, &c0, w, &dw0, NULL), A1 = wdir(a, &c1, w, &dw1, NULL);\n        double dz = U[k0 + 1] - U[k0];\n        if (g->extrap == 3) {",
+        "double A0 = wdir(a, &c0, w, &dw0, NULL), A1 = wdir(a, &c1, w, &dw1, NULL);\n        double dz = U[k0 + 1] - U[k0];\n        if (g->extrap == 3 && w >= g->W[0] && w <= g->W[g->rows - 1]) {"),
+}
+
+
 def build_variant(tmp, text):
     src = os.path.join(tmp, "orc.c")
     with open(src, "w") as f:
@@ -222,4 +232,28 @@ def test_planted_gradient_mistake_is_caught(name, tmp_path, swap_oracle):
     assert text.count(old) == 1, f"mutation site not unique: {name}"
     O._lib = build_variant(str(tmp_path), text.replace(old, new))
     assert gradient_pins_fail(), f"no pin catches: {name}"
+    shutil.rmtree(tmp_path, ignore_errors=True)
+
+
+def continuation_pins_fail():
+    from tests import test_oracle_modes as M
+    try:
+        M.test_continuation_reproduces_power_laws_outside()
+        M.test_continuation_inside_equals_linear_and_falls_back_where_not_positive()
+    except AssertionError:
+        return True
+    return False
+
+
+def test_unmodified_oracle_passes_the_continuation_pins():
+    assert not continuation_pins_fail()
+
+
+@pytest.mark.parametrize("name", sorted(CONT_MUTANTS))
+def test_planted_continuation_mistake_is_caught(name, tmp_path, swap_oracle):
+    old, new = CONT_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    O._lib = build_variant(str(tmp_path), text.replace(old, new))
+    assert continuation_pins_fail(), f"no pin catches: {name}"
     shutil.rmtree(tmp_path, ignore_errors=True)
