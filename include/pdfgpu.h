@@ -81,14 +81,23 @@ enum {
 };
 
 /* Extrapolation outside the knot range (pdfgpu_grid_desc.extrap):
- *   LINEAR  continue linearly in ln x / ln Q^2 from the two edge knots
- *   FREEZE  the value at the nearest edge of the grid (zero derivative
- *           across the edge)
- *   ERROR   NaN and the PDF_S_RANGE status bit                            */
+ *   LINEAR        continue linearly in ln x / ln Q^2 from the two edge knots
+ *   FREEZE        the value at the nearest edge of the grid (zero derivative
+ *                 across the edge)
+ *   ERROR         NaN and the PDF_S_RANGE status bit
+ *   CONTINUATION  LHAPDF-style power law from the same two edge values y0, y1
+ *                 (lower and upper knot of the edge interval, t the position
+ *                 in it): y0^(1-t) y1^t when both exceed 1e-3, else the
+ *                 LINEAR value (sign-safe); ln Q^2 is continued first (per
+ *                 edge x column in the corners), then ln x.  The result is
+ *                 not linear in the grid values: the adjoint entry points
+ *                 (xfxQ2_backward, pdf_lumi_backward) return PDF_E_ARG for
+ *                 such a grid; alphasQ2_grad supports it.                */
 enum {
     PDF_EXTRAP_LINEAR = 0,
     PDF_EXTRAP_FREEZE = 1,
-    PDF_EXTRAP_ERROR = 2
+    PDF_EXTRAP_ERROR = 2,
+    PDF_EXTRAP_CONTINUATION = 3
 };
 
 #define PDF_MAX_PIDS 64   /* flavours per matrix-form call                  */
@@ -107,7 +116,7 @@ enum {
  *   interp                 PDF_INTERP_* (0: log-bicubic); alpha_s follows the
  *                          same kind along ln Q^2
  *   extrap                 PDF_EXTRAP_* (0: linear continuation), also for
- *                          alpha_s                                           */
+ *                          alpha_s (which continues by the same rule)        */
 typedef struct {
     int32_t n_x;
     const double *x_knots;
@@ -190,7 +199,8 @@ int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_p
  *   grad_q2 DEVICE [n] or NULL: dL/dQ^2_i    (overwritten)
  *   grad_values DEVICE [n_rows][n_x][n_flav] of `member`, or NULL: dL/dvalues,
  *     ACCUMULATED (+=) with FP64 atomics (summation order is not fixed).
- * Domain errors give NaN in grad_x / grad_q2 and add nothing to grad_values. */
+ * Domain errors give NaN in grad_x / grad_q2 and add nothing to grad_values.
+ * PDF_E_ARG for a grid loaded with PDF_EXTRAP_CONTINUATION. */
 int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                    int32_t pointwise, const double *x, const double *q2, int64_t n,
                    const double *grad_out, double *grad_x, double *grad_q2,
@@ -277,7 +287,8 @@ int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double
  * recompute those values.  Events with a domain error add nothing.  Uses
  * library-owned scratch of the grid handle (allocated on first use, about
  * 0.3 KB per event for up to 8.4e6 events per chunk, or 40 B per event when
- * saved_p is given): calls on the same grid must not overlap in time. */
+ * saved_p is given): calls on the same grid must not overlap in time.
+ * PDF_E_ARG for a grid loaded with PDF_EXTRAP_CONTINUATION. */
 int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double *y,
                       const uint8_t *flags, const double *ln_mu2, const double *ln_x1,
                       double ln_s, int64_t n, double dL, const double *saved_p,

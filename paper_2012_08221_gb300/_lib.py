@@ -26,7 +26,7 @@ PDF_MAX_PIDS = 64
 PDF_S_DOMAIN = 1
 PDF_S_RANGE = 2
 INTERP = {"logbicubic": 0, "logbilinear": 1, "logbicubic_small_linear": 2}
-EXTRAP = {"linear": 0, "freeze": 1, "error": 2}
+EXTRAP = {"linear": 0, "freeze": 1, "error": 2, "continuation": 3}
 ERRORS = {-1: "PDF_E_ARG", -2: "PDF_E_DESC", -3: "PDF_E_CUDA", -4: "PDF_E_UNBOUND",
           -5: "PDF_E_NOMEM", -6: "PDF_E_RANGE"}
 

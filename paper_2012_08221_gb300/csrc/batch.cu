@@ -54,7 +54,7 @@ struct StageTables {
     double2 qcell[kStageQ];
 };
 
-template <int QPT, bool STAGE>
+template <int QPT, bool STAGE, bool CONT>
 __global__ void k_batch(const GridDev *__restrict__ grids, const BatchReq *__restrict__ reqs, int nreq,
                         int64_t ntiles, unsigned long long *ticket, int out_stride)
 {
@@ -142,7 +142,7 @@ __global__ void k_batch(const GridDev *__restrict__ grids, const BatchReq *__res
             double *srow = wbuf + lane * npid;
             for (int a = 0; a < npid; ++a) {
                 int col = sr.cols[a];
-                double v = col >= 0 ? patch(cell + col * 16, X, Q) : 0.0;
+                double v = col >= 0 ? patch_any<CONT>(g, cell + col * 16, X, Q) : 0.0;
                 srow[a] = bad ? qnan() : v;
             }
             __syncwarp();
@@ -162,17 +162,21 @@ struct Shape {
 
 using KernelFn = void (*)(const GridDev *, const BatchReq *, int, int64_t, unsigned long long *, int);
 
-KernelFn kernel_for(const Shape &s)
+template <bool CONT>
+KernelFn kernel_for_t(const Shape &s)
 {
     if (s.stage) {
-        if (s.qpt == 1) return k_batch<1, true>;
-        if (s.qpt == 2) return k_batch<2, true>;
-        return k_batch<4, true>;
+        if (s.qpt == 1) return k_batch<1, true, CONT>;
+        if (s.qpt == 2) return k_batch<2, true, CONT>;
+        return k_batch<4, true, CONT>;
     }
-    if (s.qpt == 1) return k_batch<1, false>;
-    if (s.qpt == 2) return k_batch<2, false>;
-    return k_batch<4, false>;
+    if (s.qpt == 1) return k_batch<1, false, CONT>;
+    if (s.qpt == 2) return k_batch<2, false, CONT>;
+    return k_batch<4, false, CONT>;
 }
+
+// `cont`: some grid of the launch uses the continuation extrapolation.
+KernelFn kernel_for(const Shape &s, bool cont) { return cont ? kernel_for_t<true>(s) : kernel_for_t<false>(s); }
 
 // ---------------------------------------------------------- tune cache (JSON)
 // One entry per line: "signature": {"block": B, "qpt": Q, "stage": S, "ms": T}
@@ -231,6 +235,7 @@ struct pdfgpu_batch {
     int out_stride = 1;
     int64_t ntiles = 0;
     Shape shape{256, 2, 1};
+    bool cont = false;                  // some grid uses the continuation extrapolation
     int ctas = 0;
     size_t smem = 0;
     float tuned_ms = 0;
@@ -255,7 +260,7 @@ static int configure(pdfgpu_batch *b, const Shape &s, cudaStream_t st)
     b->ntiles = acc;
     PDF_CUDA(cudaMemcpyAsync(b->d_reqs, b->host_reqs.data(), b->host_reqs.size() * sizeof(BatchReq),
                              cudaMemcpyHostToDevice, st));
-    KernelFn k = kernel_for(s);
+    KernelFn k = kernel_for(s, b->cont);
     size_t smem = shape_smem(b, s);
     int rc = allow_dynamic_smem((const void *)k, smem);
     if (rc) return rc;
@@ -268,7 +273,7 @@ static int configure(pdfgpu_batch *b, const Shape &s, cudaStream_t st)
 static int enqueue(pdfgpu_batch *b, cudaStream_t st)
 {
     PDF_CUDA(cudaMemsetAsync(b->d_ticket, 0, sizeof(unsigned long long), st));
-    KernelFn k = kernel_for(b->shape);
+    KernelFn k = kernel_for(b->shape, b->cont);
     k<<<b->ctas, b->shape.block, b->smem, st>>>(b->d_grids, b->d_reqs, b->nreq, b->ntiles, b->d_ticket,
                                                  b->out_stride);
     PDF_CUDA(cudaGetLastError());
@@ -330,6 +335,7 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
             gi = (int)b->grid_handles.size();
             b->grid_handles.push_back(D.grid);
             gd.push_back(D.grid->d);
+            if (D.grid->d.extrap == PDF_EXTRAP_CONTINUATION) b->cont = true;
         }
         Cols cols;
         int rc2 = resolve_cols(D.grid, D.pids, D.n_pid, &cols);
@@ -507,6 +513,7 @@ extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_d
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     NoAllocScratch &H = g_noalloc_host;
     int ngrids = 0;
+    bool cont = false;                  // some grid uses the continuation extrapolation
     pdfgpu_grid_t handles[kNoAllocMaxGrids];
     int out_stride = 1;
     const int block = 256, qpt = 2;
@@ -528,6 +535,7 @@ extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_d
                 return fail(PDF_E_RANGE, "pdf_batch_run_noalloc takes at most 32 distinct grids");
             gi = ngrids++;
             handles[gi] = D.grid;
+            if (D.grid->d.extrap == PDF_EXTRAP_CONTINUATION) cont = true;
             H.grids[gi] = D.grid->d;
         }
         Cols cols;
@@ -562,7 +570,7 @@ extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_d
     size_t bytes = offsetof(NoAllocScratch, reqs) + (size_t)n_desc * sizeof(BatchReq);
     PDF_CUDA(cudaMemcpyAsync(S, &H, bytes, cudaMemcpyHostToDevice, st));
     if (ntiles == 0) return PDF_OK;
-    KernelFn k = kernel_for(Shape{block, qpt, 0});
+    KernelFn k = kernel_for(Shape{block, qpt, 0}, cont);
     size_t smem = (size_t)block * out_stride * sizeof(double);
     int rc = allow_dynamic_smem((const void *)k, smem);
     if (rc) return rc;

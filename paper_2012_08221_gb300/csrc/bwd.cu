@@ -152,6 +152,9 @@ extern "C" int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pi
     clear_error();
     int rc = check_grid(g, true);
     if (rc) return rc;
+    if (g->d.extrap == PDF_EXTRAP_CONTINUATION)
+        return fail(PDF_E_ARG, "the adjoint needs linear, freeze or error extrapolation (continuation is not linear "
+                               "in the grid values)");
     if (n < 0) return fail(PDF_E_ARG, "negative n");
     if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
     Cols cols;

@@ -24,7 +24,7 @@ __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000
 // is 16-byte aligned and a multiple of 16 bytes long, else coalesced stores
 // by the whole warp.  Only warp-level synchronisation, no block barriers in
 // the loop.
-template <bool Q_IS_Q>
+template <bool Q_IS_Q, bool CONT>
 __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid, int member,
                                                   const double *__restrict__ x,
                                                   const double *__restrict__ q,
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         warp_run_reuse(lane);                 // the previous run has left the slice
         for (int a = 0; a < npid; ++a) {
             int col = scol[a];
-            double v = col >= 0 ? patch(cell + col * 16, X, Q) : 0.0;
+            double v = col >= 0 ? patch_any<CONT>(g, cell + col * 16, X, Q) : 0.0;
             srow[a] = bad ? qnan() : v;
         }
         const int rows = (int)min((int64_t)32, n - base);
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
     if (lane == 0) bulk_wait_all();
 }
 
+template <bool CONT>
 __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
                                                      const int *__restrict__ pid,
                                                      const double *__restrict__ x,
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
         double v = 0.0;
-        if (col >= 0) v = patch(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
+        if (col >= 0) v = patch_any<CONT>(g, cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
         out[i] = bad ? qnan() : v;
     }
 }
@@ -120,9 +121,7 @@ __global__ void __launch_bounds__(kBlock) k_alphas(GridDev g, const double *__re
         const bool oor = g.extrap == PDF_EXTRAP_ERROR && !Q.in;
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
-        const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
-        double2 a01 = __ldg(A), a23 = __ldg(A + 1);
-        double v = horner(Q, a01.x, a01.y, a23.x, a23.y);
+        double v = alphas_any(g, ld4(g.acoef + (size_t)Q.cell * 4), Q);
         out[i] = bad ? qnan() : v;
     }
 }
@@ -142,12 +141,16 @@ __global__ void __launch_bounds__(kBlock) k_alphas_grad(GridDev g, const double 
         const bool oor = g.extrap == PDF_EXTRAP_ERROR && !Q.in;
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
-        const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
-        double2 a01 = __ldg(A), a23 = __ldg(A + 1);
-        double v = horner(Q, a01.x, a01.y, a23.x, a23.y);
+        const D4 a = ld4(g.acoef + (size_t)Q.cell * 4);
+        double v = alphas_any(g, a, Q);
         double d2 = Q.in ? 2.0 * Q.t : 1.0, d3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
-        double dt = fma(d3, a23.y, fma(d2, a23.x, a01.y));
+        double dt = fma(d3, a.w, fma(d2, a.z, a.y));
         if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dt = 0.0;
+        if (!Q.in && g.extrap == PDF_EXTRAP_CONTINUATION) {
+            // d/dt of the continuation from the edge values y0 = a(0), y1 = a(1)
+            const double y0 = a.x, y1 = a.x + a.y + a.z + a.w;
+            dt = (y0 > kContMin && y1 > kContMin) ? v * log(y1 / y0) : y1 - y0;
+        }
         if (out) out[i] = bad ? qnan() : v;
         dq2[i] = bad ? qnan() : dt * g.qcell[Q.cell].y * __drcp_rn(qi);
     }
@@ -175,14 +178,14 @@ int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n
     if (n == 0) return PDF_OK;
     if (!x || !q || !out) return fail(PDF_E_ARG, "null array");
     size_t smem = (size_t)kBlock * n_pid * sizeof(double);
-    const void *kern = q_is_q ? (const void *)k_xfxq2<true> : (const void *)k_xfxq2<false>;
-    rc = allow_dynamic_smem(kern, smem);
+    using Kern = void (*)(GridDev, Cols, int, int, const double *, const double *, int64_t, double *);
+    const bool cont = g->d.extrap == PDF_EXTRAP_CONTINUATION;
+    Kern k = q_is_q ? (cont ? k_xfxq2<true, true> : k_xfxq2<true, false>)
+                    : (cont ? k_xfxq2<false, true> : k_xfxq2<false, false>);
+    rc = allow_dynamic_smem((const void *)k, smem);
     if (rc) return rc;
-    int grid = wave_grid(g, kern, kBlock, smem, n);
-    if (q_is_q)
-        k_xfxq2<true><<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out);
-    else
-        k_xfxq2<false><<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out);
+    int grid = wave_grid(g, (const void *)k, kBlock, smem, n);
+    k<<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
@@ -230,8 +233,9 @@ extern "C" int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, con
     if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
     if (n == 0) return PDF_OK;
     if (!pid || !x || !q2 || !out) return fail(PDF_E_ARG, "null array");
-    int grid = wave_grid(g, (const void *)k_xfxq2_pw, kBlock, 0, n);
-    k_xfxq2_pw<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, member, pid, x, q2, n, out);
+    auto k = g->d.extrap == PDF_EXTRAP_CONTINUATION ? k_xfxq2_pw<true> : k_xfxq2_pw<false>;
+    int grid = wave_grid(g, (const void *)k, kBlock, 0, n);
+    k<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, member, pid, x, q2, n, out);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }

@@ -260,7 +260,7 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     if (D.n_members < 1) return fail(PDF_E_DESC, "need at least 1 member");
     if (D.interp < PDF_INTERP_LOGBICUBIC || D.interp > PDF_INTERP_LOGBICUBIC_SMALL_LINEAR)
         return fail(PDF_E_DESC, "unknown interpolation kind");
-    if (D.extrap < PDF_EXTRAP_LINEAR || D.extrap > PDF_EXTRAP_ERROR)
+    if (D.extrap < PDF_EXTRAP_LINEAR || D.extrap > PDF_EXTRAP_CONTINUATION)
         return fail(PDF_E_DESC, "unknown extrapolation mode");
     for (int k = 0; k < D.n_x; ++k) {
         double x = D.x_knots[k];

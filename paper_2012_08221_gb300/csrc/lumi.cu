@@ -50,7 +50,7 @@ __device__ __forceinline__ Event event(int64_t e, const double *ln_tau, const do
 
 // At most 64 registers (4 CTAs per SM): with the 32-byte coefficient loads
 // the unbounded build takes 80 and runs 1 % slower at 3 CTAs per SM.
-template <bool SAVE>
+template <bool SAVE, bool CONT>
 __global__ void __launch_bounds__(kBlock, 4) k_lumi(GridDev g, Cols anti, int member,
                                                     const double *__restrict__ ln_tau,
                                                     const double *__restrict__ y,
@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(kBlock, 4) k_lumi(GridDev g, Cols anti, int me
         for (int a = 0; a < g.nflav; ++a) {
             int b = santi[a];
             if (b < 0) continue;
-            double p1 = patch(c1 + a * 16, X1, Q);
-            double p2 = patch(c2 + b * 16, X2, Q);
+            double p1 = patch_any<CONT>(g, c1 + a * 16, X1, Q);
+            double p2 = patch_any<CONT>(g, c2 + b * 16, X2, Q);
             s = fma(p1, p2, s);
             if (SAVE) {
                 // the partner factors the adjoint needs: [event][parton][flavour]
@@ -101,9 +101,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_lumi(GridDev g, Cols anti, int me
         if (lum) lum[e] = s;
         acc += s;
         if (as) {
-            const double2 *A = reinterpret_cast<const double2 *>(g.acoef + (size_t)Q.cell * 4);
-            double2 a01 = __ldg(A), a23 = __ldg(A + 1);
-            double v = horner(Q, a01.x, a01.y, a23.x, a23.y);
+            double v = alphas_any(g, ld4(g.acoef + (size_t)Q.cell * 4), Q);
             as[e] = E.bad ? qnan() : v;
         }
     }
@@ -413,8 +411,12 @@ extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, c
         return PDF_OK;
     }
     if (alphas && !g->has_alphas) alphas = nullptr;
-    const void *kern = save_p ? (const void *)k_lumi<true> : (const void *)k_lumi<false>;
-    int grid = wave_grid(g, kern, kBlock, 0, n);
+    using Kern = void (*)(GridDev, Cols, int, const double *, const double *, const uint8_t *, const double *,
+                          const double *, double, int64_t, double *, double *, double *, double *);
+    const bool cont = g->d.extrap == PDF_EXTRAP_CONTINUATION;
+    Kern k = save_p ? (cont ? k_lumi<true, true> : k_lumi<true, false>)
+                    : (cont ? k_lumi<false, true> : k_lumi<false, false>);
+    int grid = wave_grid(g, (const void *)k, kBlock, 0, n);
     if (g->partials_cap < grid) {
         if (g->partials) cudaFree(g->partials);
         g->partials = nullptr;
@@ -422,12 +424,8 @@ extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, c
         PDF_CUDA(cudaMalloc(&g->partials, (size_t)grid * sizeof(double)));
         g->partials_cap = grid;
     }
-    if (save_p)
-        k_lumi<true><<<grid, kBlock, 0, s>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, n, lum,
-                                             alphas, g->partials, save_p);
-    else
-        k_lumi<false><<<grid, kBlock, 0, s>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, n,
-                                              lum, alphas, g->partials, nullptr);
+    k<<<grid, kBlock, 0, s>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, n, lum, alphas,
+                              g->partials, save_p);
     PDF_CUDA(cudaGetLastError());
     k_lumi_final<<<1, 256, 0, s>>>(g->partials, grid, 1.0 / (double)n, L);
     PDF_CUDA(cudaGetLastError());
@@ -443,6 +441,9 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     Cols anti;
     int rc = lumi_common(g, member, ln_tau, y, n, &anti);
     if (rc) return rc;
+    if (g->d.extrap == PDF_EXTRAP_CONTINUATION)
+        return fail(PDF_E_ARG, "the adjoint needs linear, freeze or error extrapolation (continuation is not linear "
+                               "in the grid values)");
     if (!grad_values) return fail(PDF_E_ARG, "null grad_values");
     if (n == 0) return PDF_OK;
     cudaStream_t st = (cudaStream_t)stream;

@@ -266,6 +266,65 @@ __device__ __forceinline__ double patch(const double *__restrict__ C, const Axis
     return horner(Q, i0, i1, i2, i3);
 }
 
+// LHAPDF-style continuation from the values y0, y1 at the lower and upper
+// knot of an edge interval to the position t in it (t < 0 or t > 1): the
+// power law y0^(1-t) y1^t when both values exceed kContMin, else the straight
+// line (no logarithm of a value that is not clearly positive).
+constexpr double kContMin = 1e-3;
+__device__ __forceinline__ double cont(double y0, double y1, double t)
+{
+    if (y0 > kContMin && y1 > kContMin) return y0 * exp(t * log(y1 / y0));
+    return fma(t, y1 - y0, y0);
+}
+
+// A patch outside the knot range under PDF_EXTRAP_CONTINUATION.  The patch
+// of the edge cell restricted to tq = 0 / 1 (or tx = 0 / 1) is the
+// interpolant along the lower / upper knot of that cell, so the edge values
+// come from the same 16 coefficients: Q is continued first (per edge x
+// column in a corner), then x.
+__device__ inline double patch_cont(const double *__restrict__ C, const Axis &X, const Axis &Q)
+{
+    D4 r0 = ld4(C), r1 = ld4(C + 4), r2 = ld4(C + 8), r3 = ld4(C + 12);
+    if (X.in) {   // Q out of range: rows tq = 0 and tq = 1 at tx
+        double i0 = horner(X, r0.x, r0.y, r0.z, r0.w);
+        double i1 = horner(X, r1.x, r1.y, r1.z, r1.w);
+        double i2 = horner(X, r2.x, r2.y, r2.z, r2.w);
+        double i3 = horner(X, r3.x, r3.y, r3.z, r3.w);
+        return cont(i0, i0 + i1 + i2 + i3, Q.t);
+    }
+    // the column sums give the tx = 1 edge; column 0 the tx = 0 edge
+    const double s0 = r0.x + r0.y + r0.z + r0.w, s1 = r1.x + r1.y + r1.z + r1.w;
+    const double s2 = r2.x + r2.y + r2.z + r2.w, s3 = r3.x + r3.y + r3.z + r3.w;
+    double a0, a1;
+    if (Q.in) {
+        a0 = horner(Q, r0.x, r1.x, r2.x, r3.x);
+        a1 = horner(Q, s0, s1, s2, s3);
+    } else {
+        a0 = cont(r0.x, r0.x + r1.x + r2.x + r3.x, Q.t);
+        a1 = cont(s0, s0 + s1 + s2 + s3, Q.t);
+    }
+    return cont(a0, a1, X.t);
+}
+
+// Value of a patch under the grid's extrapolation option.  Kernels are
+// instantiated with CONT = false for launches on grids without the
+// continuation option, so that the common path carries none of its code.
+template <bool CONT>
+__device__ __forceinline__ double patch_any(const GridDev &g, const double *__restrict__ C, const Axis &X,
+                                            const Axis &Q)
+{
+    if (CONT && g.extrap == PDF_EXTRAP_CONTINUATION && !(X.in && Q.in)) return patch_cont(C, X, Q);
+    return patch(C, X, Q);
+}
+
+// alpha_s from the 4 cubic coefficients of its Q cell, under the grid's
+// extrapolation option.
+__device__ __forceinline__ double alphas_any(const GridDev &g, const D4 &a, const Axis &Q)
+{
+    if (g.extrap == PDF_EXTRAP_CONTINUATION && !Q.in) return cont(a.x, a.x + a.y + a.z + a.w, Q.t);
+    return horner(Q, a.x, a.y, a.z, a.w);
+}
+
 // Patch value and its derivatives with respect to tx and tq.
 // (1, dx2, dx3) and (1, dq2, dq3) are the derivative bases of the two axes:
 // (1, 2t, 3t^2) inside the knot range, (1, 1, 1) for the linear continuation.

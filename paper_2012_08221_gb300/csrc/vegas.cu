@@ -27,6 +27,7 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kMaxBins = 1024;
 
+template <bool CONT>
 __global__ void __launch_bounds__(kBlock) k_vegas(GridDev g, Cols anti, int member, double ln_tau_min,
                                                   double ln_s, int n_bins, const double *__restrict__ edges,
                                                   const double *__restrict__ v, int64_t n,
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kBlock) k_vegas(GridDev g, Cols anti, int memb
         for (int a = 0; a < g.nflav; ++a) {
             int b = santi[a];
             if (b < 0) continue;
-            lum = fma(patch(c1 + a * 16, X1, Q), patch(c2 + b * 16, X2, Q), lum);
+            lum = fma(patch_any<CONT>(g, c1 + a * 16, X1, Q), patch_any<CONT>(g, c2 + b * 16, X2, Q), lum);
         }
         const double w = (-ln_tau_min) * (-ln_tau) * lum * jac;
         s1 += w;
@@ -151,9 +152,10 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
     PDF_CUDA(cudaMemsetAsync(sums, 0, (2 + 2 * (size_t)n_bins) * sizeof(double), s));
     if (n == 0) return PDF_OK;
     size_t smem = 2 * (size_t)n_bins * sizeof(double);
-    rc = allow_dynamic_smem((const void *)k_vegas, smem);
+    auto k = g->d.extrap == PDF_EXTRAP_CONTINUATION ? k_vegas<true> : k_vegas<false>;
+    rc = allow_dynamic_smem((const void *)k, smem);
     if (rc) return rc;
-    int grid = wave_grid(g, (const void *)k_vegas, kBlock, smem, n);
+    int grid = wave_grid(g, (const void *)k, kBlock, smem, n);
     if (g->partials_cap < 2 * grid) {
         if (g->partials) cudaFree(g->partials);
         g->partials = nullptr;
@@ -161,7 +163,7 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
         PDF_CUDA(cudaMalloc(&g->partials, (size_t)2 * grid * sizeof(double)));
         g->partials_cap = 2 * grid;
     }
-    k_vegas<<<grid, kBlock, smem, s>>>(g->d, anti, member, ln_tau_min, ln_s, n_bins, edges, v, n, g->partials,
+    k<<<grid, kBlock, smem, s>>>(g->d, anti, member, ln_tau_min, ln_s, n_bins, edges, v, n, g->partials,
                                        sums + 2);
     PDF_CUDA(cudaGetLastError());
     k_vegas_final<<<1, 256, 0, s>>>(g->partials, grid, sums);

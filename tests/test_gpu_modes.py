@@ -101,3 +101,82 @@ def test_batched_and_luminosity_follow_the_grid_modes(built):
         assert np.array_equal(np.isnan(got), np.isnan(lumr))
         m = ~np.isnan(lumr)
         assert np.all(np.abs(got[m] - lumr[m]) <= 1e-12 * scale[m])
+
+
+# ------------------------------------------------ power-law continuation (3)
+
+def _edge_positions(knots_log, z):
+    """Position t of z in the edge interval of the knots when z is outside
+    (t < 0 below, t > 1 above), 0 inside."""
+    t = np.zeros_like(z)
+    lo, hi = z < knots_log[0], z > knots_log[-1]
+    t[lo] = (z[lo] - knots_log[0]) / (knots_log[1] - knots_log[0])
+    t[hi] = (z[hi] - knots_log[-2]) / (knots_log[-1] - knots_log[-2])
+    return t
+
+
+@pytest.mark.parametrize("interp", [0, 1, 2])
+def test_continuation_forward_and_alphas(built, interp):
+    """x*f and alpha_s under the power-law continuation against the oracle
+    with the same option.  The oracle's kappa is a linear-interpolation
+    scale, so outside the grid it is widened by the continuation's growth
+    (1 + |t_x|)(1 + |t_Q|) (rounding of the edge values carries through the
+    power law with those weights); inside, the results equal the linear
+    option's bit for bit."""
+    from paper_2012_08221_gb300.pdf import PDF
+    for g in (tiny_two_sub(seed=31, dup_equal=False), synth.grid_nnpdf()):
+        pc = PDF.from_grid(g, interp=interp, extrap="continuation")
+        pl = PDF.from_grid(g, interp=interp, extrap="linear")
+        oc = OracleGrid.from_synth(g, interp=interp, extrap=3)
+        ol = OracleGrid.from_synth(g, interp=interp, extrap=0)
+        x, q2 = _points(g, 20_011, 41)
+        X, Q = cuda(x), cuda(q2)
+        got = pc.xfxQ2(g.pids, X, Q).cpu().numpy()
+        lin = pl.xfxQ2(g.pids, X, Q).cpu().numpy()
+        assert pc.status() == 0
+        U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+        tu, tw = _edge_positions(U, np.log(x)), _edge_positions(W, np.log(q2))
+        inside = (tu == 0) & (tw == 0)
+        assert np.array_equal(got[inside], lin[inside])
+        grow = ((1 + np.abs(tu)) * (1 + np.abs(tw)))[:, None]
+        ref = oc.xfxq2_batch(g.pids, x, q2)
+        kap = ol.kappa(g.pids, x, q2)
+        parity.check(got, ref, kap * np.where(inside[:, None], 1.0, 10 * grow),
+                     what=f"continuation interp {interp} {g.name}")
+        ga = pc.alphasQ2(Q).cpu().numpy()
+        ra = oc.alphas_batch(q2)
+        parity.check(ga, ra, 8 * np.abs(ra) * (1 + np.abs(tw)), what="alphas continuation")
+        v, d = pc.alphasQ2_grad(Q)
+        rd = np.array([oc.alphas_grad(q)[1] for q in q2[:3000]])
+        assert np.allclose(d.cpu().numpy()[:3000], rd, rtol=1e-9, atol=1e-12 * np.max(np.abs(rd)))
+
+
+def test_continuation_refuses_the_adjoint_and_follows_into_batches_and_luminosity(built):
+    from paper_2012_08221_gb300._lib import PdfError
+    from paper_2012_08221_gb300.batch import Batch
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_nnpdf(seeds=(1005,))
+    pdf = PDF.from_grid(g, extrap="continuation")
+    o = OracleGrid.from_synth(g, extrap=3)
+    x, q2 = _points(g, 5003, 42)
+    pid = np.full(x.size, 2, np.int32)
+    with pytest.raises(PdfError):
+        pdf.xfxQ2_backward(cuda(pid), cuda(x), cuda(q2), cuda(np.ones(x.size)), pointwise=True)
+    out = torch.empty((x.size, 3), dtype=torch.float64, device="cuda")
+    pids = np.array([-2, 0, 4], dtype=np.int32)
+    Batch([(pdf, 0, pids, cuda(x), cuda(q2), out)], autotune=False).run()
+    torch.cuda.synchronize()
+    assert torch.equal(out, pdf.xfxQ2(pids, cuda(x), cuda(q2)))
+    ev = synth.events_lhc(4000, seed=43)
+    dev = DeviceEvents.from_host(ev)
+    L, lum, a_s = luminosity(pdf, dev)
+    Lr, lumr, asr = o.lumi(ev)
+    got = lum.cpu().numpy()
+    # the injected tail sits up to ~40 x-intervals and ~30 Q-intervals below
+    # the grid, where the power law multiplies the edge values' rounding
+    assert np.all(np.abs(got - lumr) <= 1e-9 * (np.abs(lumr) + 1e3))
+    assert np.allclose(a_s.cpu().numpy(), asr, rtol=1e-12, atol=0)
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    with pytest.raises(PdfError):
+        luminosity_backward(pdf, dev, 1.0, gv)
