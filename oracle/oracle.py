@@ -110,6 +110,10 @@ def _declare(L):
     L.orc_vegas_sums.argtypes = [_G, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
                                  C.c_int64, _D]
     L.orc_vegas_refine.argtypes = [_D, C.c_int, C.c_double, _D]
+    L.orc_vegas_map.argtypes = [C.c_int, C.c_int, _D, _D, C.c_int64, _D, _D, C.POINTER(C.c_int)]
+    L.orc_vegas_map.restype = None
+    L.orc_vegas_accumulate.argtypes = [C.c_int, C.c_int, _D, C.POINTER(C.c_int), C.c_int64, _D]
+    L.orc_vegas_accumulate.restype = None
 
 
 def _d(a):
@@ -298,6 +302,31 @@ def vegas_refine(bin_w2, alpha, edges):
     e = _f64(edges).copy()
     lib().orc_vegas_refine(_d(b), b.size, float(alpha), _d(e))
     return e
+
+
+def vegas_map(edges, v):
+    """The VEGAS map of uniforms v [n][dim] through edges [dim][n_bins+1]:
+    (r [n][dim], Jacobian [n], bins [n][dim])."""
+    e = _f64(np.atleast_2d(edges))
+    dim, n_bins = e.shape[0], e.shape[1] - 1
+    v = _f64(v).reshape(-1, dim)
+    r = np.empty_like(v)
+    jac = np.empty(v.shape[0])
+    bins = np.empty(v.shape, dtype=np.int32)
+    lib().orc_vegas_map(dim, n_bins, _d(e), _d(v), v.shape[0], _d(r), _d(jac),
+                        bins.ctypes.data_as(C.POINTER(C.c_int)))
+    return r, jac, bins
+
+
+def vegas_accumulate(n_bins, w, bins):
+    """[sum w, sum w^2, per-dimension per-bin sums of w^2] of weights w [n]
+    with their bins [n][dim]."""
+    w = _f64(w)
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    dim = bins.shape[1]
+    out = np.empty(2 + dim * n_bins)
+    lib().orc_vegas_accumulate(dim, n_bins, _d(w), bins.ctypes.data_as(C.POINTER(C.c_int)), w.size, _d(out))
+    return out
 
 
 def vegas_sums(grid: "OracleGrid", member, ln_tau_min, ln_s, edges, v):

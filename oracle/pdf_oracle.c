@@ -690,6 +690,45 @@ void orc_vegas_sums(const orc_grid *g, int member, double ln_tau_min, double ln_
     }
 }
 
+/* The VEGAS map for an integrand the caller evaluates (any dimension): per
+ * point and dimension d, the uniform v lands in bin b = floor(v n) (at most
+ * n - 1) at fraction v n - b, and maps to r = e_b + frac (e_{b+1} - e_b); the
+ * Jacobian is the product over d of n (e_{b+1} - e_b).  edges [dim][n+1],
+ * v and r [n_pts][dim], bins [n_pts][dim]. */
+void orc_vegas_map(int dim, int n_bins, const double *edges, const double *v, int64_t n_pts, double *r,
+                   double *jac, int *bins)
+{
+    for (int64_t i = 0; i < n_pts; ++i) {
+        double j = 1.0;
+        for (int d = 0; d < dim; ++d) {
+            const double *e = edges + (size_t)d * (n_bins + 1);
+            double vn = v[i * dim + d] * n_bins;
+            int b = (int)vn;
+            if (b > n_bins - 1) b = n_bins - 1;
+            double frac = vn - b;
+            double width = e[b + 1] - e[b];
+            r[i * dim + d] = e[b] + frac * width;
+            j *= n_bins * width;
+            bins[i * dim + d] = b;
+        }
+        jac[i] = j;
+    }
+}
+
+/* Sums of one iteration from the weights w_i = f(r_i) J_i: out[0] = sum w,
+ * out[1] = sum w^2, then for each dimension d the per-bin sums of w^2,
+ * out[2 + d n + b].  Serial, in point order. */
+void orc_vegas_accumulate(int dim, int n_bins, const double *w, const int *bins, int64_t n_pts, double *out)
+{
+    for (int k = 0; k < 2 + dim * n_bins; ++k) out[k] = 0.0;
+    for (int64_t i = 0; i < n_pts; ++i) {
+        double wi = w[i];
+        out[0] += wi;
+        out[1] += wi * wi;
+        for (int d = 0; d < dim; ++d) out[2 + d * n_bins + bins[i * dim + d]] += wi * wi;
+    }
+}
+
 /* One refinement of one dimension's edges from its per-bin sums of w^2
  * (Lepage's rule): smooth the sums with their neighbours, damp them as
  * r_i = ((1 - d_i) / ln(1 / d_i))^alpha with d_i the normalised smoothed sum,

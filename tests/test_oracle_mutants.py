@@ -52,7 +52,13 @@ LUMI_MUTANTS = {
 
 VEGAS_MUTANTS = {
     "VEGAS Jacobian without the bin count": ("jac *= n_bins * width;", "jac *= width;"),
-    "VEGAS bin index off by one": ("int b = (int)vn;", "int b = (int)vn + 1;"),
+    "VEGAS bin index off by one": ("double vn = v[2 * i + d] * n_bins;\n            int b = (int)vn;",
+                                   "double vn = v[2 * i + d] * n_bins;\n            int b = (int)vn + 1;"),
+    "general VEGAS map without the bin count in the Jacobian": ("j *= n_bins * width;", "j *= width;"),
+    "general VEGAS map bin index off by one": ("double vn = v[i * dim + d] * n_bins;\n            int b = (int)vn;",
+                                               "double vn = v[i * dim + d] * n_bins;\n            int b = (int)vn + 1;"),
+    "general VEGAS accumulate drops the square": ("out[2 + d * n_bins + bins[i * dim + d]] += wi * wi;",
+                                                  "out[2 + d * n_bins + bins[i * dim + d]] += wi;"),
     "VEGAS tau mapped the other way": ("double ln_tau = (1.0 - r[0]) * ln_tau_min;",
                                        "double ln_tau = r[0] * ln_tau_min;"),
 }
@@ -187,6 +193,8 @@ def vegas_pins_fail():
     try:
         V.test_identity_map_on_constant_grid_is_the_closed_form()
         V.test_non_uniform_map_midpoint_rule_is_exact()
+        V.test_general_map_midpoint_lattice_is_exact_for_multilinear_integrands()
+        V.test_general_map_and_accumulate_reproduce_the_fused_luminosity_sums()
     except AssertionError:
         return True
     return False

@@ -5,7 +5,7 @@ import math
 
 import numpy as np
 
-from oracle.oracle import OracleGrid, vegas_refine, vegas_sums
+from oracle.oracle import OracleGrid, vegas_accumulate, vegas_map, vegas_refine, vegas_sums
 from paper_2012_08221_gb300 import synth
 from tests.tinygrids import fill
 
@@ -94,3 +94,48 @@ def test_non_uniform_map_midpoint_rule_is_exact():
     assert abs(s[0] / v.shape[0] - per / 2) <= 1e-12 * per
     assert abs(s[2:2 + nb].sum() - s[1]) <= 1e-12 * s[1]
     assert abs(s[2 + nb:].sum() - s[1]) <= 1e-12 * s[1]
+
+
+def test_general_map_midpoint_lattice_is_exact_for_multilinear_integrands():
+    """Any dimension: through random non-uniform edges, f(r) = prod_d (a_d +
+    b_d r_d) times the Jacobian is multilinear in v inside every bin cell, so
+    a midpoint lattice with whole numbers of points per bin integrates it
+    exactly: mean weight = prod_d (a_d + b_d / 2)."""
+    rng = np.random.default_rng(5)
+    dim, nb = 3, 8
+    edges = np.stack([np.concatenate([[0.0], np.sort(rng.uniform(0, 1, nb - 1)), [1.0]]) for _ in range(dim)])
+    m = (2 * nb, 3 * nb, nb)
+    axes = [(np.arange(k) + 0.5) / k for k in m]
+    v = np.stack(np.meshgrid(*axes, indexing="ij"), axis=-1).reshape(-1, dim)
+    r, jac, bins = vegas_map(edges, v)
+    a, b = np.array([0.5, 2.0, -1.0]), np.array([1.5, -0.7, 3.0])
+    w = np.prod(a + b * r, axis=1) * jac
+    s = vegas_accumulate(nb, w, bins)
+    assert abs(s[0] / v.shape[0] - np.prod(a + b / 2)) <= 1e-12
+    for d in range(dim):
+        assert abs(s[2 + d * nb: 2 + (d + 1) * nb].sum() - s[1]) <= 1e-12 * s[1]
+        # r stays in the bin the point was counted in
+        lo, hi = edges[d][bins[:, d]], edges[d][bins[:, d] + 1]
+        assert np.all((r[:, d] >= lo) & (r[:, d] <= hi))
+
+
+def test_general_map_and_accumulate_reproduce_the_fused_luminosity_sums():
+    """The fused luminosity iteration equals map -> the luminosity integrand
+    computed outside (events built from r, the oracle's luminosity) ->
+    accumulate: two independent routes through the oracle."""
+    g = synth.grid_nnpdf()
+    o = OracleGrid.from_synth(g)
+    rng = np.random.default_rng(6)
+    nb = 25
+    edges = np.stack([np.concatenate([[0.0], np.sort(rng.uniform(0, 1, nb - 1)), [1.0]]) for _ in range(2)])
+    v = rng.uniform(0, 1, (3000, 2))
+    fused = vegas_sums(o, 0, LN_TAU_MIN, LN_S, edges, v)
+    r, jac, bins = vegas_map(edges, v)
+    ln_tau = (1.0 - r[:, 0]) * LN_TAU_MIN
+    y = (2.0 * r[:, 1] - 1.0) * (-0.5 * ln_tau)
+    n = v.shape[0]
+    ev = synth.Events(ln_tau, y, np.zeros(n, np.uint8), np.zeros(n), np.zeros(n), LN_S)
+    _, lum, _ = o.lumi(ev)
+    w = (-LN_TAU_MIN) * (-ln_tau) * lum * jac
+    split = vegas_accumulate(nb, w, bins)
+    assert np.allclose(split, fused, rtol=1e-13, atol=0)
