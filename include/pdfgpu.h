@@ -344,6 +344,31 @@ int pdf_lhapdf_close(pdfgpu_lhapdf_t h);
  * `stream` first. */
 int pdf_get_status(pdfgpu_grid_t g, pdfgpu_stream_t stream, uint32_t *bits);
 
+/* General VEGAS (Lepage, J. Comput. Phys. 27 (1978) 192) around an
+ * integrand the caller evaluates: in the paper's use (Sec. 3.1) the
+ * integrand, a matrix element times PDFs, is user code that calls the PDF
+ * interface.  One iteration over [0, 1]^dim is
+ *   pdf_vegas_map -> r, J, bins;  f(r) by the caller's own kernels (for
+ *   example with xfxQ2);  w = f J;  pdf_vegas_accumulate(w, bins) -> sums;
+ *   pdf_vegas_refine for each dimension (host).
+ * pdf_vegas_map: edges DEVICE [dim][n_bins + 1] (0 = e_0 < ... < e_n = 1 per
+ *   dimension), v DEVICE [n][dim] uniforms in [0, 1) (values outside are
+ *   clamped into the first / last bin), r DEVICE [n][dim] out: r = e_b +
+ *   (v n - b)(e_{b+1} - e_b) with b = floor(v n); jac DEVICE [n] out: the
+ *   product over dimensions of n (e_{b+1} - e_b); bins DEVICE [n][dim] int32
+ *   out.
+ * pdf_vegas_accumulate: w DEVICE [n] weights, bins DEVICE [n][dim] as from
+ *   pdf_vegas_map (entries outside [0, n_bins) are left out of the per-bin
+ *   sums), sums DEVICE [2 + dim n_bins] (overwritten): sum w, sum w^2, then
+ *   per dimension the per-bin sums of w^2.  Summation order is not fixed.
+ * 1 <= dim <= 16, 2 <= n_bins <= 1024.  Asynchronous on `stream`; no grid
+ * handle and no library-owned scratch, so calls on different streams are
+ * independent.  The library has no counterpart of the caller's integrand. */
+int pdf_vegas_map(int32_t dim, int32_t n_bins, const double *edges, const double *v, int64_t n, double *r,
+                  double *jac, int32_t *bins, pdfgpu_stream_t stream);
+int pdf_vegas_accumulate(int32_t dim, int32_t n_bins, const double *w, const int32_t *bins, int64_t n,
+                         double *sums, pdfgpu_stream_t stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *pdf_last_error(void);
 

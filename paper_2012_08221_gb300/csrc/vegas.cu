@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kBlock) k_vegas(GridDev g, Cols anti, int memb
         for (int d = 0; d < 2; ++d) {
             const double *e = edges + (size_t)d * (n_bins + 1);
             double vn = (d ? vv.y : vv.x) * nb;
-            int b = min((int)vn, n_bins - 1);
+            int b = min(max((int)vn, 0), n_bins - 1);    // uniforms outside [0, 1) stay in range
             double lo = __ldg(e + b), width = __ldg(e + b + 1) - lo;
             r[d] = fma(vn - (double)b, width, lo);
             jac *= nb * width;
@@ -126,6 +126,85 @@ __global__ void k_vegas_final(const double *__restrict__ partials, int nb, doubl
         out[0] = r1[0];
         out[1] = r2[0];
     }
+}
+
+constexpr int kMaxVegasDim = 16;
+
+// The VEGAS map for an integrand the caller evaluates: one point per
+// thread, every dimension through its own bin edges.
+__global__ void __launch_bounds__(kBlock) k_vegas_map(int dim, int n_bins, const double *__restrict__ edges,
+                                                      const double *__restrict__ v, int64_t n,
+                                                      double *__restrict__ r, double *__restrict__ jac,
+                                                      int *__restrict__ bins)
+{
+    const double nb = (double)n_bins;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double j = 1.0;
+        for (int d = 0; d < dim; ++d) {
+            const double *e = edges + (size_t)d * (n_bins + 1);
+            double vn = v[i * dim + d] * nb;
+            int b = min(max((int)vn, 0), n_bins - 1);    // uniforms outside [0, 1) stay in range
+            double lo = __ldg(e + b), width = __ldg(e + b + 1) - lo;
+            r[i * dim + d] = fma(vn - (double)b, width, lo);
+            j *= nb * width;
+            bins[i * dim + d] = b;
+        }
+        jac[i] = j;
+    }
+}
+
+// Sums of one iteration from the caller's weights: per block, sum w and
+// sum w^2 by shuffles and the per-bin sums of w^2 in shared memory, then
+// one atomic per nonzero block total.
+__global__ void __launch_bounds__(kBlock) k_vegas_accumulate(int dim, int n_bins, const double *__restrict__ w,
+                                                             const int *__restrict__ bins, int64_t n,
+                                                             double *__restrict__ sums)
+{
+    extern __shared__ double sb[];           // [dim][n_bins]
+    __shared__ double red[2][kBlock / 32];
+    const int nsb = dim * n_bins;
+    for (int k = threadIdx.x; k < nsb; k += blockDim.x) sb[k] = 0.0;
+    __syncthreads();
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w[i], w2 = wi * wi;
+        s1 += wi;
+        s2 += w2;
+        for (int d = 0; d < dim; ++d) {
+            int b = bins[i * dim + d];
+            if (b >= 0 && b < n_bins) atomicAdd(&sb[d * n_bins + b], w2);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s1;
+        red[1][threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            t1 += red[0][k];
+            t2 += red[1][k];
+        }
+        atomicAdd(&sums[0], t1);
+        atomicAdd(&sums[1], t2);
+    }
+    for (int k = threadIdx.x; k < nsb; k += blockDim.x)
+        if (dbits(sb[k]) << 1) atomicAdd(&sums[2 + k], sb[k]);
+}
+
+int vegas_grid(int64_t n)
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + kBlock - 1) / kBlock, (int64_t)sms * 8));
 }
 
 }  // namespace
@@ -204,5 +283,39 @@ extern "C" int pdf_vegas_refine(const double *bin_w2, int32_t n_bins, double alp
     }
     edges[0] = 0.0;
     edges[n_bins] = 1.0;
+    return PDF_OK;
+}
+
+extern "C" int pdf_vegas_map(int32_t dim, int32_t n_bins, const double *edges, const double *v, int64_t n,
+                             double *r, double *jac, int32_t *bins, pdfgpu_stream_t stream)
+{
+    clear_error();
+    if (dim < 1 || dim > kMaxVegasDim) return fail(PDF_E_RANGE, "dim must be in [1, 16]");
+    if (n_bins < 2 || n_bins > kMaxBins) return fail(PDF_E_RANGE, "n_bins must be in [2, 1024]");
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (n == 0) return PDF_OK;
+    if (!edges || !v || !r || !jac || !bins) return fail(PDF_E_ARG, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_vegas_map<<<vegas_grid(n), kBlock, 0, s>>>(dim, n_bins, edges, v, n, r, jac, bins);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
+extern "C" int pdf_vegas_accumulate(int32_t dim, int32_t n_bins, const double *w, const int32_t *bins,
+                                    int64_t n, double *sums, pdfgpu_stream_t stream)
+{
+    clear_error();
+    if (dim < 1 || dim > kMaxVegasDim) return fail(PDF_E_RANGE, "dim must be in [1, 16]");
+    if (n_bins < 2 || n_bins > kMaxBins) return fail(PDF_E_RANGE, "n_bins must be in [2, 1024]");
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (!sums || (n > 0 && (!w || !bins))) return fail(PDF_E_ARG, "null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    PDF_CUDA(cudaMemsetAsync(sums, 0, (2 + (size_t)dim * n_bins) * sizeof(double), s));
+    if (n == 0) return PDF_OK;
+    size_t smem = (size_t)dim * n_bins * sizeof(double);
+    int rc = allow_dynamic_smem((const void *)k_vegas_accumulate, smem);
+    if (rc) return rc;
+    k_vegas_accumulate<<<vegas_grid(n), kBlock, smem, s>>>(dim, n_bins, w, bins, n, sums);
+    PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
