@@ -9,8 +9,10 @@ further points: `xfxQ2` + `alphasQ2` through the C ABI on device-resident
 inputs.  `value` = x*f evaluations per second over all ranks.  The other forms
 of the hot path are timed in the same run and reported under "forms":
 forward+backward (pointwise, 1e7 points, autograd adjoint), the batched
-graph-captured launch (400 uneven requests over 3 grids) and the fused
-luminosity (1e8 events, forward and forward+backward).
+graph-captured launch (400 uneven requests over 3 grids), the fused
+luminosity (1e8 events, forward and forward+backward), VEGAS on the fused
+luminosity, and VEGAS around a single-top-like integrand written as user
+code.
 
 Timing: W warm-up steps, then K steps between a barrier + synchronize and
 CUDA events on the launching stream; the max over ranks is reported.  Inputs
@@ -275,7 +277,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="all", help="comma list of fwdbwd,batched,lumi,vegas or all/none")
+    ap.add_argument("--forms", default="all",
+                    help="comma list of fwdbwd,batched,lumi,vegas,vegas_user or all/none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="points of the headline workload (smaller only for profiling captures)")
@@ -382,7 +385,7 @@ def main():
                 "kernel_ms": k_ms}
 
     forms = {}
-    want = set(["fwdbwd", "batched", "lumi", "vegas"] if args.forms == "all" else
+    want = set(["fwdbwd", "batched", "lumi", "vegas", "vegas_user"] if args.forms == "all" else
                ([] if args.forms == "none" else args.forms.split(",")))
 
     # --------------------------------------------------- forward + backward
@@ -516,6 +519,53 @@ def main():
             "value": world * pts * 2 * gv.n_flav / (ms6 * 1e-3), "unit": "evals/s",
             "points_per_s": world * pts / (ms6 * 1e-3), "ms_per_step": ms6,
             "fp64_frac": pts * work.vegas_point_flops(gv.n_flav) / (ms6 * 1e-3) / peak,
+            "integral": r.integral, "error": r.error, "chi2_dof": r.chi2_dof}
+        del U
+
+    # ------------------------------------- VEGAS around a user integrand
+    if "vegas_user" in want:
+        from paper_2012_08221_gb300.vegas import Vegas
+        gs = synth.grid_nnpdf()
+        ps = PDF.from_grid(gs, device=dev)
+        n_it, n_pts = 5, args.vegas_points
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2007)
+        U = [torch.rand((n_pts, 3), generator=gen, dtype=torch.float64, device=dev) for _ in range(n_it)]
+        b_pid = np.array([5], dtype=np.int32)
+        q_pids = np.array([2, 4, -1, -3], dtype=np.int32)
+        mt, mw, s_had = 173.0, 80.4, 13000.0 ** 2
+        ln_tau_min = math.log(mt * mt / s_had)
+
+        def single_top_like(r):
+            # phase space (tau, y, cos theta), a t-channel W propagator and
+            # b x (u, c, d-bar, s-bar) luminosity: the shape of a single-top
+            # LO integrand, with a toy matrix element
+            ln_tau = (1.0 - r[:, 0]) * ln_tau_min
+            tau = torch.exp(ln_tau)
+            y = (2.0 * r[:, 1] - 1.0) * (-0.5 * ln_tau)
+            x1, x2 = torch.exp(0.5 * ln_tau + y), torch.exp(0.5 * ln_tau - y)
+            shat = tau * s_had
+            that = -(shat - mt * mt) * (1.0 - (2.0 * r[:, 2] - 1.0)) / 2.0
+            me2 = shat * (shat - mt * mt) / (that - mw * mw) ** 2
+            q2 = torch.full_like(x1, mt * mt)
+            lum = ps.xfxQ2(b_pid, x1, q2)[:, 0] * ps.xfxQ2(q_pids, x2, q2).sum(1) / (x1 * x2)
+            return (-ln_tau_min) * tau * (-ln_tau) * 2.0 * me2 * lum / (2.0 * shat)
+
+        res = {}
+
+        def step7():
+            res["r"] = Vegas(3, n_bins=50, device=dev).integrate(single_top_like, n_iter=n_it,
+                                                                 n_per_iter=n_pts, uniforms=U)
+
+        ms7, _ = timed(step7, 2, args.warmup)
+        r = res["r"]
+        pts = n_it * n_pts
+        forms["vegas_user"] = {
+            "workload": f"VEGAS over 3 dimensions around a single-top-like LO integrand written as user code "
+                        f"(torch operations; xfxQ2 for b at x1 and u, c, d-bar, s-bar at x2, Q = 173 GeV); "
+                        f"{n_it} adapting iterations x {n_pts} points, 50 bins per dimension",
+            "value": world * pts * 5 / (ms7 * 1e-3), "unit": "evals/s",
+            "points_per_s": world * pts / (ms7 * 1e-3), "ms_per_step": ms7,
             "integral": r.integral, "error": r.error, "chi2_dof": r.chi2_dof}
         del U
 
