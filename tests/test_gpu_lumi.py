@@ -38,14 +38,14 @@ def _event_logs(ev, n):
     return u1, u2, w
 
 
-def _lum_kappa(g, o, ev, n):
+def _lum_kappa(g, o, ev, n, member=0):
     """Term scale of lum: sum_a kappa(x1)_a |f(x2)_-a| + |f(x1)_a| kappa(x2)_-a."""
     u1, u2, w = _event_logs(ev, n)
     x1, x2, q2 = np.exp(u1), np.exp(u2), np.exp(w)
-    k1 = o.kappa(g.pids, x1, q2)
-    k2 = o.kappa(g.pids, x2, q2)
-    f1 = np.abs(o.xfxq2_batch(g.pids, x1, q2))
-    f2 = np.abs(o.xfxq2_batch(g.pids, x2, q2))
+    k1 = o.kappa(g.pids, x1, q2, member=member)
+    k2 = o.kappa(g.pids, x2, q2, member=member)
+    f1 = np.abs(o.xfxq2_batch(g.pids, x1, q2, member=member))
+    f2 = np.abs(o.xfxq2_batch(g.pids, x2, q2, member=member))
     anti = np.array([list(g.pids).index(-p) for p in g.pids])
     return np.sum(k1 * f2[:, anti] + f1 * k2[:, anti] + k1 * k2[:, anti], axis=1)
 
@@ -178,3 +178,23 @@ def test_full_size_luminosity_sampled(lhc):
     for b in range(g.n_flav):
         want = acc[anti[b]] / n
         assert abs(G[:, :, b].sum() - want) <= 1e-9 * (abs(want) + acc_abs[anti[b]] / n)
+
+
+def test_other_members_forward_and_gradient(lhc):
+    """Replicas 1 and 2 of the three-member grid: luminosity and its grid
+    gradient (into that member's slice) against the oracle for the same
+    member; replica 2 differs from replica 0."""
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
+    g, pdf, o = lhc
+    ev = synth.events_lhc(3001, seed=94)
+    dev = DeviceEvents.from_host(ev)
+    for m in (1, 2):
+        L, lum, a_s = luminosity(pdf, dev, member=m)
+        Lr, lumr, asr = o.lumi(ev, member=m)
+        parity.check(lum.cpu().numpy(), lumr, _lum_kappa(g, o, ev, 3001, member=m), what=f"lum member {m}")
+        gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+        luminosity_backward(pdf, dev, 1.0, gv, member=m)
+        ref = o.lumi_dgrid(ev, member=m)
+        tol = 1e-9 * np.maximum(np.abs(ref), o.lumi_dgrid(ev, member=m, absval=True)) + 1e-300
+        assert np.all(np.abs(gv.cpu().numpy() - ref) <= tol)
+    assert not np.allclose(o.lumi(ev, member=2)[1], o.lumi(ev, member=0)[1])
