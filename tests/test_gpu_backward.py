@@ -83,6 +83,22 @@ def test_matrix_gradients_against_oracle(lib_small=None):
     _check(gq.cpu().numpy(), rdq, gs * 4 * kap / (np.min(np.diff(W)) * q2), "matrix dL/dQ2")
 
 
+def test_gradient_larger_than_shared_memory():
+    """The NNPDF-shaped grid's gradient (1 MB per member) does not fit in
+    shared memory: the adjoint adds straight into global memory."""
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_nnpdf()
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    x, q2, _ = synth.queries_nnpdf(3001, seed=44)
+    pids = np.array([-2, 0, 5], dtype=np.int32)
+    gout = np.random.default_rng(45).standard_normal((x.size, pids.size))
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    assert gv.numel() * 8 > 200 * 1024
+    pdf.xfxQ2_backward(pids, cuda(x), cuda(q2), cuda(gout), grad_values=gv)
+    ref = o.dgrid(pids, x, q2, gout)
+    _check(gv.cpu().numpy(), ref, o.dgrid(pids, x, q2, gout, absval=True), "global-memory dL/dvalues")
+
+
 def test_central_finite_differences(diffgrid):
     """h = 1e-6 relative, on points more than 2h (in log) from every knot."""
     g, pdf, o = diffgrid

@@ -222,6 +222,19 @@ def test_edge_cases(nnpdf):
     assert np.all(err <= 1e-13 * (np.abs(want) + 1e-3))
 
 
+def test_maximum_pid_count(nnpdf):
+    """64 requested pids (the limit; repeats allowed): 128 KB of staged rows
+    per CTA, above the default shared-memory limit; every column equals the
+    same pid's column of a 13-pid call bit for bit."""
+    g, pdf, o = nnpdf
+    x, q2, _ = synth.queries_nnpdf(20_001, seed=35)
+    X, Q = cuda(x), cuda(q2)
+    pids = np.array([g.pids[k % g.n_flav] for k in range(64)], dtype=np.int32)
+    wide = pdf.xfxQ2(pids, X, Q).cpu().numpy()
+    base = pdf.xfxQ2(g.pids, X, Q).cpu().numpy()
+    assert np.array_equal(wide, base[:, [k % g.n_flav for k in range(64)]])
+
+
 def test_empty_and_tiny_batches(small):
     g, pdf, o = small
     e = torch.empty(0, dtype=torch.float64, device="cuda")
