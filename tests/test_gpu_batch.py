@@ -118,3 +118,30 @@ def test_full_size_batched_workload_sampled(sets):
         got = out[cuda(sel)].cpu().numpy()
         ref = o.xfxq2_batch(pids, b.x[sel], b.q2[sel], member=member)
         parity.check(got, ref, o.kappa(pids, b.x[sel], b.q2[sel], member=member), what=f"full req {k}")
+
+
+def test_staged_shape_with_a_grid_beyond_the_staging_tables():
+    """The default (untuned) shape stages knot and log tables in shared
+    memory; a grid with more x cells than the staged tables hold (299 > 256)
+    must fall back to the global tables inside the same launch, next to a
+    grid that is staged."""
+    from paper_2012_08221_gb300.batch import Batch
+    from paper_2012_08221_gb300.pdf import PDF
+    big = synth.grid_small()
+    x = np.exp(np.linspace(np.log(1e-7), 0.0, 300))
+    rng = np.random.default_rng(46)
+    vals = rng.uniform(0.1, 2.0, (1, big.n_rows, x.size, big.n_flav))
+    big = synth.Grid(x, big.n_q, big.q_knots, big.pids, vals, big.alphas, "x300")
+    small = synth.grid_small()
+    pb, ps = PDF.from_grid(big), PDF.from_grid(small)
+    reqs = []
+    for k, p in enumerate((pb, ps, pb)):
+        xq, q2 = synth.queries_small(7001 + 1000 * k, seed=47 + k)
+        out = torch.empty((xq.size, 3), dtype=torch.float64, device="cuda")
+        reqs.append((p, 0, np.array([-1, 0, 2], dtype=np.int32), cuda(xq), cuda(q2), out))
+    B = Batch(reqs, autotune=False)
+    assert B.info()["stage"] == 1
+    B.run()
+    torch.cuda.synchronize()
+    for p, m, pids, xq, q2, out in reqs:
+        assert torch.equal(out, p.xfxQ2(pids, xq, q2, m))
