@@ -273,3 +273,37 @@ def test_table_log_against_cuda_log(small):
     ulp = np.spacing(np.abs(ref))
     assert np.all(np.abs(got - ref) <= 3 * ulp + 1e-18)
     assert got[-4] == 0.0                        # ln 1 is exact
+
+
+def test_concurrent_streams_and_host_threads(nnpdf):
+    """Device calls on two streams at once, and host-buffer calls from two
+    host threads at once, on the same grid: the same results as one at a
+    time (the forward kernels use no grid-owned scratch; the host-buffer
+    path serialises its staging buffers per grid)."""
+    import threading
+    g, pdf, o = nnpdf
+    xa, qa, _ = synth.queries_nnpdf(200_003, seed=51)
+    xb, qb, _ = synth.queries_nnpdf(150_001, seed=52)
+    ref_a = pdf.xfxQ2(g.pids, cuda(xa), cuda(qa))
+    ref_b = pdf.xfxQ2(g.pids, cuda(xb), cuda(qb))
+    Xa, Qa, Xb, Qb = cuda(xa), cuda(qa), cuda(xb), cuda(qb)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        a = pdf.xfxQ2(g.pids, Xa, Qa)
+    with torch.cuda.stream(s2):
+        b = pdf.xfxQ2(g.pids, Xb, Qb)
+    torch.cuda.synchronize()
+    assert torch.equal(a, ref_a) and torch.equal(b, ref_b)
+    out = {}
+
+    def host_call(key, x, q):
+        out[key] = pdf.xfxQ2_host(g.pids, torch.as_tensor(x).pin_memory(), torch.as_tensor(q).pin_memory())
+
+    ts = [threading.Thread(target=host_call, args=("a", xa, qa)),
+          threading.Thread(target=host_call, args=("b", xb, qb))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert torch.equal(out["a"], ref_a.cpu()) and torch.equal(out["b"], ref_b.cpu())
