@@ -29,6 +29,10 @@
  *     Calls are asynchronous unless documented otherwise.
  *   - Arrays documented as HOST are read during the call (copied) unless
  *     documented otherwise.
+ *   - xfxQ2 and alphasQ2 (and their Q forms) may be captured in a CUDA graph
+ *     on `stream` once a first call on the grid has run outside the capture
+ *     (that call may raise a kernel's shared-memory limit, which a capture
+ *     must not do); the graph's replays read the captured device arrays.
  *   - Per-element domain errors do not fail a call: x <= 0, x > 1, Q^2 <= 0,
  *     Q^2 infinite or any NaN input gives NaN for every requested flavour and
  *     sets PDF_S_DOMAIN in the grid's status word (PDF_S_RANGE for points

@@ -307,3 +307,30 @@ def test_concurrent_streams_and_host_threads(nnpdf):
     for t in ts:
         t.join()
     assert torch.equal(out["a"], ref_a.cpu()) and torch.equal(out["b"], ref_b.cpu())
+
+
+def test_cuda_graph_capture_and_replay(nnpdf):
+    """The headline step (x*f for 13 pids plus alpha_s) captured once in a
+    CUDA graph and replayed on new inputs copied into the captured buffers:
+    the same results as direct calls."""
+    g, pdf, o = nnpdf
+    x, q2, qa = synth.queries_nnpdf(100_003, seed=53)
+    X, Q, QA = cuda(x), cuda(q2), cuda(qa)
+    OUT = torch.empty((x.size, g.n_flav), dtype=torch.float64, device="cuda")
+    AS = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    pdf.xfxQ2(g.pids, X, Q, out=OUT)            # first calls outside the capture
+    pdf.alphasQ2(QA, out=AS)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        pdf.xfxQ2(g.pids, X, Q, out=OUT)
+        pdf.alphasQ2(QA, out=AS)
+    for seed in (54, 55):
+        x2, q22, qa2 = synth.queries_nnpdf(x.size, seed=seed)
+        X.copy_(cuda(x2))
+        Q.copy_(cuda(q22))
+        QA.copy_(cuda(qa2))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(OUT, pdf.xfxQ2(g.pids, cuda(x2), cuda(q22)))
+        assert torch.equal(AS, pdf.alphasQ2(cuda(qa2)))
