@@ -66,8 +66,10 @@ enum {
 /* Status bits accumulated by kernels in the grid's device status word. */
 enum {
     PDF_S_DOMAIN = 1u,    /* some input x / Q^2 was out of the domain (output NaN)   */
-    PDF_S_RANGE = 2u      /* some input was outside the knot range of a grid loaded
+    PDF_S_RANGE = 2u,     /* some input was outside the knot range of a grid loaded
                              with PDF_EXTRAP_ERROR (output NaN)                      */
+    PDF_S_BOUNDS = 4u     /* checked builds only (PDFGPU_CHECKED): a table index computed
+                             on the device was out of range and was replaced        */
 };
 
 /* Interpolation kind of a grid (pdfgpu_grid_desc.interp).  The paper keeps

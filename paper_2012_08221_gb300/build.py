@@ -2,7 +2,8 @@
 
 Every ``csrc/*.cu`` file is compiled by nvcc in parallel
 (``-gencode arch=compute_103a,code=sm_103a -O3 -lineinfo``) and linked into
-one shared object under ``paper_2012_08221_gb300/_build/``.  No PyTorch
+one shared object under ``paper_2012_08221_gb300/_build/`` (``_build_checked/``
+for the range-checked variant, ``PDFGPU_CHECKED=1``).  No PyTorch
 headers are involved: the library exposes only the C ABI of
 ``include/pdfgpu.h``.
 """
@@ -18,7 +19,10 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(PKG, "_build")
+# PDFGPU_CHECKED=1 builds (and loads) a separate library in which every table
+# index computed on the device is range-checked (status bit PDF_S_BOUNDS).
+CHECKED = os.environ.get("PDFGPU_CHECKED", "") not in ("", "0")
+BUILD = os.path.join(PKG, "_build_checked" if CHECKED else "_build")
 LIB = os.path.join(BUILD, "libpdfgpu.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -50,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
-                    "-I", INCLUDE, "-I", CSRC]
+                    "-I", INCLUDE, "-I", CSRC] + (["-DPDFGPU_CHECKED"] if CHECKED else [])
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")

@@ -142,6 +142,7 @@ __global__ void k_batch(const GridDev *__restrict__ grids, const BatchReq *__res
             double *srow = wbuf + lane * npid;
             for (int a = 0; a < npid; ++a) {
                 int col = sr.cols[a];
+                if (col >= 0) col = checked_index(g.status, col, g.nflav);
                 double v = col >= 0 ? patch_any<CONT>(g, cell + col * 16, X, Q) : 0.0;
                 srow[a] = bad ? qnan() : v;
             }
@@ -282,6 +283,7 @@ static int enqueue(pdfgpu_batch *b, cudaStream_t st)
 
 extern "C" int pdf_batch_free(pdfgpu_batch_t b)
 {
+    PDF_TRACE("pdf_batch_free");
     clear_error();
     if (!b) return fail(PDF_E_ARG, "null batch");
     cudaSetDevice(b->device);
@@ -307,6 +309,7 @@ extern "C" int pdf_batch_free(pdfgpu_batch_t b)
 extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc, int32_t autotune,
                                  pdfgpu_stream_t stream, pdfgpu_batch_t *out)
 {
+    PDF_TRACE("pdf_batch_prepare");
     clear_error();
     if (!descs || !out || n_desc < 1) return fail(PDF_E_ARG, "need at least one request");
     *out = nullptr;
@@ -451,6 +454,7 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
 
 extern "C" int pdf_batch_run(pdfgpu_batch_t b, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_batch_run");
     clear_error();
     if (!b || !b->exec) return fail(PDF_E_ARG, "batch not prepared");
     PDF_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
@@ -460,6 +464,7 @@ extern "C" int pdf_batch_run(pdfgpu_batch_t b, pdfgpu_stream_t stream)
 extern "C" int pdf_batch_info(pdfgpu_batch_t b, int32_t *block, int32_t *qpt, int32_t *stage, int32_t *ctas,
                               float *ms)
 {
+    PDF_TRACE("pdf_batch_info");
     clear_error();
     if (!b) return fail(PDF_E_ARG, "null batch");
     if (block) *block = b->shape.block;
@@ -502,6 +507,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocS
 extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_desc,
                                      pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_batch_run_noalloc");
     clear_error();
     if (!descs) return fail(PDF_E_ARG, "null request list");
     if (n_desc < 1 || n_desc > kNoAllocMaxRequests)

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
         const int na = PW ? 1 : npid;
         for (int a = 0; a < na; ++a) {
             int col = PW ? pid_col(g, pid[i]) : scol[a];
+            if (col >= 0) col = checked_index(g.status, col, g.nflav);
             if (col < 0) continue;
             double ga = PW ? gout[i] : gout[i * npid + a];
             double dtx, dtq;
@@ -99,7 +100,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
                 for (int j = 0; j < 4; ++j) {
                     if (!((qmask >> j) & 1)) continue;
                     double gj = ga * Wq[j];
-                    double *rowp = acc + ((size_t)(r0 + j) * g.nx) * g.nflav + col;
+                    const int row = checked_index(g.status, r0 + j, g.nrows);
+                    double *rowp = acc + ((size_t)row * g.nx) * g.nflav + col;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         int kk = k0 + k;
@@ -149,6 +151,7 @@ extern "C" int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pi
                               const double *grad_out, double *grad_x, double *grad_q2,
                               double *grad_values, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("xfxQ2_backward");
     clear_error();
     int rc = check_grid(g, true);
     if (rc) return rc;

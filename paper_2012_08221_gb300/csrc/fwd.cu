@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         warp_run_reuse(lane);                 // the previous run has left the slice
         for (int a = 0; a < npid; ++a) {
             int col = scol[a];
+            if (col >= 0) col = checked_index(g.status, col, g.nflav);
             double v = col >= 0 ? patch_any<CONT>(g, cell + col * 16, X, Q) : 0.0;
             srow[a] = bad ? qnan() : v;
         }
@@ -214,18 +215,21 @@ int launch_alphas(pdfgpu_grid *g, const double *q, int64_t n, double *out, cudaS
 extern "C" int xfxQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                      const double *x, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("xfxQ2");
     return launch_matrix(g, member, pids, n_pid, x, q2, n, out, (cudaStream_t)stream, false);
 }
 
 extern "C" int xfxQ(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                     const double *x, const double *q, int64_t n, double *out, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("xfxQ");
     return launch_matrix(g, member, pids, n_pid, x, q, n, out, (cudaStream_t)stream, true);
 }
 
 extern "C" int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
                         const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("xfxQ2_pw");
     clear_error();
     int rc = check_grid(g, true);
     if (rc) return rc;
@@ -242,17 +246,20 @@ extern "C" int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, con
 
 extern "C" int alphasQ2(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("alphasQ2");
     return launch_alphas(g, q2, n, out, (cudaStream_t)stream, false);
 }
 
 extern "C" int alphasQ(pdfgpu_grid_t g, const double *q, int64_t n, double *out, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("alphasQ");
     return launch_alphas(g, q, n, out, (cudaStream_t)stream, true);
 }
 
 extern "C" int alphasQ2_grad(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, double *dq2,
                              pdfgpu_stream_t stream)
 {
+    PDF_TRACE("alphasQ2_grad");
     clear_error();
     int rc = check_grid(g, false);
     if (rc) return rc;
@@ -269,6 +276,7 @@ extern "C" int alphasQ2_grad(pdfgpu_grid_t g, const double *q2, int64_t n, doubl
 extern "C" int pdf_debug_log(pdfgpu_grid_t g, const double *in, int64_t n, double *out,
                              pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_debug_log");
     clear_error();
     int rc = check_grid(g, false);
     if (rc) return rc;
@@ -287,6 +295,7 @@ extern "C" int pdf_debug_log(pdfgpu_grid_t g, const double *in, int64_t n, doubl
 extern "C" int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                           const double *x, const double *q2, int64_t n, double *out)
 {
+    PDF_TRACE("xfxQ2_host");
     clear_error();
     int rc = check_grid(g, true);
     if (rc) return rc;

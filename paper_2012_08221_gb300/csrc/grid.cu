@@ -250,6 +250,7 @@ static int dev_upload(pdfgpu_grid *g, const T *host, size_t count, const T **dst
 
 extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
 {
+    PDF_TRACE("pdf_load_grid");
     clear_error();
     if (!desc || !out) return fail(PDF_E_ARG, "null argument");
     *out = nullptr;
@@ -474,6 +475,7 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
 
 extern "C" int pdf_bind_values(pdfgpu_grid_t g, const double *dev_values, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_bind_values");
     clear_error();
     int rc = check_grid(g, false);
     if (rc) return rc;
@@ -483,6 +485,7 @@ extern "C" int pdf_bind_values(pdfgpu_grid_t g, const double *dev_values, pdfgpu
 
 extern "C" int pdf_free_grid(pdfgpu_grid_t g)
 {
+    PDF_TRACE("pdf_free_grid");
     clear_error();
     if (!g) return fail(PDF_E_ARG, "null grid handle");
     cudaSetDevice(g->device);
@@ -502,6 +505,7 @@ extern "C" int pdf_free_grid(pdfgpu_grid_t g)
 extern "C" int pdf_grid_info(pdfgpu_grid_t g, int32_t *n_x, int32_t *n_rows, int32_t *n_flav,
                              int32_t *n_members, int32_t *has_alphas)
 {
+    PDF_TRACE("pdf_grid_info");
     clear_error();
     if (!g) return fail(PDF_E_ARG, "null grid handle");
     if (n_x) *n_x = g->d.nx;
@@ -514,6 +518,7 @@ extern "C" int pdf_grid_info(pdfgpu_grid_t g, int32_t *n_x, int32_t *n_rows, int
 
 extern "C" int pdf_get_status(pdfgpu_grid_t g, pdfgpu_stream_t stream, uint32_t *bits)
 {
+    PDF_TRACE("pdf_get_status");
     clear_error();
     int rc = check_grid(g, false);
     if (rc) return rc;

@@ -133,6 +133,7 @@ int read_member(const std::string &path, Member &m)
 extern "C" int pdf_lhapdf_open(const char *set_dir, int32_t first_member, int32_t n_members,
                                pdfgpu_lhapdf_t *out)
 {
+    PDF_TRACE("pdf_lhapdf_open");
     clear_error();
     if (!set_dir || !out || first_member < 0 || n_members < 1) return fail(PDF_E_ARG, "bad argument");
     *out = nullptr;
@@ -197,6 +198,7 @@ extern "C" int pdf_lhapdf_open(const char *set_dir, int32_t first_member, int32_
 
 extern "C" int pdf_lhapdf_desc(pdfgpu_lhapdf_t h, pdfgpu_grid_desc *desc)
 {
+    PDF_TRACE("pdf_lhapdf_desc");
     clear_error();
     if (!h || !desc) return fail(PDF_E_ARG, "null argument");
     memset(desc, 0, sizeof(*desc));
@@ -217,6 +219,7 @@ extern "C" int pdf_lhapdf_desc(pdfgpu_lhapdf_t h, pdfgpu_grid_desc *desc)
 
 extern "C" int pdf_lhapdf_close(pdfgpu_lhapdf_t h)
 {
+    PDF_TRACE("pdf_lhapdf_close");
     clear_error();
     if (!h) return fail(PDF_E_ARG, "null handle");
     delete h;

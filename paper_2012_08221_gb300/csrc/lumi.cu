@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
         int qc = cell / g.nxc, xc = cell - qc * g.nxc;
         int row = g.qrow[qc] - 1 + j, col = xc - 1 + i;
         bool ok = ((g.qmask[qc] >> j) & 1) && col >= 0 && col < g.nx;
+        if (ok) row = checked_index(g.status, row, g.nrows);
 #pragma unroll
         for (int b = 0; b < kF; ++b) {
             if (ok && b < F && santi[b] >= 0 && (dbits(acc[b]) << 1))
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
         if (r < end) {
             int rec = perm[r];
             int e = rec >> 1, side = rec & 1;
-            kr = key[rec];
+            kr = checked_index(g.status, key[rec], g.nqc * g.nxc);
             int qc = kr / g.nxc, xc = kr - qc * g.nxc;
             uint8_t f = fin[rec];
             Axis Q = axis_from(qc, tq[e], f & 1);
@@ -400,6 +401,7 @@ extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, c
                         int64_t n, double *lum, double *alphas, double *L, double *save_p,
                         pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_lumi");
     clear_error();
     Cols anti;
     int rc = lumi_common(g, member, ln_tau, y, n, &anti);
@@ -437,6 +439,7 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
                                  double ln_s, int64_t n, double dL, const double *saved_p,
                                  double *grad_values, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_lumi_backward");
     clear_error();
     Cols anti;
     int rc = lumi_common(g, member, ln_tau, y, n, &anti);

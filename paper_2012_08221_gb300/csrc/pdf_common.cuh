@@ -139,6 +139,22 @@ __device__ __forceinline__ int find_cell(const K *keys, int ncell, int step, K k
     return lo;
 }
 
+// Checked builds (-DPDFGPU_CHECKED, the library built with PDFGPU_CHECKED=1):
+// table indices computed on the device are tested before use; one out of
+// range sets PDF_S_BOUNDS in the grid's status word and is replaced by 0, so
+// that no access leaves its array (the result is then wrong, and the status
+// says so).  Release builds compile the tests away.
+#ifdef PDFGPU_CHECKED
+__device__ __forceinline__ int checked_index(unsigned *status, int i, int n)
+{
+    if (i >= 0 && i < n) return i;
+    atomicOr(status, (unsigned)PDF_S_BOUNDS);
+    return 0;
+}
+#else
+__device__ __forceinline__ int checked_index(unsigned *, int i, int) { return i; }
+#endif
+
 // Per-axis local coordinate and basis of one query.
 struct Axis {
     int cell;
@@ -190,7 +206,7 @@ __device__ __forceinline__ Axis axis_x(const GridDev &g, double x, double *u)
 {
     uint64_t b = dbits(x);
     Axis A;
-    A.cell = find_cell<uint64_t>(g.xbits, g.nxc, g.xstep, b);
+    A.cell = checked_index(g.status, find_cell<uint64_t>(g.xbits, g.nxc, g.xstep, b), g.nxc);
     A.in = (b >= g.xlo) & (b <= g.xhi);
     A.below = b < g.xlo;
     double uu = dlog(g, x);
@@ -205,7 +221,7 @@ __device__ __forceinline__ Axis axis_u(const GridDev &g, double u)
 {
     int64_t k = dkey(u);
     Axis A;
-    A.cell = find_cell<int64_t>(g.ukey, g.nxc, g.xstep, k);
+    A.cell = checked_index(g.status, find_cell<int64_t>(g.ukey, g.nxc, g.xstep, k), g.nxc);
     A.in = (k >= g.ulo) & (k <= g.uhi);
     A.below = k < g.ulo;
     double2 c = g.xcell[A.cell];
@@ -217,7 +233,7 @@ __device__ __forceinline__ Axis axis_q2(const GridDev &g, double q2, double *w)
 {
     uint64_t b = dbits(q2);
     Axis A;
-    A.cell = find_cell<uint64_t>(g.qbits, g.nqc, g.qstep, b);
+    A.cell = checked_index(g.status, find_cell<uint64_t>(g.qbits, g.nqc, g.qstep, b), g.nqc);
     A.in = (b >= g.qlo) & (b <= g.qhi);
     A.below = b < g.qlo;
     double ww = dlog(g, q2);
@@ -231,7 +247,7 @@ __device__ __forceinline__ Axis axis_w(const GridDev &g, double w)
 {
     int64_t k = dkey(w);
     Axis A;
-    A.cell = find_cell<int64_t>(g.wkey, g.nqc, g.qstep, k);
+    A.cell = checked_index(g.status, find_cell<int64_t>(g.wkey, g.nqc, g.qstep, k), g.nqc);
     A.in = (k >= g.wlo) & (k <= g.whi);
     A.below = k < g.wlo;
     double2 c = g.qcell[A.cell];
@@ -413,7 +429,8 @@ __device__ __forceinline__ bool out_of_range(const GridDev &g, const Axis &X, co
 
 __device__ __forceinline__ int pid_col(const GridDev &g, int pid)
 {
-    return (pid >= -64 && pid <= 64) ? (int)__ldg(g.pidmap + pid + 64) : -1;
+    int col = (pid >= -64 && pid <= 64) ? (int)__ldg(g.pidmap + pid + 64) : -1;
+    return col < 0 ? col : checked_index(g.status, col, g.nflav);
 }
 
 }  // namespace pdfgpu

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <mutex>
@@ -35,6 +36,17 @@ struct pdfgpu_grid {
 };
 
 namespace pdfgpu {
+
+// One NVTX range per ABI call, named after the entry point, so that a
+// profiler's timeline shows which call launched which kernels (a no-op when
+// no tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+#define PDF_TRACE(name) pdfgpu::TraceRange pdf_trace_range__(name)
 
 // Thread-local error message and return-code helpers.
 int fail(int code, const std::string &msg);

@@ -21,6 +21,7 @@ __global__ void k_dfma_chains(double *out, int iters, double b, double c)
 
 extern "C" int pdf_probe_fp64_peak(double *flops)
 {
+    PDF_TRACE("pdf_probe_fp64_peak");
     pdfgpu::clear_error();
     if (!flops) return pdfgpu::fail(PDF_E_ARG, "null output");
     int dev = 0, sms = 0;

@@ -213,6 +213,7 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
                                         int32_t n_bins, const double *edges, const double *v, int64_t n,
                                         double *sums, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_vegas_lumi_iteration");
     clear_error();
     int rc = check_grid(g, true);
     if (rc) return rc;
@@ -256,6 +257,7 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
 // carries an equal share of sum r_i, the old bins' shares spread uniformly.
 extern "C" int pdf_vegas_refine(const double *bin_w2, int32_t n_bins, double alpha, double *edges)
 {
+    PDF_TRACE("pdf_vegas_refine");
     clear_error();
     if (!bin_w2 || !edges) return fail(PDF_E_ARG, "null array");
     if (n_bins < 2 || n_bins > kMaxBins) return fail(PDF_E_RANGE, "n_bins must be in [2, 1024]");
@@ -289,6 +291,7 @@ extern "C" int pdf_vegas_refine(const double *bin_w2, int32_t n_bins, double alp
 extern "C" int pdf_vegas_map(int32_t dim, int32_t n_bins, const double *edges, const double *v, int64_t n,
                              double *r, double *jac, int32_t *bins, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_vegas_map");
     clear_error();
     if (dim < 1 || dim > kMaxVegasDim) return fail(PDF_E_RANGE, "dim must be in [1, 16]");
     if (n_bins < 2 || n_bins > kMaxBins) return fail(PDF_E_RANGE, "n_bins must be in [2, 1024]");
@@ -304,6 +307,7 @@ extern "C" int pdf_vegas_map(int32_t dim, int32_t n_bins, const double *edges, c
 extern "C" int pdf_vegas_accumulate(int32_t dim, int32_t n_bins, const double *w, const int32_t *bins,
                                     int64_t n, double *sums, pdfgpu_stream_t stream)
 {
+    PDF_TRACE("pdf_vegas_accumulate");
     clear_error();
     if (dim < 1 || dim > kMaxVegasDim) return fail(PDF_E_RANGE, "dim must be in [1, 16]");
     if (n_bins < 2 || n_bins > kMaxBins) return fail(PDF_E_RANGE, "n_bins must be in [2, 1024]");
