@@ -51,6 +51,13 @@
  *   direction is continued first (per edge column when u is out of range
  *   too), then u.
  *
+ * Pins: every step above is checked by the test suite against closed forms,
+ * invariants, an exact-rational brute force and central differences.  The
+ * one thing no pin can fix is the *choice* of the rules outside the grid
+ * (step 6 and its options): the paper is silent there, so that choice is
+ * parity unpinned; its implementation is pinned (linear and power-law data
+ * reproduced exactly, continuity at the edge).
+ *
  * Built with -O2 -ffp-contract=off (no fused multiply-add contraction, no
  * fast-math), parallelised over points with OpenMP in the batch drivers only.
  */
