@@ -233,6 +233,8 @@ def test_maximum_pid_count(nnpdf):
     wide = pdf.xfxQ2(pids, X, Q).cpu().numpy()
     base = pdf.xfxQ2(g.pids, X, Q).cpu().numpy()
     assert np.array_equal(wide, base[:, [k % g.n_flav for k in range(64)]])
+    parity.check(wide[:3000], o.xfxq2_batch(pids, x[:3000], q2[:3000]), o.kappa(pids, x[:3000], q2[:3000]),
+                 what="64 pids")
 
 
 def test_empty_and_tiny_batches(small):

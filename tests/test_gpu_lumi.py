@@ -92,7 +92,8 @@ def test_saved_partner_factors_give_the_same_gradient(lhc):
     one that recomputes them (up to the summation order of the atomics)."""
     from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
     g, pdf, o = lhc
-    ev = DeviceEvents.from_host(synth.events_lhc(50_003, seed=95))
+    evh = synth.events_lhc(50_003, seed=95)
+    ev = DeviceEvents.from_host(evh)
     P = torch.empty((ev.n, 2, g.n_flav), dtype=torch.float64, device="cuda")
     L1, lum1, _ = luminosity(pdf, ev, save_p=P)
     L0, lum0, _ = luminosity(pdf, ev)
@@ -102,6 +103,9 @@ def test_saved_partner_factors_give_the_same_gradient(lhc):
     luminosity_backward(pdf, ev, 2.0, ga)
     luminosity_backward(pdf, ev, 2.0, gb, saved_p=P)
     assert torch.allclose(ga, gb, rtol=1e-12, atol=1e-15 * float(ga.abs().max()))
+    ref = 2.0 * o.lumi_dgrid(evh)
+    kap = 2.0 * o.lumi_dgrid(evh, absval=True)
+    assert np.all(np.abs(gb.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kap) + 1e-300)
 
 
 def test_sixteen_flavours_with_an_unpaired_one(lhc):
@@ -143,8 +147,10 @@ def test_luminosity_autograd(lhc):
 
 def test_full_size_luminosity_sampled(lhc):
     """1e8 events in one launch: L equals the mean of the per-event values,
-    sampled events match the oracle, and the grid gradient obeys the exact
-    flavour sum rule sum_cells dL/dv[.][b] = mean_e(f_-b(x2) + f_-b(x1))."""
+    sampled events match the oracle, and the grid gradient (12 chunks of
+    events) obeys the exact flavour sum rule sum_cells dL/dv[.][b] =
+    mean_e(f_-b(x2) + f_-b(x1)) with the right-hand side from the oracle (the
+    interpolation's weights sum to 1), for the gluon and the u quark."""
     from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
     g, pdf, o = lhc
     n = 100_000_000
@@ -162,22 +168,24 @@ def test_full_size_luminosity_sampled(lhc):
     gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
     luminosity_backward(pdf, dev, 1.0, gv)
     G = gv.cpu().numpy()
-    # sum rule from the forward kernel on the same points (x from ln x)
+    # sum rule, right-hand side from the oracle on the same partons, for the
+    # gluon (its own partner) and the u quark (partner u-bar)
     u1, u2, w = _event_logs(ev, n)
-    anti = [list(g.pids).index(-p) for p in g.pids]
-    acc = np.zeros(g.n_flav)
-    acc_abs = np.zeros(g.n_flav)
+    pids = list(g.pids)
+    cols = [pids.index(0), pids.index(2)]
+    partners = np.array([0, -2], dtype=np.int32)
+    acc = np.zeros(2)
+    acc_abs = np.zeros(2)
     step = 10_000_000
     for s in range(0, n, step):
-        X1, X2, Q2 = cuda(np.exp(u1[s:s + step])), cuda(np.exp(u2[s:s + step])), cuda(np.exp(w[s:s + step]))
-        f1 = pdf.xfxQ2(g.pids, X1, Q2).sum(0).cpu().numpy()
-        f2 = pdf.xfxQ2(g.pids, X2, Q2).sum(0).cpu().numpy()
-        acc += f1 + f2
-        a1 = pdf.xfxQ2(g.pids, X1, Q2).abs().sum(0).cpu().numpy()
-        acc_abs += a1
-    for b in range(g.n_flav):
-        want = acc[anti[b]] / n
-        assert abs(G[:, :, b].sum() - want) <= 1e-9 * (abs(want) + acc_abs[anti[b]] / n)
+        q2 = np.exp(w[s:s + step])
+        f1 = o.xfxq2_batch(partners, np.exp(u1[s:s + step]), q2)
+        f2 = o.xfxq2_batch(partners, np.exp(u2[s:s + step]), q2)
+        acc += f1.sum(0) + f2.sum(0)
+        acc_abs += np.abs(f1).sum(0) + np.abs(f2).sum(0)
+    for k, b in enumerate(cols):
+        want = acc[k] / n
+        assert abs(G[:, :, b].sum() - want) <= 1e-9 * (abs(want) + acc_abs[k] / n)
 
 
 def test_other_members_forward_and_gradient(lhc):
