@@ -7,7 +7,8 @@ full device and can synchronise the whole device).  `pdf_batch_run_noalloc`
 runs the batched kernel with its scratch (tile ticket, request and grid
 tables) in a fixed static device array instead.  This test checks it against
 the regular prepared batch (`pdf_batch_prepare` + `pdf_batch_run`) on two
-calls in a row, and that it refuses requests beyond its fixed capacity.
+calls in a row and against the oracle on a sample, and that it refuses
+requests beyond its fixed capacity.
 
 This file is collected last on purpose: it must pass alone in a fresh process
 and after every other test.
@@ -17,6 +18,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+from oracle.oracle import OracleGrid
 from paper_2012_08221_gb300 import synth
 from tests import parity
 
@@ -74,6 +76,14 @@ def test_noalloc_batch_matches_prepared_batch_twice():
             ref = r_ref[5].cpu().numpy()
             got = r_new[5].cpu().numpy()
             parity.check(got, ref, np.abs(ref), what=f"no-alloc call {call}")
+    # and against the oracle on the first points of every tenth request
+    orcs = [OracleGrid.from_synth(g) for g in grids]
+    for b, r in list(zip(batches, new_reqs))[::10]:
+        m = min(b.x.size, 500)
+        o = orcs[b.set_index]
+        want = o.xfxq2_batch(b.pids, b.x[:m], b.q2[:m], member=b.member)
+        kap = o.kappa(b.pids, b.x[:m], b.q2[:m], member=b.member)
+        parity.check(r[5][:m].cpu().numpy(), want, kap, what="no-alloc vs oracle")
 
 
 def test_noalloc_after_a_narrower_prepared_batch():
