@@ -12,7 +12,8 @@ forward+backward (pointwise, 1e7 points, autograd adjoint), the batched
 graph-captured launch (400 uneven requests over 3 grids), the fused
 luminosity (1e8 events, forward and forward+backward), VEGAS on the fused
 luminosity, and VEGAS around a single-top-like integrand written as user
-code.
+code.  "sweep" holds the x*f throughput against the number of points (1e3 to
+1e8, the paper's Fig. 2 axis), with the oracle's under cpu_baseline.
 
 Timing: W warm-up steps, then K steps between a barrier + synchronize and
 CUDA events on the launching stream; the max over ranks is reported.  Inputs
@@ -280,6 +281,7 @@ def main():
     ap.add_argument("--forms", default="all",
                     help="comma list of fwdbwd,batched,lumi,vegas,vegas_user or all/none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the throughput-against-length sweep")
     ap.add_argument("--points", type=int, default=N_POINTS,
                     help="points of the headline workload (smaller only for profiling captures)")
     ap.add_argument("--lumi-events", type=int, default=100_000_000,
@@ -383,6 +385,26 @@ def main():
                 "algorithmic_bytes": bytes_launch,
                 "hbm_frac": (bytes_launch / (k_ms * 1e-3)) / (peaks().get("hbm_gbs", 6790.7) * 1e9),
                 "kernel_ms": k_ms}
+
+    # --------------------------- throughput against the query length (Fig. 2)
+    sweep = None
+    if not args.no_sweep:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2010)
+        sweep = {"what": "xfxQ2 over 13 flavours on the NNPDF-shaped grid against the number of points "
+                         "(ln x ~ U[ln 1e-8, 0), ln Q^2 ~ U[0, ln 1e10]); below ~1e6 points the inputs and "
+                         "outputs stay in L2 and the launch is latency-bound",
+                 "n": [], "ms": [], "evals_per_s": [], "fp64_frac": []}
+        for n_s in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7, 10 ** 8):
+            Xs = torch.exp(torch.rand(n_s, generator=gen, dtype=torch.float64, device=dev) * math.log(1e-8))
+            Qs = torch.exp(torch.rand(n_s, generator=gen, dtype=torch.float64, device=dev) * math.log(1e10))
+            Os = torch.empty((n_s, g.n_flav), dtype=torch.float64, device=dev)
+            ms_s, _ = timed(lambda: pdf.xfxQ2(pids, Xs, Qs, out=Os), 5 if n_s >= 10 ** 8 else 20, args.warmup)
+            sweep["n"].append(n_s)
+            sweep["ms"].append(ms_s)
+            sweep["evals_per_s"].append(world * n_s * g.n_flav / (ms_s * 1e-3))
+            sweep["fp64_frac"].append(n_s * work.xfxq2_point_flops(g.n_flav) / (ms_s * 1e-3) / peak)
+            del Xs, Qs, Os
 
     forms = {}
     want = set(["fwdbwd", "batched", "lumi", "vegas", "vegas_user"] if args.forms == "all" else
@@ -593,6 +615,14 @@ def main():
         rate, done, dt = cpu_oracle_rate((x, q2), cores, budget_s=10.0)
         cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
                "sample": f"first {done} points of the 1e7-point workload x 13 flavours ({dt:.1f} s)"}
+        if sweep is not None:
+            # the oracle against the query length, as the GPU sweep (small N only)
+            cs = {"n": [], "evals_per_s": []}
+            for n_s in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6):
+                r_s, _, _ = cpu_oracle_rate((x, q2), cores, budget_s=None, max_points=n_s)
+                cs["n"].append(n_s)
+                cs["evals_per_s"].append(r_s)
+            cpu["sweep"] = cs
         if forms:
             fcpu = forms_cpu_baselines(cores)
             for k in forms:
@@ -611,7 +641,7 @@ def main():
                            "n_points": npts, "n_flav": int(g.n_flav), "alphas_points": npts, "parallelism": f"replicas x{world}",
                            "l2": "inputs + outputs of a step (1.36 GB) exceed the 129 MB L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 2 * args.steps, "clocks": clk, "forms": forms}
+                "gpu_launches": 2 * args.steps, "clocks": clk, "forms": forms, "sweep": sweep}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
