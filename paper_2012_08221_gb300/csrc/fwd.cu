@@ -75,6 +75,56 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
     if (lane == 0) bulk_wait_all();
 }
 
+// Small queries (at most kPairMax point-flavour pairs): one thread per pair,
+// so that a few thousand points still spread over every SM and each thread's
+// dependent chain is one flavour long; the coordinates are recomputed for
+// every flavour of a point.  Outputs are written in pair order, which is the
+// row-major [n][npid] layout.
+constexpr int64_t kPairMax = 1 << 18;
+
+template <bool Q_IS_Q, bool CONT>
+__global__ void __launch_bounds__(kBlock) k_xfxq2_pairs(GridDev g, Cols cols, int npid, int member,
+                                                        const double *__restrict__ x,
+                                                        const double *__restrict__ q,
+                                                        int64_t n, double *__restrict__ out)
+{
+    __shared__ signed char scol[PDF_MAX_PIDS];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < PDF_MAX_PIDS; ++k) scol[k] = cols.c[k];
+    }
+    __syncthreads();
+    const size_t cell_stride = (size_t)g.nflav * 16;
+    const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
+    const int64_t total = n * npid;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = p / npid;
+        const int a = (int)(p - i * npid);
+        double xi = x[i], qi = q[i];
+        if (Q_IS_Q) qi = qi * qi;
+        bool bad = !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
+        flag_status(g, bad);
+        if (bad) {
+            xi = 0.5;
+            qi = 10.0;
+        }
+        double u, w;
+        Axis X = axis_x(g, xi, &u);
+        Axis Q = axis_q2(g, qi, &w);
+        const bool oor = out_of_range(g, X, Q);
+        flag_status(g, oor, PDF_S_RANGE);
+        bad |= oor;
+        int col = scol[a];
+        double v = 0.0;
+        if (col >= 0) {
+            col = checked_index(g.status, col, g.nflav);
+            v = patch_any<CONT>(g, cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
+        }
+        out[p] = bad ? qnan() : v;
+    }
+}
+
 template <bool CONT>
 __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
                                                      const int *__restrict__ pid,
@@ -178,9 +228,17 @@ int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n
     if (rc) return rc;
     if (n == 0) return PDF_OK;
     if (!x || !q || !out) return fail(PDF_E_ARG, "null array");
-    size_t smem = (size_t)kBlock * n_pid * sizeof(double);
     using Kern = void (*)(GridDev, Cols, int, int, const double *, const double *, int64_t, double *);
     const bool cont = g->d.extrap == PDF_EXTRAP_CONTINUATION;
+    if (n * n_pid <= kPairMax) {
+        Kern k = q_is_q ? (cont ? k_xfxq2_pairs<true, true> : k_xfxq2_pairs<true, false>)
+                        : (cont ? k_xfxq2_pairs<false, true> : k_xfxq2_pairs<false, false>);
+        int grid = wave_grid(g, (const void *)k, kBlock, 0, n * n_pid);
+        k<<<grid, kBlock, 0, s>>>(g->d, cols, n_pid, member, x, q, n, out);
+        PDF_CUDA(cudaGetLastError());
+        return PDF_OK;
+    }
+    size_t smem = (size_t)kBlock * n_pid * sizeof(double);
     Kern k = q_is_q ? (cont ? k_xfxq2<true, true> : k_xfxq2<true, false>)
                     : (cont ? k_xfxq2<false, true> : k_xfxq2<false, false>);
     rc = allow_dynamic_smem((const void *)k, smem);
