@@ -394,7 +394,9 @@ def main():
         sweep = {"what": "xfxQ2 over 13 flavours on the NNPDF-shaped grid against the number of points "
                          "(ln x ~ U[ln 1e-8, 0), ln Q^2 ~ U[0, ln 1e10]); below ~1e6 points the inputs and "
                          "outputs stay in L2 and the launch is latency-bound",
-                 "n": [], "ms": [], "evals_per_s": [], "fp64_frac": []}
+                 "n": [], "ms": [], "evals_per_s": [], "fp64_frac": [],
+                 "ms_graph": [], "note_graph": "the same call captured once in a CUDA graph and replayed: "
+                                               "the host-side cost of the Python call left out"}
         for n_s in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7, 10 ** 8):
             Xs = torch.exp(torch.rand(n_s, generator=gen, dtype=torch.float64, device=dev) * math.log(1e-8))
             Qs = torch.exp(torch.rand(n_s, generator=gen, dtype=torch.float64, device=dev) * math.log(1e10))
@@ -404,7 +406,12 @@ def main():
             sweep["ms"].append(ms_s)
             sweep["evals_per_s"].append(world * n_s * g.n_flav / (ms_s * 1e-3))
             sweep["fp64_frac"].append(n_s * work.xfxq2_point_flops(g.n_flav) / (ms_s * 1e-3) / peak)
-            del Xs, Qs, Os
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                pdf.xfxQ2(pids, Xs, Qs, out=Os)
+            ms_g, _ = timed(graph.replay, 5 if n_s >= 10 ** 8 else 20, args.warmup)
+            sweep["ms_graph"].append(ms_g)
+            del Xs, Qs, Os, graph
 
     forms = {}
     want = set(["fwdbwd", "batched", "lumi", "vegas", "vegas_user"] if args.forms == "all" else
