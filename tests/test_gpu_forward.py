@@ -336,3 +336,25 @@ def test_cuda_graph_capture_and_replay(nnpdf):
         torch.cuda.synchronize()
         assert torch.equal(OUT, pdf.xfxQ2(g.pids, cuda(x2), cuda(q22)))
         assert torch.equal(AS, pdf.alphasQ2(cuda(qa2)))
+
+
+def test_small_query_kernel_matches_the_per_point_kernel(nnpdf):
+    """Queries of at most 2^18 point-flavour pairs run one thread per pair;
+    larger ones one thread per point.  The same points give the same bits
+    both ways (the value of a point does not depend on the batch it is in),
+    and the small launch matches the oracle, for x*f and x*f(Q)."""
+    g, pdf, o = nnpdf
+    x, q2, _ = synth.queries_nnpdf(100_003, seed=17)
+    X, Q = cuda(x), cuda(q2)
+    big = pdf.xfxQ2(g.pids, X, Q)                        # 100003 x 13 pairs: per point
+    for n in (1, 31, 1001, (1 << 18) // g.n_flav):       # per pair
+        small = pdf.xfxQ2(g.pids, X[:n].clone(), Q[:n].clone())
+        assert torch.equal(torch.nan_to_num(small, nan=7.0), torch.nan_to_num(big[:n], nan=7.0)), n
+    n = 1001
+    got = pdf.xfxQ2(g.pids, X[:n], Q[:n]).cpu().numpy()
+    parity.check(got, o.xfxq2_batch(g.pids, x[:n], q2[:n]), o.kappa(g.pids, x[:n], q2[:n]),
+                 what="small query xfxQ2")
+    q = torch.sqrt(Q)
+    assert torch.equal(pdf.xfxQ(g.pids, X[:n], q[:n]), pdf.xfxQ(g.pids, X, q)[:n])
+    three = np.array([21, -1, 2], dtype=np.int32)            # 100003 x 3 > 2^18 pairs
+    assert torch.equal(pdf.xfxQ2(three, X[:n], Q[:n]), pdf.xfxQ2(three, X, Q)[:n])
