@@ -130,6 +130,28 @@ def cpu_oracle_rate(points, cores, budget_s=10.0, chunk=200_000, max_points=None
     return done * g.n_flav / dt, done, dt
 
 
+def host_cpu_model():
+    """The host CPU's name from /proc/cpuinfo ("model name" on x86; the
+    implementer and part numbers on Arm), else the platform's machine name."""
+    import platform
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.machine()
+    fields = {}
+    for line in txt.splitlines():
+        k, _, v = line.partition(":")
+        k, v = k.strip(), v.strip()
+        if k and v and k not in fields:
+            fields[k] = v
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return (f"{platform.machine()} CPU implementer {fields.get('CPU implementer', '?')} "
+                f"part {fields['CPU part']}")
+    return platform.machine()
+
+
 def _timed_rate(fn, units):
     t0 = time.perf_counter()
     fn()
@@ -620,8 +642,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
         rate, done, dt = cpu_oracle_rate((x, q2), cores, budget_s=10.0)
+        rate1, done1, dt1 = cpu_oracle_rate((x, q2), 1, budget_s=3.0, chunk=20_000)
         cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {done} points of the 1e7-point workload x 13 flavours ({dt:.1f} s)"}
+               "sample": f"first {done} points of the 1e7-point workload x 13 flavours ({dt:.1f} s)",
+               "cpu_model": host_cpu_model(),
+               "single_core": {"value": rate1, "unit": "evals/s",
+                               "sample": f"first {done1} points, one thread ({dt1:.1f} s)"}}
         if sweep is not None:
             # the oracle against the query length, as the GPU sweep (small N only)
             cs = {"n": [], "evals_per_s": []}
