@@ -358,3 +358,40 @@ def test_small_query_kernel_matches_the_per_point_kernel(nnpdf):
     assert torch.equal(pdf.xfxQ(g.pids, X[:n], q[:n]), pdf.xfxQ(g.pids, X, q)[:n])
     three = np.array([21, -1, 2], dtype=np.int32)            # 100003 x 3 > 2^18 pairs
     assert torch.equal(pdf.xfxQ2(three, X[:n], Q[:n]), pdf.xfxQ2(three, X, Q)[:n])
+
+
+def test_more_than_two_to_the_31_outputs(nnpdf):
+    """Offsets past 32 bits: x*f over n points with n*13 > 2^31 outputs, and
+    alpha_s over more than 2^31 points.  The inputs tile a seeded base set on
+    the device, so every sampled output (spread over the array, around the
+    2^31 boundary and at the very end) must match the oracle at its base
+    point."""
+    g, pdf, o = nnpdf
+    base = 1_000_003
+    x, q2, _ = synth.queries_nnpdf(base, seed=19)
+    reps = 166
+    X, Q = cuda(x).repeat(reps), cuda(q2).repeat(reps)
+    n = X.numel()
+    assert n * g.n_flav > 2 ** 31
+    out = pdf.xfxQ2(g.pids, X, Q)
+    del X, Q
+    rng = np.random.default_rng(23)
+    edge = 2 ** 31 // g.n_flav
+    idx = np.concatenate([rng.choice(n, 400, replace=False), np.arange(edge - 40, edge + 40),
+                          np.arange(n - 200, n)])
+    got = out[cuda(idx)].cpu().numpy()
+    del out
+    b = idx % base
+    parity.check(got, o.xfxq2_batch(g.pids, x[b], q2[b]), o.kappa(g.pids, x[b], q2[b]),
+                 what="x*f beyond 2^31 outputs")
+    reps_a = 2 ** 31 // base + 2
+    QA = cuda(q2).repeat(reps_a)
+    na = QA.numel()
+    assert na > 2 ** 31
+    a_s = pdf.alphasQ2(QA)
+    del QA
+    idx = np.concatenate([rng.choice(na, 400, replace=False), np.arange(2 ** 31 - 40, 2 ** 31 + 40),
+                          np.arange(na - 200, na)])
+    got = a_s[cuda(idx)].cpu().numpy()
+    ref = o.alphas_batch(q2[idx % base])
+    parity.check(got, ref, 8 * np.abs(ref), what="alpha_s beyond 2^31 points")
