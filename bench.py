@@ -9,8 +9,9 @@ further points: `xfxQ2` + `alphasQ2` through the C ABI on device-resident
 inputs.  `value` = x*f evaluations per second over all ranks; "alphas" times
 the alpha_s launch alone; "e2e" times the same step from pinned host memory
 (copies in and out inside the timed region).  The other forms
-of the hot path are timed in the same run and reported under "forms":
-forward+backward (pointwise, 1e7 points, autograd adjoint), the batched
+of the hot path are timed in the same run and reported under "forms": the
+small 50 x 20 grid (1e5 points x 11 flavours + alpha_s, L2 flushed before each
+step), forward+backward (pointwise, 1e7 points, autograd adjoint), the batched
 graph-captured launch (400 uneven requests over 3 grids), the fused
 luminosity (1e8 events, forward and forward+backward), VEGAS on the fused
 luminosity, and VEGAS around a single-top-like integrand written as user
@@ -169,6 +170,16 @@ def forms_cpu_baselines(cores):
     from paper_2012_08221_gb300 import synth
     set_threads(cores)
     out = {}
+    g1 = synth.grid_small()
+    o1 = OracleGrid.from_synth(g1)
+    x1, q1 = synth.queries_small()
+
+    def small():
+        o1.xfxq2_batch(g1.pids, x1, q1)
+        o1.alphas_batch(q1)
+    small()
+    out["small"] = {"value": _timed_rate(small, x1.size * g1.n_flav), "unit": "evals/s", "cores": cores,
+                    "kind": "oracle", "sample": f"the whole workload ({x1.size} points and alpha_s)"}
     gs = synth.grid_small(seed=1003, pids=synth.PIDS_13)
     o3 = OracleGrid.from_synth(gs)
     pid, x, q2, w = synth.queries_pointwise(20_000)
@@ -303,7 +314,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--forms", default="all",
-                    help="comma list of fwdbwd,batched,lumi,vegas,vegas_user or all/none")
+                    help="comma list of small,fwdbwd,batched,lumi,vegas,vegas_user or all/none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the throughput-against-length sweep")
     ap.add_argument("--points", type=int, default=N_POINTS,
@@ -447,8 +458,58 @@ def main():
             del Xs, Qs, Os, graph
 
     forms = {}
-    want = set(["fwdbwd", "batched", "lumi", "vegas", "vegas_user"] if args.forms == "all" else
+    want = set(["small", "fwdbwd", "batched", "lumi", "vegas", "vegas_user"] if args.forms == "all" else
                ([] if args.forms == "none" else args.forms.split(",")))
+
+    # ------------------------- the small grid: 50 x 20 knots, 11 flavours
+    if "small" in want:
+        g1 = synth.grid_small()
+        p1 = PDF.from_grid(g1, device=dev)
+        x1h, q1h = synth.queries_small()
+        n1 = x1h.size
+        X1, Q1 = torch.as_tensor(x1h, device=dev), torch.as_tensor(q1h, device=dev)
+        O1 = torch.empty((n1, g1.n_flav), dtype=torch.float64, device=dev)
+        A1 = torch.empty(n1, dtype=torch.float64, device=dev)
+        flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)     # 256 MB > L2
+
+        def step1():
+            p1.xfxQ2(g1.pids, X1, Q1, out=O1)
+            p1.alphasQ2(Q1, out=A1)
+
+        def flushed(fn, K):
+            """Mean device time of fn, L2 flushed before each call (outside
+            the events)."""
+            for _ in range(args.warmup):
+                fn()
+            barrier()
+            evs = []
+            for _ in range(K):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                evs.append((a, b))
+            barrier()
+            return max_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
+
+        ms1 = flushed(step1, 20)
+        graph1 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph1):
+            step1()
+        ms1g = flushed(graph1.replay, 20)
+        forms["small"] = {
+            "workload": f"50 x 20 grid (x in [1e-7, 1], one Q subgrid [1.65, 1e4] GeV), {g1.n_flav} flavours; "
+                        f"{n1} points x {g1.n_flav} flavours + alpha_s at the same {n1} Q^2",
+            "value": whole_job_rate(n1 * g1.n_flav, world, ms1), "unit": "evals/s", "ms_per_step": ms1,
+            "ms_graph": ms1g, "value_graph": whole_job_rate(n1 * g1.n_flav, world, ms1g),
+            "fp64_frac": n1 * (work.xfxq2_point_flops(g1.n_flav) + work.alphas_point_flops())
+                         / (ms1 * 1e-3) / peak,
+            "l2": "flushed (256 MB write) before every timed step; the step's data fit in L2",
+            "note": "1e5 points occupy about half of one wave of resident threads (152 SMs x 1280): "
+                    "the time is mostly one thread's latency (11 patches after coefficient loads that "
+                    "miss the flushed L2)"}
+        del flush, graph1
 
     # --------------------------------------------------- forward + backward
     if "fwdbwd" in want:
