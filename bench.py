@@ -521,31 +521,43 @@ def main():
         O3 = torch.empty(x3.size, dtype=torch.float64, device=dev)
         GV = torch.zeros(gs.values.shape[1:], dtype=torch.float64, device=dev)
 
+        T3 = p3.new_tape(x3.size)            # the forward's adjoint tape (32 B per point)
+
         def step3():
             p3.bind_values(V3)
-            p3.xfxQ2_pw(P3, X3, Q3, out=O3)
+            p3.xfxQ2_pw(P3, X3, Q3, out=O3, tape=T3)
             GV.zero_()
-            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV)
+            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV, tape=T3)
 
         def kstep3(a, b):
             p3.bind_values(V3)
-            p3.xfxQ2_pw(P3, X3, Q3, out=O3)
+            p3.xfxQ2_pw(P3, X3, Q3, out=O3, tape=T3)
             GV.zero_()
             a.record(stream)
-            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV)
+            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV, tape=T3)
             b.record(stream)
 
+        def step3n():                        # the same without the tape
+            p3.bind_values(V3)
+            p3.xfxQ2_pw(P3, X3, Q3, out=O3)
+            GV.zero_()
+            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV)
+
         ms3, kb = timed(step3, args.steps, args.warmup, kstep3)
+        ms3n, _ = timed(step3n, max(3, args.steps // 2), args.warmup)
         n3 = x3.size
-        fl = n3 * (work.pw_fwd_point_flops() + work.pw_bwd_point_flops())
+        fl = n3 * (work.pw_fwd_point_flops() + work.pw_bwd_tape_point_flops())
         forms["fwd_bwd"] = {
             "workload": "pointwise x*f and its adjoint (dL/dx, dL/dQ^2, dL/dgrid) at 1e7 points, "
                         "50x20 grid, 13 flavours, L = sum w_i xf_{a_i}",
             "value": world * n3 / (ms3 * 1e-3), "unit": "evals/s (fwd+bwd)", "ms_per_step": ms3,
             "fp64_frac": (fl / (ms3 * 1e-3)) / peak,
-            "bwd_kernel": {"kernel": "k_bwd", "ms": kb,
-                           "frac": n3 * work.pw_bwd_point_flops() / (kb * 1e-3) / peak}}
-        del P3, X3, Q3, W3, O3
+            "bwd_kernel": {"kernel": "k_bwd (from the tape)", "ms": kb,
+                           "frac": n3 * work.pw_bwd_tape_point_flops() / (kb * 1e-3) / peak},
+            "tape": "the forward pass writes 32 bytes per point (cells, local coordinates, flags) that the "
+                    "adjoint reads instead of searching the knots and taking logarithms again",
+            "without_tape": {"ms_per_step": ms3n, "value": world * n3 / (ms3n * 1e-3)}}
+        del P3, X3, Q3, W3, O3, T3
 
     # ------------------------------------------------------------- batched
     if "batched" in want:

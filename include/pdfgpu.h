@@ -212,6 +212,35 @@ int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t
                    const double *grad_out, double *grad_x, double *grad_q2,
                    double *grad_values, pdfgpu_stream_t stream);
 
+/* Adjoint tape (an addition beyond the paper, for the differentiation above):
+ * the forward calls below are xfxQ2 / xfxQ2_pw that also write, per point, a
+ * 32-byte record of what the adjoint needs about the point's position in the
+ * grid (both cells, both local coordinates, range and domain flags), so that
+ * xfxQ2_backward_tape skips the knot searches and logarithms.
+ *   tape DEVICE [n][4] doubles, caller-owned, 32-byte aligned (PDF_E_ARG
+ *   otherwise); its content is private to the library.  A tape depends on
+ *   the points, the grid's knots and its extrapolation option only, not on
+ *   the member or the values: it stays valid across pdf_bind_values and for
+ *   every member of the grid.  PDF_E_ARG for a grid loaded with
+ *   PDF_EXTRAP_CONTINUATION (which has no adjoint) and for a NULL tape.
+ * Outputs of the forward calls are bit for bit those of xfxQ2 / xfxQ2_pw. */
+int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+               const double *x, const double *q2, int64_t n, double *out, double *tape,
+               pdfgpu_stream_t stream);
+int xfxQ2_pw_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
+                  const double *q2, int64_t n, double *out, double *tape, pdfgpu_stream_t stream);
+
+/* xfxQ2_backward from the tape a forward call wrote for the same grid and the
+ * same points (x and q2 are still read, for the chain rule of grad_x and
+ * grad_q2).  Same arguments and results as xfxQ2_backward, bit for bit in
+ * grad_x and grad_q2.  A tape of other points or another grid gives wrong
+ * numbers; its cells are clamped into the grid's tables, so no access leaves
+ * them. */
+int xfxQ2_backward_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                        int32_t pointwise, const double *x, const double *q2, int64_t n,
+                        const double *tape, const double *grad_out, double *grad_x,
+                        double *grad_q2, double *grad_values, pdfgpu_stream_t stream);
+
 /* One request of a batched evaluation (several grids, members, flavour
  * subsets and sizes in one launch).  grid/member/pids are read at prepare
  * time; x, q2, out are DEVICE pointers that must stay valid while the batch

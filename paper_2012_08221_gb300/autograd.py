@@ -4,26 +4,33 @@
 the forward rebuilds the interpolation coefficients from the tensor and runs
 the forward kernel; the backward runs the hand-written adjoint kernel, which
 returns dL/dx, dL/dQ^2 and the scatter of the 16 bicubic stencil weights
-into dL/dvalues (the derivative a PDF fit needs).  ``LumiFn`` does the same
+into dL/dvalues (the derivative a PDF fit needs).  The forward keeps a
+32-byte adjoint tape per point (cells, local coordinates, flags), so that the
+backward does not search the knots or take logarithms again.  ``LumiFn`` does the same
 for the fused luminosity workload, L = (1/n) sum_e sum_a f_a(x1) f_-a(x2).
 """
 from __future__ import annotations
 
 import torch
 
+from ._lib import EXTRAP
 from .pdf import PDF
 
 
 class XfxQ2Fn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, values, x, q2, pdf: PDF, pids, member: int, pointwise: bool):
+    def forward(ctx, values, x, q2, pdf: PDF, pids, member: int, pointwise: bool, use_tape: bool = True):
         pdf.bind_values(values)
+        # the adjoint tape (32 bytes per point) saves the backward pass the
+        # knot searches and logarithms; the power-law continuation has no
+        # adjoint, so it gets none
+        tape = pdf.new_tape(x.numel()) if use_tape and pdf.extrap != EXTRAP["continuation"] else None
         if pointwise:
-            out = pdf.xfxQ2_pw(pids, x, q2, member)
+            out = pdf.xfxQ2_pw(pids, x, q2, member, tape=tape)
         else:
-            out = pdf.xfxQ2(pids, x, q2, member)
+            out = pdf.xfxQ2(pids, x, q2, member, tape=tape)
         ctx.save_for_backward(values, x, q2)
-        ctx.pdf, ctx.pids, ctx.member, ctx.pointwise = pdf, pids, member, pointwise
+        ctx.pdf, ctx.pids, ctx.member, ctx.pointwise, ctx.tape = pdf, pids, member, pointwise, tape
         return out
 
     @staticmethod
@@ -38,18 +45,18 @@ class XfxQ2Fn(torch.autograd.Function):
             gvals = torch.zeros_like(values)
             gslice = gvals[ctx.member] if values.dim() == 4 else gvals
         gx, gq, _ = pdf.xfxQ2_backward(ctx.pids, x, q2, gout, ctx.member, ctx.pointwise,
-                                       grad_x=need_x, grad_q2=need_q, grad_values=gslice)
-        return gvals, gx, gq, None, None, None, None
+                                       grad_x=need_x, grad_q2=need_q, grad_values=gslice, tape=ctx.tape)
+        return gvals, gx, gq, None, None, None, None, None
 
 
-def xfxQ2(pdf: PDF, values, pids, x, q2, member: int = 0):
+def xfxQ2(pdf: PDF, values, pids, x, q2, member: int = 0, use_tape: bool = True):
     """Differentiable x*f for a shared pid list: ``[n][len(pids)]``."""
-    return XfxQ2Fn.apply(values, x, q2, pdf, pids, member, False)
+    return XfxQ2Fn.apply(values, x, q2, pdf, pids, member, False, use_tape)
 
 
-def xfxQ2_pw(pdf: PDF, values, pid, x, q2, member: int = 0):
+def xfxQ2_pw(pdf: PDF, values, pid, x, q2, member: int = 0, use_tape: bool = True):
     """Differentiable x*f with one pid per point: ``[n]``."""
-    return XfxQ2Fn.apply(values, x, q2, pdf, pid, member, True)
+    return XfxQ2Fn.apply(values, x, q2, pdf, pid, member, True, use_tape)
 
 
 class AlphasFn(torch.autograd.Function):

@@ -11,7 +11,10 @@
 // formulas with the linear basis give the derivatives of the linear
 // continuation.  The grid gradient is accumulated with FP64 atomics, either
 // into a shared-memory copy per CTA (flushed once at the end) when the
-// member's gradient fits, or straight into global memory.
+// member's gradient fits, or straight into global memory.  Given the tape of
+// the forward pass over the same points, the adjoint rebuilds each point's
+// cells and local coordinates from it instead of searching the knots and
+// taking the two logarithms again; the arithmetic that follows is the same.
 #include <math.h>
 
 #include <algorithm>
@@ -27,11 +30,12 @@ constexpr size_t kSmemGradMax = 200 * 1024;
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000000000000ll); }
 
-template <bool PW, bool SMEM>
+template <bool PW, bool SMEM, bool TAPE>
 __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, int member,
                                                 const int *__restrict__ pid,
                                                 const double *__restrict__ x,
                                                 const double *__restrict__ q2, int64_t n,
+                                                const double *__restrict__ tape,
                                                 const double *__restrict__ gout,
                                                 double *__restrict__ gx, double *__restrict__ gq,
                                                 double *__restrict__ gval)
@@ -52,19 +56,28 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double xi = x[i], qi = q2[i];
-        bool bad = !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
-        if (bad) {
-            if (gx) gx[i] = qnan();
-            if (gq) gq[i] = qnan();
-            continue;
-        }
-        double u, w;
-        Axis X = axis_x(g, xi, &u);
-        Axis Q = axis_q2(g, qi, &w);
-        if (out_of_range(g, X, Q)) {
-            if (gx) gx[i] = qnan();
-            if (gq) gq[i] = qnan();
-            continue;
+        Axis X, Q;
+        if (TAPE) {
+            if (tape_get(g, tape, i, X, Q)) {
+                if (gx) gx[i] = qnan();
+                if (gq) gq[i] = qnan();
+                continue;
+            }
+        } else {
+            bool bad = !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
+            if (bad) {
+                if (gx) gx[i] = qnan();
+                if (gq) gq[i] = qnan();
+                continue;
+            }
+            double u, w;
+            X = axis_x(g, xi, &u);
+            Q = axis_q2(g, qi, &w);
+            if (out_of_range(g, X, Q)) {
+                if (gx) gx[i] = qnan();
+                if (gq) gq[i] = qnan();
+                continue;
+            }
         }
         // derivative bases: (0, 1, 2t, 3t^2) inside; outside (0, 1, 1, 1) for
         // the linear continuation, and no derivative across a frozen edge
@@ -123,25 +136,59 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
     }
 }
 
-template <bool PW>
+template <bool PW, bool TAPE>
 int launch(pdfgpu_grid *g, const Cols &cols, int npid, int member, const int *pid, const double *x,
-           const double *q2, int64_t n, const double *gout, double *gx, double *gq, double *gval,
-           cudaStream_t s)
+           const double *q2, int64_t n, const double *tape, const double *gout, double *gx, double *gq,
+           double *gval, cudaStream_t s)
 {
     size_t gbytes = (size_t)g->d.nrows * g->d.nx * g->d.nflav * sizeof(double);
     if (gval && gbytes <= kSmemGradMax) {
-        const void *kern = (const void *)k_bwd<PW, true>;
+        const void *kern = (const void *)k_bwd<PW, true, TAPE>;
         int rc = allow_dynamic_smem(kern, gbytes);
         if (rc) return rc;
         int grid = wave_grid(g, kern, kBlock, gbytes, n);
-        k_bwd<PW, true><<<grid, kBlock, gbytes, s>>>(g->d, cols, npid, member, pid, x, q2, n, gout, gx, gq, gval);
+        k_bwd<PW, true, TAPE><<<grid, kBlock, gbytes, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape, gout,
+                                                            gx, gq, gval);
     } else {
-        const void *kern = (const void *)k_bwd<PW, false>;
+        const void *kern = (const void *)k_bwd<PW, false, TAPE>;
         int grid = wave_grid(g, kern, kBlock, 0, n);
-        k_bwd<PW, false><<<grid, kBlock, 0, s>>>(g->d, cols, npid, member, pid, x, q2, n, gout, gx, gq, gval);
+        k_bwd<PW, false, TAPE><<<grid, kBlock, 0, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape, gout, gx,
+                                                        gq, gval);
     }
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
+}
+
+int backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid, int32_t pointwise,
+             const double *x, const double *q2, int64_t n, const double *tape, const double *grad_out,
+             double *grad_x, double *grad_q2, double *grad_values, cudaStream_t s)
+{
+    clear_error();
+    int rc = check_grid(g, true);
+    if (rc) return rc;
+    if (g->d.extrap == PDF_EXTRAP_CONTINUATION)
+        return fail(PDF_E_ARG, "the adjoint needs linear, freeze or error extrapolation (continuation is not linear "
+                               "in the grid values)");
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
+    if (tape && (uintptr_t)tape % 32) return fail(PDF_E_ARG, "tape must be 32-byte aligned");
+    Cols cols;
+    memset(&cols, -1, sizeof(cols));
+    if (!pointwise) {
+        rc = resolve_cols(g, pids, n_pid, &cols);
+        if (rc) return rc;
+    }
+    if (n == 0) return PDF_OK;
+    if (!x || !q2 || !grad_out || !pids) return fail(PDF_E_ARG, "null array");
+    if (pointwise)
+        return tape ? launch<true, true>(g, cols, 1, member, pids, x, q2, n, tape, grad_out, grad_x, grad_q2,
+                                         grad_values, s)
+                    : launch<true, false>(g, cols, 1, member, pids, x, q2, n, nullptr, grad_out, grad_x, grad_q2,
+                                          grad_values, s);
+    return tape ? launch<false, true>(g, cols, n_pid, member, nullptr, x, q2, n, tape, grad_out, grad_x, grad_q2,
+                                      grad_values, s)
+                : launch<false, false>(g, cols, n_pid, member, nullptr, x, q2, n, nullptr, grad_out, grad_x,
+                                       grad_q2, grad_values, s);
 }
 
 }  // namespace
@@ -152,24 +199,20 @@ extern "C" int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pi
                               double *grad_values, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_backward");
-    clear_error();
-    int rc = check_grid(g, true);
-    if (rc) return rc;
-    if (g->d.extrap == PDF_EXTRAP_CONTINUATION)
-        return fail(PDF_E_ARG, "the adjoint needs linear, freeze or error extrapolation (continuation is not linear "
-                               "in the grid values)");
-    if (n < 0) return fail(PDF_E_ARG, "negative n");
-    if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
-    Cols cols;
-    memset(&cols, -1, sizeof(cols));
-    if (!pointwise) {
-        rc = resolve_cols(g, pids, n_pid, &cols);
-        if (rc) return rc;
+    return backward(g, member, pids, n_pid, pointwise, x, q2, n, nullptr, grad_out, grad_x, grad_q2, grad_values,
+                    (cudaStream_t)stream);
+}
+
+extern "C" int xfxQ2_backward_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                                   int32_t pointwise, const double *x, const double *q2, int64_t n,
+                                   const double *tape, const double *grad_out, double *grad_x, double *grad_q2,
+                                   double *grad_values, pdfgpu_stream_t stream)
+{
+    PDF_TRACE("xfxQ2_backward_tape");
+    if (!tape) {
+        clear_error();
+        return fail(PDF_E_ARG, "null tape");
     }
-    if (n == 0) return PDF_OK;
-    if (!x || !q2 || !grad_out || !pids) return fail(PDF_E_ARG, "null array");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (pointwise)
-        return launch<true>(g, cols, 1, member, pids, x, q2, n, grad_out, grad_x, grad_q2, grad_values, s);
-    return launch<false>(g, cols, n_pid, member, nullptr, x, q2, n, grad_out, grad_x, grad_q2, grad_values, s);
+    return backward(g, member, pids, n_pid, pointwise, x, q2, n, tape, grad_out, grad_x, grad_q2, grad_values,
+                    (cudaStream_t)stream);
 }

@@ -23,12 +23,13 @@ __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000
 // output is [n][npid] row-major): one bulk copy issued by lane 0 when the run
 // is 16-byte aligned and a multiple of 16 bytes long, else coalesced stores
 // by the whole warp.  Only warp-level synchronisation, no block barriers in
-// the loop.
-template <bool Q_IS_Q, bool CONT>
+// the loop.  With TAPE each point's adjoint tape record is written as well.
+template <bool Q_IS_Q, bool CONT, bool TAPE>
 __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid, int member,
                                                   const double *__restrict__ x,
                                                   const double *__restrict__ q,
-                                                  int64_t n, double *__restrict__ out)
+                                                  int64_t n, double *__restrict__ out,
+                                                  double *__restrict__ tape)
 {
     extern __shared__ __align__(16) double sout[];
     __shared__ signed char scol[PDF_MAX_PIDS];
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         const bool oor = live && out_of_range(g, X, Q);
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
+        if (TAPE && live) tape_put(tape, i, X, Q, bad);
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
         double *srow = wbuf + lane * npid;
         warp_run_reuse(lane);                 // the previous run has left the slice
@@ -82,11 +84,12 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
 // row-major [n][npid] layout.
 constexpr int64_t kPairMax = 1 << 18;
 
-template <bool Q_IS_Q, bool CONT>
+template <bool Q_IS_Q, bool CONT, bool TAPE>
 __global__ void __launch_bounds__(kBlock) k_xfxq2_pairs(GridDev g, Cols cols, int npid, int member,
                                                         const double *__restrict__ x,
                                                         const double *__restrict__ q,
-                                                        int64_t n, double *__restrict__ out)
+                                                        int64_t n, double *__restrict__ out,
+                                                        double *__restrict__ tape)
 {
     __shared__ signed char scol[PDF_MAX_PIDS];
     if (threadIdx.x == 0) {
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pairs(GridDev g, Cols cols, in
         const bool oor = out_of_range(g, X, Q);
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
+        if (TAPE && a == 0) tape_put(tape, i, X, Q, bad);
         int col = scol[a];
         double v = 0.0;
         if (col >= 0) {
@@ -125,12 +129,13 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pairs(GridDev g, Cols cols, in
     }
 }
 
-template <bool CONT>
+template <bool CONT, bool TAPE>
 __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
                                                      const int *__restrict__ pid,
                                                      const double *__restrict__ x,
                                                      const double *__restrict__ q2,
-                                                     int64_t n, double *__restrict__ out)
+                                                     int64_t n, double *__restrict__ out,
+                                                     double *__restrict__ tape)
 {
     const size_t cell_stride = (size_t)g.nflav * 16;
     const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
@@ -150,6 +155,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
         const bool oor = out_of_range(g, X, Q);
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
+        if (TAPE) tape_put(tape, i, X, Q, bad);
         double v = 0.0;
         if (col >= 0) v = patch_any<CONT>(g, cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
         out[i] = bad ? qnan() : v;
@@ -214,8 +220,20 @@ __global__ void k_log(GridDev g, const double *__restrict__ in, int64_t n, doubl
         out[i] = dlog(g, in[i]);
 }
 
+// A tape is only written for the adjoint's grids (not under the power-law
+// continuation, which has no adjoint) and must allow 32-byte loads.
+int check_tape(const pdfgpu_grid *g, const double *tape)
+{
+    if (!tape) return PDF_OK;
+    if (g->d.extrap == PDF_EXTRAP_CONTINUATION)
+        return fail(PDF_E_ARG, "no adjoint tape under the power-law continuation (the adjoint needs linear, "
+                               "freeze or error extrapolation)");
+    if ((uintptr_t)tape % 32) return fail(PDF_E_ARG, "tape must be 32-byte aligned");
+    return PDF_OK;
+}
+
 int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n_pid,
-                  const double *x, const double *q, int64_t n, double *out, cudaStream_t s,
+                  const double *x, const double *q, int64_t n, double *out, double *tape, cudaStream_t s,
                   bool q_is_q)
 {
     clear_error();
@@ -226,25 +244,29 @@ int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n
     Cols cols;
     rc = resolve_cols(g, pids, n_pid, &cols);
     if (rc) return rc;
+    rc = check_tape(g, tape);
+    if (rc) return rc;
     if (n == 0) return PDF_OK;
     if (!x || !q || !out) return fail(PDF_E_ARG, "null array");
-    using Kern = void (*)(GridDev, Cols, int, int, const double *, const double *, int64_t, double *);
+    using Kern = void (*)(GridDev, Cols, int, int, const double *, const double *, int64_t, double *, double *);
     const bool cont = g->d.extrap == PDF_EXTRAP_CONTINUATION;
     if (n * n_pid <= kPairMax) {
-        Kern k = q_is_q ? (cont ? k_xfxq2_pairs<true, true> : k_xfxq2_pairs<true, false>)
-                        : (cont ? k_xfxq2_pairs<false, true> : k_xfxq2_pairs<false, false>);
+        Kern k = tape ? k_xfxq2_pairs<false, false, true>
+                 : q_is_q ? (cont ? k_xfxq2_pairs<true, true, false> : k_xfxq2_pairs<true, false, false>)
+                          : (cont ? k_xfxq2_pairs<false, true, false> : k_xfxq2_pairs<false, false, false>);
         int grid = wave_grid(g, (const void *)k, kBlock, 0, n * n_pid);
-        k<<<grid, kBlock, 0, s>>>(g->d, cols, n_pid, member, x, q, n, out);
+        k<<<grid, kBlock, 0, s>>>(g->d, cols, n_pid, member, x, q, n, out, tape);
         PDF_CUDA(cudaGetLastError());
         return PDF_OK;
     }
     size_t smem = (size_t)kBlock * n_pid * sizeof(double);
-    Kern k = q_is_q ? (cont ? k_xfxq2<true, true> : k_xfxq2<true, false>)
-                    : (cont ? k_xfxq2<false, true> : k_xfxq2<false, false>);
+    Kern k = tape ? k_xfxq2<false, false, true>
+             : q_is_q ? (cont ? k_xfxq2<true, true, false> : k_xfxq2<true, false, false>)
+                      : (cont ? k_xfxq2<false, true, false> : k_xfxq2<false, false, false>);
     rc = allow_dynamic_smem((const void *)k, smem);
     if (rc) return rc;
     int grid = wave_grid(g, (const void *)k, kBlock, smem, n);
-    k<<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out);
+    k<<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out, tape);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
@@ -268,38 +290,70 @@ int launch_alphas(pdfgpu_grid *g, const double *q, int64_t n, double *out, cudaS
     return PDF_OK;
 }
 
+int launch_pw(pdfgpu_grid *g, int32_t member, const int32_t *pid, const double *x, const double *q2, int64_t n,
+              double *out, double *tape, cudaStream_t s)
+{
+    clear_error();
+    int rc = check_grid(g, true);
+    if (rc) return rc;
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
+    rc = check_tape(g, tape);
+    if (rc) return rc;
+    if (n == 0) return PDF_OK;
+    if (!pid || !x || !q2 || !out) return fail(PDF_E_ARG, "null array");
+    auto k = tape ? k_xfxq2_pw<false, true>
+             : g->d.extrap == PDF_EXTRAP_CONTINUATION ? k_xfxq2_pw<true, false> : k_xfxq2_pw<false, false>;
+    int grid = wave_grid(g, (const void *)k, kBlock, 0, n);
+    k<<<grid, kBlock, 0, s>>>(g->d, member, pid, x, q2, n, out, tape);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
 }  // namespace
 
 extern "C" int xfxQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                      const double *x, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2");
-    return launch_matrix(g, member, pids, n_pid, x, q2, n, out, (cudaStream_t)stream, false);
+    return launch_matrix(g, member, pids, n_pid, x, q2, n, out, nullptr, (cudaStream_t)stream, false);
 }
 
 extern "C" int xfxQ(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                     const double *x, const double *q, int64_t n, double *out, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ");
-    return launch_matrix(g, member, pids, n_pid, x, q, n, out, (cudaStream_t)stream, true);
+    return launch_matrix(g, member, pids, n_pid, x, q, n, out, nullptr, (cudaStream_t)stream, true);
 }
 
 extern "C" int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
                         const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_pw");
-    clear_error();
-    int rc = check_grid(g, true);
-    if (rc) return rc;
-    if (n < 0) return fail(PDF_E_ARG, "negative n");
-    if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
-    if (n == 0) return PDF_OK;
-    if (!pid || !x || !q2 || !out) return fail(PDF_E_ARG, "null array");
-    auto k = g->d.extrap == PDF_EXTRAP_CONTINUATION ? k_xfxq2_pw<true> : k_xfxq2_pw<false>;
-    int grid = wave_grid(g, (const void *)k, kBlock, 0, n);
-    k<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, member, pid, x, q2, n, out);
-    PDF_CUDA(cudaGetLastError());
-    return PDF_OK;
+    return launch_pw(g, member, pid, x, q2, n, out, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                          const double *x, const double *q2, int64_t n, double *out, double *tape,
+                          pdfgpu_stream_t stream)
+{
+    PDF_TRACE("xfxQ2_tape");
+    if (!tape) {
+        clear_error();
+        return fail(PDF_E_ARG, "null tape");
+    }
+    return launch_matrix(g, member, pids, n_pid, x, q2, n, out, tape, (cudaStream_t)stream, false);
+}
+
+extern "C" int xfxQ2_pw_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
+                             const double *q2, int64_t n, double *out, double *tape, pdfgpu_stream_t stream)
+{
+    PDF_TRACE("xfxQ2_pw_tape");
+    if (!tape) {
+        clear_error();
+        return fail(PDF_E_ARG, "null tape");
+    }
+    return launch_pw(g, member, pid, x, q2, n, out, tape, (cudaStream_t)stream);
 }
 
 extern "C" int alphasQ2(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
@@ -405,7 +459,7 @@ extern "C" int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, 
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(g->stage[s][1], q2 + off, m * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return drain(cuda_fail(e, "host-to-device copy"));
-        rc = launch_matrix(g, member, pids, n_pid, g->stage[s][0], g->stage[s][1], m, g->stage[s][2], st, false);
+        rc = launch_matrix(g, member, pids, n_pid, g->stage[s][0], g->stage[s][1], m, g->stage[s][2], nullptr, st, false);
         if (rc) return drain(rc);
         e = cudaMemcpyAsync(out + off * n_pid, g->stage[s][2], m * n_pid * sizeof(double), cudaMemcpyDeviceToHost,
                             st);

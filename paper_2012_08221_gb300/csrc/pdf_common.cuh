@@ -427,6 +427,60 @@ __device__ __forceinline__ bool out_of_range(const GridDev &g, const Axis &X, co
     return g.extrap == PDF_EXTRAP_ERROR && !(X.in && Q.in);
 }
 
+// Adjoint tape: 32 bytes per point that a forward pass keeps for the adjoint
+// of the same points, so that the adjoint skips the domain checks, both knot
+// searches and both logarithms.  Layout (four doubles, 32-byte aligned):
+//   [0] t of the x axis, [1] t of the Q axis (after make_basis),
+//   [2] bits: x cell (low 32) and Q cell (high 32),
+//   [3] bits: 1 x inside, 2 x below, 4 Q inside, 8 Q below, 16 bad point
+//       (domain error, or outside the grid under the error option).
+// It depends on the points, the knots and the extrapolation option only (not
+// on the member or the values), so it stays valid across pdf_bind_values.
+constexpr unsigned kTapeBad = 16u;
+
+__device__ __forceinline__ void tape_put(double *__restrict__ tape, int64_t i, const Axis &X, const Axis &Q,
+                                         bool bad)
+{
+    const unsigned f = (X.in ? 1u : 0u) | (X.below ? 2u : 0u) | (Q.in ? 4u : 0u) | (Q.below ? 8u : 0u) |
+                       (bad ? kTapeBad : 0u);
+    double2 *d = reinterpret_cast<double2 *>(tape + 4 * i);
+    d[0] = make_double2(X.t, Q.t);
+    d[1] = make_double2(dfrom((uint64_t)(uint32_t)X.cell | ((uint64_t)(uint32_t)Q.cell << 32)),
+                        dfrom((uint64_t)f));
+}
+
+// A cell read back from a tape: range-checked (and flagged) in checked
+// builds, clamped into the table otherwise, so that a tape from another grid
+// gives wrong numbers but no access outside the tables.
+__device__ __forceinline__ int tape_cell(unsigned *status, uint32_t v, int n)
+{
+#ifdef PDFGPU_CHECKED
+    return checked_index(status, (int)v, n);
+#else
+    (void)status;
+    return (int)min(v, (uint32_t)(n - 1));
+#endif
+}
+
+// Rebuilds the two axes of point i from its tape record; returns whether the
+// point is bad.
+__device__ __forceinline__ bool tape_get(const GridDev &g, const double *__restrict__ tape, int64_t i, Axis &X,
+                                         Axis &Q)
+{
+    const D4 r = ld4(tape + 4 * i);
+    const uint64_t cells = dbits(r.z);
+    const unsigned f = (unsigned)dbits(r.w);
+    X.cell = tape_cell(g.status, (uint32_t)cells, g.nxc);
+    Q.cell = tape_cell(g.status, (uint32_t)(cells >> 32), g.nqc);
+    X.in = f & 1u;
+    X.below = f & 2u;
+    Q.in = f & 4u;
+    Q.below = f & 8u;
+    make_basis(X, r.x, g.extrap);
+    make_basis(Q, r.y, g.extrap);
+    return f & kTapeBad;
+}
+
 __device__ __forceinline__ int pid_col(const GridDev &g, int pid)
 {
     int col = (pid >= -64 && pid <= 64) ? (int)__ldg(g.pidmap + pid + 64) : -1;

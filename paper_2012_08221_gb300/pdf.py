@@ -128,9 +128,11 @@ class PDF:
         self._bound_ref = v      # keep alive until the stream has read it
 
     # ------------------------------------------------------------- queries
-    def xfxQ2(self, pids, x, q2, member=0, out=None):
-        """x*f for every pid in ``pids`` at each (x_i, Q^2_i): ``[n][len(pids)]``."""
-        return self._matrix("xfxQ2", pids, x, q2, member, out)
+    def xfxQ2(self, pids, x, q2, member=0, out=None, tape=None):
+        """x*f for every pid in ``pids`` at each (x_i, Q^2_i): ``[n][len(pids)]``.
+        ``tape`` (``[n][4]`` float64 on the device, see ``new_tape``) also
+        receives the adjoint tape of the points for ``xfxQ2_backward``."""
+        return self._matrix("xfxQ2", pids, x, q2, member, out, tape)
 
     def xfxQ(self, pids, x, q, member=0, out=None):
         return self._matrix("xfxQ", pids, x, q, member, out)
@@ -138,7 +140,7 @@ class PDF:
     py_xfxQ2 = xfxQ2
     py_xfxQ = xfxQ
 
-    def _matrix(self, name, pids, x, q, member, out):
+    def _matrix(self, name, pids, x, q, member, out, tape=None):
         arr, pp = _pids_host(pids)
         x = _f64_cuda(x, self.device)
         q = _f64_cuda(q, self.device)
@@ -146,19 +148,38 @@ class PDF:
         assert q.numel() == n, "x and Q arrays differ in length"
         if out is None:
             out = torch.empty((n, arr.size), dtype=torch.float64, device=self.device)
+        if tape is not None:
+            self._check_tape(tape, n)
+            check("xfxQ2_tape", lib().xfxQ2_tape(self.handle, int(member), pp, arr.size, _ptr(x), _ptr(q), n,
+                                                 _ptr(out), _ptr(tape), _stream(self.device)))
+            return out
         f = getattr(lib(), name)
         check(name, f(self.handle, int(member), pp, arr.size, _ptr(x), _ptr(q), n, _ptr(out),
                       _stream(self.device)))
         return out
 
-    def xfxQ2_pw(self, pid, x, q2, member=0, out=None):
-        """One pid per point: ``out[i] = x*f_{pid_i}(x_i, Q^2_i)``."""
+    def new_tape(self, n):
+        """Device buffer for the adjoint tape of ``n`` points (32 bytes each)."""
+        return torch.empty((n, 4), dtype=torch.float64, device=self.device)
+
+    def _check_tape(self, tape, n):
+        assert tape.dtype == torch.float64 and tape.is_cuda and tape.is_contiguous(), "tape: contiguous float64"
+        assert tape.numel() >= 4 * n, "tape too small (4 doubles per point)"
+
+    def xfxQ2_pw(self, pid, x, q2, member=0, out=None, tape=None):
+        """One pid per point: ``out[i] = x*f_{pid_i}(x_i, Q^2_i)``; ``tape`` as
+        for ``xfxQ2``."""
         x = _f64_cuda(x, self.device)
         q2 = _f64_cuda(q2, self.device)
         pid = torch.as_tensor(pid, device=self.device).to(torch.int32).contiguous()
         n = x.numel()
         if out is None:
             out = torch.empty(n, dtype=torch.float64, device=self.device)
+        if tape is not None:
+            self._check_tape(tape, n)
+            check("xfxQ2_pw_tape", lib().xfxQ2_pw_tape(self.handle, int(member), _ptr(pid), _ptr(x), _ptr(q2),
+                                                       n, _ptr(out), _ptr(tape), _stream(self.device)))
+            return out
         check("xfxQ2_pw", lib().xfxQ2_pw(self.handle, int(member), _ptr(pid), _ptr(x), _ptr(q2), n,
                                          _ptr(out), _stream(self.device)))
         return out
@@ -206,10 +227,11 @@ class PDF:
 
     # --------------------------------------------------------------- adjoint
     def xfxQ2_backward(self, pids, x, q2, grad_out, member=0, pointwise=False,
-                       grad_x=True, grad_q2=True, grad_values=None):
+                       grad_x=True, grad_q2=True, grad_values=None, tape=None):
         """dL/dx, dL/dQ^2 and (accumulated into ``grad_values``, shape
         ``[rows][n_x][n_flav]``) dL/dvalues for
-        L = sum grad_out * xf.  Returns (grad_x, grad_q2, grad_values)."""
+        L = sum grad_out * xf.  Returns (grad_x, grad_q2, grad_values).
+        ``tape``: the adjoint tape a forward call wrote for the same points."""
         x = _f64_cuda(x, self.device)
         q2 = _f64_cuda(q2, self.device)
         n = x.numel()
@@ -223,9 +245,15 @@ class PDF:
             arr, _ = _pids_host(pids)
             keep = arr
             pp, npid = C.c_void_p(arr.ctypes.data), arr.size
-        check("xfxQ2_backward", lib().xfxQ2_backward(
-            self.handle, int(member), pp, npid, int(bool(pointwise)), _ptr(x), _ptr(q2), n,
-            _ptr(gout), _ptr(gx), _ptr(gq), _ptr(grad_values), _stream(self.device)))
+        if tape is not None:
+            self._check_tape(tape, n)
+            check("xfxQ2_backward_tape", lib().xfxQ2_backward_tape(
+                self.handle, int(member), pp, npid, int(bool(pointwise)), _ptr(x), _ptr(q2), n,
+                _ptr(tape), _ptr(gout), _ptr(gx), _ptr(gq), _ptr(grad_values), _stream(self.device)))
+        else:
+            check("xfxQ2_backward", lib().xfxQ2_backward(
+                self.handle, int(member), pp, npid, int(bool(pointwise)), _ptr(x), _ptr(q2), n,
+                _ptr(gout), _ptr(gx), _ptr(gq), _ptr(grad_values), _stream(self.device)))
         del keep
         return gx, gq, grad_values
 

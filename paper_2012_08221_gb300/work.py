@@ -58,6 +58,15 @@ def pw_bwd_point_flops() -> int:
 PW_BWD_POINT_BYTES = 44                # grad_out, x, Q^2, pid in; dx, dQ^2 out
 
 
+def pw_bwd_tape_point_flops() -> int:
+    """The same adjoint from the forward pass's tape: the two logs and the
+    two t are read back instead of recomputed."""
+    return pw_bwd_point_flops() - 2 * LOG_FLOPS - 2 * AXIS_FLOPS
+
+
+TAPE_POINT_BYTES = 32                  # written by the forward, read by the adjoint
+
+
 def lumi_event_flops(n_flav: int) -> int:
     """Kinematics (1 multiply, 3 adds), t for 3 axes, 2 F patches,
     F FMA for the flavour-paired sum, alpha_s cubic (3 FMA), 1 add to the

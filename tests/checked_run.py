@@ -46,6 +46,13 @@ def main():
             gx, gq, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
                                          pointwise=True, grad_values=gv)
             res += [gx, gq]
+            # the same through the adjoint tape (its cells are range-checked too)
+            T = p.new_tape(x.size)
+            res += [p.xfxQ2_pw(pid, X, Q, tape=T), p.xfxQ2(g.pids, X, Q, member=1, tape=T)]
+            gt = torch.zeros_like(gv)
+            gxt, gqt, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
+                                           pointwise=True, grad_values=gt, tape=T)
+            res += [gxt, gqt]
         ev = DeviceEvents.from_host(synth.events_lhc(50_001, seed=63))
         L, lum, als = luminosity(p, ev)
         res += [lum, als]

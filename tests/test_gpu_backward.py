@@ -219,3 +219,102 @@ def test_alphas_derivative_and_autograd():
     Q = cuda(q2[:6]).requires_grad_(True)
     assert torch.autograd.gradcheck(lambda z: alphasQ2(pdf, z), (Q,), eps=1e-6 * float(Q.min()),
                                     atol=1e-9, rtol=1e-5)
+
+
+def _points_with_edges(g, n, seed):
+    """Points inside, below and above both knot ranges, plus domain errors."""
+    rng = np.random.default_rng(seed)
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    x = np.exp(rng.uniform(U[0] - 2, 0.0, n))
+    q2 = np.exp(rng.uniform(W[0] - 2, W[-1] + 2, n))
+    x[:4] = [0.0, 1.5, np.nan, 1.0]
+    q2[4:7] = [-1.0, np.inf, np.nan]
+    return x, q2
+
+
+@pytest.mark.parametrize("extrap", ["linear", "freeze", "error"])
+def test_tape_gives_the_same_forward_and_adjoint(extrap):
+    """The forward calls that write the adjoint tape give the same outputs,
+    and the adjoint from the tape the same dL/dx and dL/dQ^2 bit for bit (the
+    grid gradient up to the order of the atomic sums), pointwise and for a
+    shared pid list, on a two-subgrid grid, the small grid (shared-memory
+    gradient) and the NNPDF-shaped grid (global-memory gradient), with
+    points outside the grid and domain errors."""
+    from paper_2012_08221_gb300.pdf import PDF
+    same = lambda a, b: torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
+    for g in (tiny_two_sub(seed=51), synth.grid_small(seed=1003, pids=synth.PIDS_13), synth.grid_nnpdf()):
+        pdf = PDF.from_grid(g, extrap=extrap)
+        x, q2 = _points_with_edges(g, 30_011, 52)
+        X, Q = cuda(x), cuda(q2)
+        rng = np.random.default_rng(53)
+        pid = cuda(rng.choice(np.append(g.pids, 7), x.size).astype(np.int32))   # 7: absent
+        pids = np.array([g.pids[0], 21, g.pids[-1], 7], dtype=np.int32)
+        T = pdf.new_tape(x.size)
+        for pointwise in (True, False):
+            if pointwise:
+                ref = pdf.xfxQ2_pw(pid, X, Q)
+                got = pdf.xfxQ2_pw(pid, X, Q, tape=T)
+                gout = cuda(rng.standard_normal(x.size))
+                ids = pid
+            else:
+                ref = pdf.xfxQ2(pids, X, Q)
+                got = pdf.xfxQ2(pids, X, Q, tape=T)
+                gout = cuda(rng.standard_normal((x.size, pids.size)))
+                ids = pids
+            assert same(got, ref)
+            gv0 = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+            gv1 = torch.zeros_like(gv0)
+            gx0, gq0, _ = pdf.xfxQ2_backward(ids, X, Q, gout, pointwise=pointwise, grad_values=gv0)
+            gx1, gq1, _ = pdf.xfxQ2_backward(ids, X, Q, gout, pointwise=pointwise, grad_values=gv1, tape=T)
+            assert same(gx1, gx0) and same(gq1, gq0)
+            assert torch.allclose(gv1, gv0, rtol=1e-12, atol=1e-15 * float(gv0.abs().max()))
+            assert bool(torch.isnan(gx1[[0, 1, 2, 4, 5, 6]]).all()) and not bool(torch.isnan(gx1[3]))   # x = 1 is valid
+        torch.cuda.synchronize()
+
+
+def test_tape_survives_new_values_and_other_members():
+    """A tape depends on the points and the knots only: after binding other
+    values, and for another member, the adjoint from the old tape equals the
+    adjoint that recomputes the coordinates."""
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_nnpdf(seeds=(1005, 1006))
+    pdf = PDF.from_grid(g)
+    x, q2, _ = synth.queries_nnpdf(20_003, seed=54)
+    X, Q = cuda(x), cuda(q2)
+    pids = np.array([-1, 0, 2], dtype=np.int32)
+    T = pdf.new_tape(x.size)
+    pdf.xfxQ2(pids, X, Q, tape=T)
+    pdf.bind_values(cuda(g.values * 1.5 - 0.25))
+    gout = cuda(np.random.default_rng(55).standard_normal((x.size, 3)))
+    for m in (0, 1):
+        gv0 = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+        gv1 = torch.zeros_like(gv0)
+        gx0, gq0, _ = pdf.xfxQ2_backward(pids, X, Q, gout, member=m, grad_values=gv0)
+        gx1, gq1, _ = pdf.xfxQ2_backward(pids, X, Q, gout, member=m, grad_values=gv1, tape=T)
+        assert torch.equal(gx0, gx1) and torch.equal(gq0, gq1)
+        assert torch.allclose(gv1, gv0, rtol=1e-12, atol=1e-15 * float(gv0.abs().max()))
+
+
+def test_tape_arguments_are_checked():
+    from paper_2012_08221_gb300._lib import PdfError
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_small(seed=1003, pids=synth.PIDS_13)
+    pdf = PDF.from_grid(g)
+    x, q2 = synth.queries_small(1001, seed=56)
+    X, Q = cuda(x), cuda(q2)
+    pid = cuda(np.full(x.size, 2, np.int32))
+    buf = torch.empty(4 * x.size + 4, dtype=torch.float64, device="cuda")
+    odd = buf[1:1 + 4 * x.size]                       # 8-byte aligned only
+    with pytest.raises(PdfError):
+        pdf.xfxQ2_pw(pid, X, Q, tape=odd)
+    with pytest.raises(PdfError):
+        pdf.xfxQ2_backward(pid, X, Q, cuda(np.ones(x.size)), pointwise=True, tape=odd)
+    pc = PDF.from_grid(g, extrap="continuation")
+    with pytest.raises(PdfError):
+        pc.xfxQ2(g.pids, X, Q, tape=pc.new_tape(x.size))
+    with pytest.raises(AssertionError):
+        pdf.xfxQ2_pw(pid, X, Q, tape=pdf.new_tape(x.size - 1))
+    # autograd on a continuation grid still runs its forward (no tape)
+    from paper_2012_08221_gb300.autograd import xfxQ2 as ad_xfxQ2
+    vals = torch.tensor(g.values, device="cuda", requires_grad=True)
+    assert torch.equal(ad_xfxQ2(pc, vals, g.pids, X, Q), pc.xfxQ2(g.pids, X, Q))
