@@ -222,7 +222,8 @@ int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t
  *   the points, the grid's knots and its extrapolation option only, not on
  *   the member or the values: it stays valid across pdf_bind_values and for
  *   every member of the grid.  PDF_E_ARG for a grid loaded with
- *   PDF_EXTRAP_CONTINUATION (which has no adjoint) and for a NULL tape.
+ *   PDF_EXTRAP_CONTINUATION (which has no adjoint) and for a NULL tape
+ *   when n > 0 (with n == 0 the calls do nothing, and the tape may be NULL).
  * Outputs of the forward calls are bit for bit those of xfxQ2 / xfxQ2_pw. */
 int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                const double *x, const double *q2, int64_t n, double *out, double *tape,

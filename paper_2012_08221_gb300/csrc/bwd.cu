@@ -209,7 +209,7 @@ extern "C" int xfxQ2_backward_tape(pdfgpu_grid_t g, int32_t member, const int32_
                                    double *grad_values, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_backward_tape");
-    if (!tape) {
+    if (!tape && n != 0) {
         clear_error();
         return fail(PDF_E_ARG, "null tape");
     }

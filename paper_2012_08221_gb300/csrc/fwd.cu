@@ -338,7 +338,7 @@ extern "C" int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, 
                           pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_tape");
-    if (!tape) {
+    if (!tape && n != 0) {
         clear_error();
         return fail(PDF_E_ARG, "null tape");
     }
@@ -349,7 +349,7 @@ extern "C" int xfxQ2_pw_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pid
                              const double *q2, int64_t n, double *out, double *tape, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_pw_tape");
-    if (!tape) {
+    if (!tape && n != 0) {
         clear_error();
         return fail(PDF_E_ARG, "null tape");
     }

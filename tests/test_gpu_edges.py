@@ -1,0 +1,87 @@
+"""Empty and one-point inputs through every entry point: n = 0 is a no-op
+that leaves accumulated outputs untouched (and gives L = 0 and zero VEGAS
+sums), a single point matches the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleGrid
+from paper_2012_08221_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nn():
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    g = synth.grid_nnpdf(seeds=(1005,))
+    return g, PDF.from_grid(g), OracleGrid.from_synth(g)
+
+
+def _e(dtype=torch.float64):
+    return torch.empty(0, dtype=dtype, device="cuda")
+
+
+def test_empty_inputs_everywhere(nn):
+    from paper_2012_08221_gb300.batch import Batch
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
+    from paper_2012_08221_gb300.vegas import Vegas
+    g, pdf, o = nn
+    e, ei = _e(), _e(torch.int32)
+    gv = torch.full(g.values.shape[1:], 3.0, dtype=torch.float64, device="cuda")
+    T = pdf.new_tape(0)
+    assert pdf.xfxQ2(g.pids, e, e, tape=T).shape == (0, g.n_flav)
+    assert pdf.xfxQ2_pw(ei, e, e, tape=T).shape == (0,)
+    v, d = pdf.alphasQ2_grad(e)
+    assert d.shape == (0,)
+    for tape in (None, T):
+        gx, gq, _ = pdf.xfxQ2_backward(ei, e, e, e, pointwise=True, grad_values=gv, tape=tape)
+        assert gx.shape == (0,) and gq.shape == (0,)
+        pdf.xfxQ2_backward(g.pids, e, e, torch.empty((0, g.n_flav), dtype=torch.float64, device="cuda"),
+                           grad_values=gv, tape=tape)
+    h = torch.empty(0, dtype=torch.float64)
+    assert pdf.xfxQ2_host(g.pids, h, h).shape == (0, g.n_flav)
+    ev = DeviceEvents(e, e, _e(torch.uint8), e, e, 2 * math.log(13000.0))
+    L, lum, a_s = luminosity(pdf, ev)
+    assert L.item() == 0.0 and lum.shape == (0,)
+    luminosity_backward(pdf, ev, 1.0, gv)
+    torch.cuda.synchronize()
+    assert bool((gv == 3.0).all())                   # nothing accumulated
+    vg = Vegas(2, n_bins=8)
+    r, jac, bins = vg.map(torch.empty((0, 2), dtype=torch.float64, device="cuda"))
+    assert r.shape == (0, 2) and jac.shape == (0,)
+    assert np.all(vg.accumulate(jac, bins) == 0.0)
+    # a batch with an empty request among others
+    x, q2, _ = synth.queries_nnpdf(1003, seed=71)
+    X, Q = torch.as_tensor(x, device="cuda"), torch.as_tensor(q2, device="cuda")
+    out = torch.empty((x.size, 2), dtype=torch.float64, device="cuda")
+    Batch([(pdf, 0, np.array([1, -1], np.int32), X[:0], Q[:0], out[:0]),
+           (pdf, 0, np.array([1, -1], np.int32), X, Q, out)], autotune=False).run()
+    torch.cuda.synchronize()
+    assert torch.equal(out, pdf.xfxQ2(np.array([1, -1], np.int32), X, Q))
+
+
+def test_one_point_everywhere(nn):
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity
+    g, pdf, o = nn
+    x, q2 = np.array([3.3e-4]), np.array([97.0])
+    X, Q = torch.as_tensor(x, device="cuda"), torch.as_tensor(q2, device="cuda")
+    got = pdf.xfxQ2(g.pids, X, Q).cpu().numpy()
+    parity.check(got, o.xfxq2_batch(g.pids, x, q2), o.kappa(g.pids, x, q2), what="one point")
+    pid = np.array([2], np.int32)
+    T = pdf.new_tape(1)
+    got = pdf.xfxQ2_pw(torch.as_tensor(pid, device="cuda"), X, Q, tape=T).cpu().numpy()
+    parity.check(got, o.xfxq2_pw(pid, x, q2), o.kappa(pid, x, q2, pointwise=True), what="one point pw")
+    gx, gq, _ = pdf.xfxQ2_backward(torch.as_tensor(pid, device="cuda"), X, Q,
+                                   torch.ones(1, dtype=torch.float64, device="cuda"), pointwise=True, tape=T)
+    rdx, rdq = o.grad_pw(pid, x, q2)
+    assert np.allclose(gx.cpu().numpy(), rdx, rtol=1e-9) and np.allclose(gq.cpu().numpy(), rdq, rtol=1e-9)
+    ev = synth.events_lhc(1, seed=72)
+    L, lum, a_s = luminosity(pdf, DeviceEvents.from_host(ev))
+    Lr, lumr, asr = o.lumi(ev)
+    assert abs(L.item() - Lr) <= 1e-12 * (abs(Lr) + 1e3) and L.item() == lum.item()
