@@ -256,10 +256,9 @@ def source_hash(files):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, units):
-    """DRAM bytes (read + write) per launch of `kernel` over `units` points,
-    scaled from the committed ncu capture's bytes per point, if that capture
-    was taken on the current sources of the kernel (else None)."""
+def _capture(kernel):
+    """The committed ncu figures of `kernel` (profiles/traffic.json) if they
+    were taken on the kernel's current sources, else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
@@ -268,7 +267,21 @@ def measured_traffic(kernel, units):
     e = d.get(kernel)
     if not e or e.get("source_hash") != source_hash(e.get("files", [])):
         return None
-    return e["dram_bytes_per_unit"] * units
+    return e
+
+
+def measured_traffic(kernel, units):
+    """DRAM bytes (read + write) per launch of `kernel` over `units` points,
+    scaled from the committed ncu capture's bytes per point, if that capture
+    was taken on the current sources of the kernel (else None)."""
+    e = _capture(kernel)
+    return None if e is None else e["dram_bytes_per_unit"] * units
+
+
+def measured_pipe(kernel):
+    """FP64-pipe occupancy (% of active cycles) of the same capture, or None."""
+    e = _capture(kernel)
+    return None if e is None else e.get("fp64_pipe_active_pct")
 
 
 def reduce_max(v, world, device):
@@ -417,6 +430,7 @@ def main():
                 "probe": {"value": probe / 1e12, "unit": "TFLOP/s",
                           "what": "FP64 FMA chains measured in this run (pdf_probe_fp64_peak)"},
                 "traffic": traffic,
+                "ncu_fp64_pipe_active_pct": measured_pipe("k_xfxq2"),
                 "algorithmic_bytes": bytes_launch,
                 "achieved_gbs": bytes_launch / (k_ms * 1e-3) / 1e9,
                 "hbm_peak_gbs": peaks().get("hbm_gbs", 6790.7),
