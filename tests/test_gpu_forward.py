@@ -342,7 +342,8 @@ def test_small_query_kernel_matches_the_per_point_kernel(nnpdf):
     """Queries of at most 2^18 point-flavour pairs run one thread per pair;
     larger ones one thread per point.  The same points give the same bits
     both ways (the value of a point does not depend on the batch it is in),
-    and the small launch matches the oracle, for x*f and x*f(Q)."""
+    and the small launch matches the oracle, for x*f, x*f(Q) and a shorter
+    pid list."""
     g, pdf, o = nnpdf
     x, q2, _ = synth.queries_nnpdf(100_003, seed=17)
     X, Q = cuda(x), cuda(q2)
