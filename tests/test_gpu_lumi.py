@@ -147,7 +147,7 @@ def test_luminosity_autograd(lhc):
 
 def test_full_size_luminosity_sampled(lhc):
     """1e8 events in one launch: L equals the mean of the per-event values,
-    sampled events match the oracle, and the grid gradient (12 chunks of
+    2e5 sampled events match the oracle, and the grid gradient (12 chunks of
     events) obeys the exact flavour sum rule sum_cells dL/dv[.][b] =
     mean_e(f_-b(x2) + f_-b(x1)) with the right-hand side from the oracle (the
     interpolation's weights sum to 1), for the gluon and the u quark."""
@@ -159,7 +159,7 @@ def test_full_size_luminosity_sampled(lhc):
     L, lum, a_s = luminosity(pdf, dev)
     lum_h = lum.cpu().numpy()
     assert abs(L.item() - lum_h.sum() / n) <= 1e-12 * np.abs(lum_h).sum() / n
-    idx = np.random.default_rng(5).choice(n, 1500, replace=False)
+    idx = np.random.default_rng(5).choice(n, 200_000, replace=False)
     sub = synth.Events(ev.ln_tau[idx], ev.y[idx], ev.flags[idx], ev.ln_mu2[idx], ev.ln_x1[idx], ev.ln_s)
     Lr, lumr, asr = o.lumi(sub)
     parity.check(lum_h[idx], lumr, _lum_kappa(g, o, sub, idx.size), what="full lum")
