@@ -557,21 +557,37 @@ def main():
             GV.zero_()
             p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV)
 
+        # the step as a user writes it: L = sum_i w_i xf_{a_i}(x_i, Q^2_i)
+        # through torch.autograd (the Function's forward keeps the tape)
+        from paper_2012_08221_gb300.autograd import xfxQ2_pw as ad_xfxQ2_pw
+        VA = V3.clone().requires_grad_(True)
+        XA, QA3 = X3.clone().requires_grad_(True), Q3.clone().requires_grad_(True)
+
+        def step3a():
+            VA.grad = XA.grad = QA3.grad = None
+            L3 = (ad_xfxQ2_pw(p3, VA, P3, XA, QA3) * W3).sum()
+            L3.backward()
+
+        ms3a, _ = timed(step3a, args.steps, args.warmup)
         ms3, kb = timed(step3, args.steps, args.warmup, kstep3)
         ms3n, _ = timed(step3n, max(3, args.steps // 2), args.warmup)
         n3 = x3.size
         fl = n3 * (work.pw_fwd_point_flops() + work.pw_bwd_tape_point_flops())
         forms["fwd_bwd"] = {
             "workload": "pointwise x*f and its adjoint (dL/dx, dL/dQ^2, dL/dgrid) at 1e7 points, "
-                        "50x20 grid, 13 flavours, L = sum w_i xf_{a_i}",
-            "value": world * n3 / (ms3 * 1e-3), "unit": "evals/s (fwd+bwd)", "ms_per_step": ms3,
-            "fp64_frac": (fl / (ms3 * 1e-3)) / peak,
+                        "50x20 grid, 13 flavours, L = sum w_i xf_{a_i}, through torch.autograd",
+            "value": world * n3 / (ms3a * 1e-3), "unit": "evals/s (fwd+bwd)", "ms_per_step": ms3a,
+            "fp64_frac": (fl / (ms3a * 1e-3)) / peak,
             "bwd_kernel": {"kernel": "k_bwd (from the tape)", "ms": kb,
                            "frac": n3 * work.pw_bwd_tape_point_flops() / (kb * 1e-3) / peak},
             "tape": "the forward pass writes 32 bytes per point (cells, local coordinates, flags) that the "
                     "adjoint reads instead of searching the knots and taking logarithms again",
-            "without_tape": {"ms_per_step": ms3n, "value": world * n3 / (ms3n * 1e-3)}}
-        del P3, X3, Q3, W3, O3, T3
+            "direct_calls": {"ms_per_step": ms3, "value": world * n3 / (ms3 * 1e-3),
+                             "what": "the same two library calls without autograd (no torch "
+                                     "multiply, sum or gradient accumulation)"},
+            "without_tape": {"ms_per_step": ms3n, "value": world * n3 / (ms3n * 1e-3),
+                             "what": "direct calls, the adjoint recomputing the coordinates"}}
+        del P3, X3, Q3, W3, O3, T3, VA, XA, QA3
 
     # ------------------------------------------------------------- batched
     if "batched" in want:
