@@ -281,11 +281,10 @@ static int enqueue(pdfgpu_batch *b, cudaStream_t st)
     return PDF_OK;
 }
 
-extern "C" int pdf_batch_free(pdfgpu_batch_t b)
+// Frees everything a batch owns, leaving the thread's error message alone
+// (a failing pdf_batch_prepare keeps the message of the step that failed).
+static void release_batch(pdfgpu_batch *b)
 {
-    PDF_TRACE("pdf_batch_free");
-    clear_error();
-    if (!b) return fail(PDF_E_ARG, "null batch");
     cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -294,6 +293,14 @@ extern "C" int pdf_batch_free(pdfgpu_batch_t b)
     if (b->d_reqs) cudaFree(b->d_reqs);
     if (b->d_ticket) cudaFree(b->d_ticket);
     delete b;
+}
+
+extern "C" int pdf_batch_free(pdfgpu_batch_t b)
+{
+    PDF_TRACE("pdf_batch_free");
+    clear_error();
+    if (!b) return fail(PDF_E_ARG, "null batch");
+    release_batch(b);
     return PDF_OK;
 }
 
@@ -301,7 +308,7 @@ extern "C" int pdf_batch_free(pdfgpu_batch_t b)
     do {                         \
         int rc__ = (x);          \
         if (rc__ != PDF_OK) {    \
-            pdf_batch_free(b);   \
+            release_batch(b);    \
             return rc__;         \
         }                        \
     } while (0)
@@ -323,12 +330,12 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
         const pdfgpu_batch_desc &D = descs[i];
         int rc = check_grid(D.grid, true);
         if (rc) {
-            pdf_batch_free(b);
+            release_batch(b);
             return rc;
         }
         if (D.member < 0 || D.member >= D.grid->d.nmem || D.n_pid < 1 || D.n_pid > kMaxReqPids || D.n < 0 ||
             (D.n > 0 && (!D.x || !D.q2 || !D.out))) {
-            pdf_batch_free(b);
+            release_batch(b);
             return fail(PDF_E_ARG, "bad request " + std::to_string(i));
         }
         int gi = -1;
@@ -343,7 +350,7 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
         Cols cols;
         int rc2 = resolve_cols(D.grid, D.pids, D.n_pid, &cols);
         if (rc2) {
-            pdf_batch_free(b);
+            release_batch(b);
             return rc2;
         }
         BatchReq r{};
@@ -361,15 +368,11 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
         evals += D.n * D.n_pid;
     }
     b->nreq = n_desc;
-    BTRY(cudaMalloc(&b->d_grids, gd.size() * sizeof(GridDev)) == cudaSuccess ? PDF_OK
-                                                                            : fail(PDF_E_NOMEM, "alloc"));
-    BTRY(cudaMalloc(&b->d_reqs, b->host_reqs.size() * sizeof(BatchReq)) == cudaSuccess
-             ? PDF_OK
-             : fail(PDF_E_NOMEM, "alloc"));
-    BTRY(cudaMalloc(&b->d_ticket, sizeof(unsigned long long)) == cudaSuccess ? PDF_OK
-                                                                             : fail(PDF_E_NOMEM, "alloc"));
+    BTRY(dev_malloc((void **)&b->d_grids, gd.size() * sizeof(GridDev), "batch grid table"));
+    BTRY(dev_malloc((void **)&b->d_reqs, b->host_reqs.size() * sizeof(BatchReq), "batch request table"));
+    BTRY(dev_malloc((void **)&b->d_ticket, sizeof(unsigned long long), "batch ticket"));
     if (cudaMemcpy(b->d_grids, gd.data(), gd.size() * sizeof(GridDev), cudaMemcpyHostToDevice) != cudaSuccess) {
-        pdf_batch_free(b);
+        release_batch(b);
         return fail(PDF_E_CUDA, "upload of grid table failed");
     }
 
@@ -409,7 +412,7 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
                         BTRY(enqueue(b, st));
                         cudaEventRecord(e1, st);
                         if (cudaEventSynchronize(e1) != cudaSuccess) {
-                            pdf_batch_free(b);
+                            release_batch(b);
                             return fail(PDF_E_CUDA, "tuning launch failed");
                         }
                         float ms = 0;
@@ -429,7 +432,7 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
     b->tuned_ms = best_ms;
     BTRY(configure(b, best, st));
     if (cudaStreamSynchronize(st) != cudaSuccess) {
-        pdf_batch_free(b);
+        release_batch(b);
         return fail(PDF_E_CUDA, "prepare");
     }
     // capture the launch (ticket reset + persistent kernel) into a graph
@@ -445,7 +448,7 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     cudaStreamDestroy(cap);
     if (e != cudaSuccess) {
-        pdf_batch_free(b);
+        release_batch(b);
         return cuda_fail(e, "graph capture of the batched launch");
     }
     *out = b;

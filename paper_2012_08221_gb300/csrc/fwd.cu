@@ -434,10 +434,10 @@ extern "C" int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, 
         int64_t pts = std::max<int64_t>(chunk, g->stage_pts);
         int np = std::max(n_pid, g->stage_pid);
         for (int s = 0; s < 3; ++s) {
-            if (cudaMalloc(&g->stage[s][0], pts * sizeof(double)) != cudaSuccess ||
-                cudaMalloc(&g->stage[s][1], pts * sizeof(double)) != cudaSuccess ||
-                cudaMalloc(&g->stage[s][2], pts * np * sizeof(double)) != cudaSuccess)
-                return fail(PDF_E_NOMEM, "staging allocation failed");
+            if (dev_malloc((void **)&g->stage[s][0], pts * sizeof(double), "host-path staging") ||
+                dev_malloc((void **)&g->stage[s][1], pts * sizeof(double), "host-path staging") ||
+                dev_malloc((void **)&g->stage[s][2], pts * np * sizeof(double), "host-path staging"))
+                return PDF_E_NOMEM;
         }
         g->stage_pts = pts;
         g->stage_pid = np;

@@ -31,7 +31,16 @@ int fail(int code, const std::string &msg)
 int cuda_fail(cudaError_t e, const char *what)
 {
     t_err = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();   // a non-sticky error must not resurface in a later check
     return PDF_E_CUDA;
+}
+
+int dev_malloc(void **p, size_t bytes, const char *what)
+{
+    if (cudaMalloc(p, bytes) == cudaSuccess) return PDF_OK;
+    *p = nullptr;
+    (void)cudaGetLastError();
+    return fail(PDF_E_NOMEM, std::string(what) + ": out of device memory");
 }
 
 void clear_error() { t_err.clear(); }
@@ -227,12 +236,31 @@ int build_coefficients(pdfgpu_grid *g, const double *dev_values, cudaStream_t s)
 
 // --------------------------------------------------------------- the ABI
 
+// Frees everything a grid handle owns.  Leaves the thread's error message
+// alone, so that a failing pdf_load_grid keeps the message of the step that
+// failed.
+static void release_grid(pdfgpu_grid *g)
+{
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    for (void *p : g->blocks) cudaFree(p);
+    if (g->partials) cudaFree(g->partials);
+    if (g->lumi_scratch) cudaFree(g->lumi_scratch);
+    for (int s = 0; s < 3; ++s) {
+        for (int k = 0; k < 3; ++k)
+            if (g->stage[s][k]) cudaFree(g->stage[s][k]);
+        if (g->hs[s]) cudaStreamDestroy(g->hs[s]);
+    }
+    delete g;
+}
+
 template <typename T>
 static int dev_upload(pdfgpu_grid *g, const T *host, size_t count, const T **dst)
 {
     void *p = nullptr;
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    if (cudaMalloc(&p, bytes) != cudaSuccess) return fail(PDF_E_NOMEM, "cudaMalloc failed");
+    int rc = dev_malloc(&p, bytes, "grid table");
+    if (rc) return rc;
     g->blocks.push_back(p);
     if (count) PDF_CUDA(cudaMemcpy(p, host, count * sizeof(T), cudaMemcpyHostToDevice));
     *dst = (const T *)p;
@@ -243,7 +271,7 @@ static int dev_upload(pdfgpu_grid *g, const T *host, size_t count, const T **dst
     do {                                \
         int rc__ = (x);                 \
         if (rc__ != PDF_OK) {           \
-            pdf_free_grid(g);           \
+            release_grid(g);            \
             return rc__;                \
         }                               \
     } while (0)
@@ -443,9 +471,9 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     size_t ncoef = (size_t)D.n_members * nqc * nxc * D.n_flav * 16;
     {
         void *p = nullptr;
-        if (cudaMalloc(&p, ncoef * sizeof(double)) != cudaSuccess) {
-            pdf_free_grid(g);
-            return fail(PDF_E_NOMEM, "cudaMalloc of the coefficient table failed");
+        if (dev_malloc(&p, ncoef * sizeof(double), "coefficient table") != PDF_OK) {
+            release_grid(g);
+            return PDF_E_NOMEM;
         }
         g->blocks.push_back(p);
         d.coef = (const double *)p;
@@ -453,9 +481,9 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     if (D.values) {
         size_t nval = (size_t)D.n_members * rows * nx * D.n_flav;
         void *p = nullptr;
-        if (cudaMalloc(&p, nval * sizeof(double)) != cudaSuccess) {
-            pdf_free_grid(g);
-            return fail(PDF_E_NOMEM, "cudaMalloc of the value upload failed");
+        if (dev_malloc(&p, nval * sizeof(double), "value upload") != PDF_OK) {
+            release_grid(g);
+            return PDF_E_NOMEM;
         }
         cudaError_t e = cudaMemcpy(p, D.values, nval * sizeof(double), cudaMemcpyHostToDevice);
         int rc = e == cudaSuccess ? build_coefficients(g, (const double *)p, 0) : cuda_fail(e, "upload");
@@ -465,7 +493,7 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
         }
         cudaFree(p);
         if (rc != PDF_OK) {
-            pdf_free_grid(g);
+            release_grid(g);
             return rc;
         }
     }
@@ -488,17 +516,7 @@ extern "C" int pdf_free_grid(pdfgpu_grid_t g)
     PDF_TRACE("pdf_free_grid");
     clear_error();
     if (!g) return fail(PDF_E_ARG, "null grid handle");
-    cudaSetDevice(g->device);
-    cudaDeviceSynchronize();
-    for (void *p : g->blocks) cudaFree(p);
-    if (g->partials) cudaFree(g->partials);
-    if (g->lumi_scratch) cudaFree(g->lumi_scratch);
-    for (int s = 0; s < 3; ++s) {
-        for (int k = 0; k < 3; ++k)
-            if (g->stage[s][k]) cudaFree(g->stage[s][k]);
-        if (g->hs[s]) cudaStreamDestroy(g->hs[s]);
-    }
-    delete g;
+    release_grid(g);
     return PDF_OK;
 }
 

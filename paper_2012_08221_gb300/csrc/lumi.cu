@@ -423,7 +423,8 @@ extern "C" int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, c
         if (g->partials) cudaFree(g->partials);
         g->partials = nullptr;
         g->partials_cap = 0;
-        PDF_CUDA(cudaMalloc(&g->partials, (size_t)grid * sizeof(double)));
+        rc = dev_malloc((void **)&g->partials, (size_t)grid * sizeof(double), "luminosity partial sums");
+        if (rc) return rc;
         g->partials_cap = grid;
     }
     k<<<grid, kBlock, 0, s>>>(g->d, anti, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s, n, lum, alphas,
@@ -467,8 +468,7 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
         if (g->lumi_scratch) cudaFree(g->lumi_scratch);
         g->lumi_scratch = nullptr;
         g->lumi_scratch_bytes = 0;
-        if (cudaMalloc(&g->lumi_scratch, need) != cudaSuccess)
-            return fail(PDF_E_NOMEM, "luminosity adjoint scratch allocation failed");
+        if (dev_malloc(&g->lumi_scratch, need, "luminosity adjoint scratch")) return PDF_E_NOMEM;
         g->lumi_scratch_bytes = need;
     }
     char *base = (char *)g->lumi_scratch;

@@ -53,6 +53,12 @@ int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 void clear_error();
 
+// cudaMalloc that leaves no error behind: on failure *p is NULL, the CUDA
+// runtime's last-error state is cleared (so that a later launch check on this
+// thread does not report it again) and PDF_E_NOMEM is returned with `what` in
+// the thread's message.
+int dev_malloc(void **p, size_t bytes, const char *what);
+
 #define PDF_CUDA(call)                                      \
     do {                                                    \
         cudaError_t e__ = (call);                           \

@@ -30,7 +30,8 @@ extern "C" int pdf_probe_fp64_peak(double *flops)
     const int block = 256, per_sm = 4, iters = 4096;
     const int blocks = sms * per_sm;
     double *buf = nullptr;
-    PDF_CUDA(cudaMalloc(&buf, (size_t)blocks * block * sizeof(double)));
+    int rc = pdfgpu::dev_malloc((void **)&buf, (size_t)blocks * block * sizeof(double), "probe buffer");
+    if (rc) return rc;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

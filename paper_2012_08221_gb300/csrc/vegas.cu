@@ -240,7 +240,8 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
         if (g->partials) cudaFree(g->partials);
         g->partials = nullptr;
         g->partials_cap = 0;
-        PDF_CUDA(cudaMalloc(&g->partials, (size_t)2 * grid * sizeof(double)));
+        rc = dev_malloc((void **)&g->partials, (size_t)2 * grid * sizeof(double), "VEGAS partial sums");
+        if (rc) return rc;
         g->partials_cap = 2 * grid;
     }
     k<<<grid, kBlock, smem, s>>>(g->d, anti, member, ln_tau_min, ln_s, n_bins, edges, v, n, g->partials,

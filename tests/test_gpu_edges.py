@@ -85,3 +85,31 @@ def test_one_point_everywhere(nn):
     L, lum, a_s = luminosity(pdf, DeviceEvents.from_host(ev))
     Lr, lumr, asr = o.lumi(ev)
     assert abs(L.item() - Lr) <= 1e-12 * (abs(Lr) + 1e3) and L.item() == lum.item()
+
+
+def test_out_of_device_memory_is_reported_and_leaves_nothing_behind(nn):
+    """A grid whose coefficient table cannot fit on the device (2e4 members of
+    15 MB: 300 GB) fails to load with PDF_E_NOMEM and a message naming the
+    table; the failed allocation leaves no error state behind, so the next
+    calls on the thread (a load, a launch) succeed."""
+    import ctypes as C
+    from paper_2012_08221_gb300._lib import GridDesc, lib
+    from paper_2012_08221_gb300.pdf import PDF
+    g, pdf, o = nn
+    xk = np.ascontiguousarray(g.x_knots, dtype=np.float64)
+    nq = np.ascontiguousarray(g.n_q, dtype=np.int32)
+    qk = np.ascontiguousarray(g.q_knots, dtype=np.float64)
+    pids = np.ascontiguousarray(g.pids, dtype=np.int32)
+    d = GridDesc()
+    d.n_x, d.x_knots = xk.size, xk.ctypes.data_as(C.POINTER(C.c_double))
+    d.n_sub, d.n_q = nq.size, nq.ctypes.data_as(C.POINTER(C.c_int32))
+    d.q_knots = qk.ctypes.data_as(C.POINTER(C.c_double))
+    d.n_flav, d.pids = pids.size, pids.ctypes.data_as(C.POINTER(C.c_int32))
+    d.n_members, d.values, d.alphas, d.interp, d.extrap = 20_000, None, None, 0, 0
+    h = C.c_void_p()
+    assert lib().pdf_load_grid(C.byref(d), C.byref(h)) == -5          # PDF_E_NOMEM
+    assert b"coefficient table" in lib().pdf_last_error()
+    x, q2, _ = synth.queries_nnpdf(5003, seed=73)
+    p2 = PDF.from_grid(g)
+    got = p2.xfxQ2(g.pids, torch.as_tensor(x, device="cuda"), torch.as_tensor(q2, device="cuda"))
+    assert torch.equal(got, pdf.xfxQ2(g.pids, torch.as_tensor(x, device="cuda"), torch.as_tensor(q2, device="cuda")))
