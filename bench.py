@@ -36,6 +36,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -249,10 +250,33 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
+def kernel_source(path, name):
+    """The text of the function `name` defined in `path` (a kernel or its
+    launcher): from the template line above its signature to its closing
+    brace."""
+    text = open(os.path.join(ROOT, path)).read()
+    m = re.search(r"^(template <[^\n]*>\n)?[A-Za-z_][^\n;]*\b" + re.escape(name) + r"\(", text, re.M)
+    if m is None:
+        raise KeyError(f"{name} not in {path}")
+    i = text.index("{", m.end())
+    depth = 0
+    for j in range(i, len(text)):
+        depth += {"{": 1, "}": -1}.get(text[j], 0)
+        if depth == 0:
+            return text[m.start():j + 1]
+    raise ValueError(f"unbalanced braces after {name} in {path}")
+
+
 def source_hash(files):
+    """Hash of a kernel's sources: whole files, or "path::kernel" for the one
+    function (so that host code beside it does not invalidate a capture)."""
     h = hashlib.sha256()
     for f in files:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+        if "::" in f:
+            path, name = f.split("::")
+            h.update(kernel_source(path, name).encode())
+        else:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
