@@ -40,10 +40,10 @@ def _requests(grids, pdfs, scale, seed=2004):
     return reqs
 
 
-def test_batched_equals_standalone_and_oracle(sets, tmp_path):
+def test_batched_equals_standalone_and_oracle(sets, tmp_path, monkeypatch):
     from paper_2012_08221_gb300.batch import Batch
     grids, pdfs = sets
-    os.environ["PDFGPU_TUNE_CACHE"] = str(tmp_path / "tune.json")
+    monkeypatch.setenv("PDFGPU_TUNE_CACHE", str(tmp_path / "tune.json"))
     reqs = _requests(grids, pdfs, scale=0.01)
     # a few edge requests: one point, out-of-range points, absent pid
     g0 = grids[0]
@@ -84,7 +84,6 @@ def test_batched_equals_standalone_and_oracle(sets, tmp_path):
     B2 = Batch([r[:6] for r in reqs])
     i2 = B2.info()
     assert (i2["block"], i2["qpt"], i2["stage"]) == (entry["block"], entry["qpt"], entry["stage"])
-    del os.environ["PDFGPU_TUNE_CACHE"]
 
 
 @pytest.mark.parametrize("shape", ["untuned"])
