@@ -265,8 +265,21 @@ int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n
                       : (cont ? k_xfxq2<false, true, false> : k_xfxq2<false, false, false>);
     rc = allow_dynamic_smem((const void *)k, smem);
     if (rc) return rc;
-    int grid = wave_grid(g, (const void *)k, kBlock, smem, n);
-    k<<<grid, kBlock, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out, tape);
+    // A query shorter than one wave runs in the smallest CTAs (32, 64 or 128
+    // threads) whose grid still fits in one wave, so that the CTAs spread
+    // evenly over the SMs: in 256-thread CTAs a short query leaves some SMs
+    // a whole CTA (8 warps of points) more than others.
+    int block = kBlock;
+    for (int b : {32, 64, 128}) {
+        const size_t sb = (size_t)b * n_pid * sizeof(double);
+        if ((n + b - 1) / b <= (int64_t)g->sm_count * occupancy((const void *)k, b, sb)) {
+            block = b;
+            smem = sb;
+            break;
+        }
+    }
+    int grid = wave_grid(g, (const void *)k, block, smem, n);
+    k<<<grid, block, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out, tape);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }

@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -47,9 +48,26 @@ void clear_error() { t_err.clear(); }
 
 int occupancy(const void *kernel, int block, size_t smem)
 {
+    // cached per (device, kernel, block, shared memory): launches ask often
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, kernel, block, smem);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) n = 1;
-    return n < 1 ? 1 : n;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 1;
+    }
+    n = n < 1 ? 1 : n;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = n;
+    return n;
 }
 
 int allow_dynamic_smem(const void *kernel, size_t bytes)
