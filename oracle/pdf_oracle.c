@@ -16,7 +16,8 @@
  *   formulas; this oracle fixes them as follows, in the order it evaluates:
  *
  *   1. Domain: x <= 0, x > 1, Q^2 <= 0, Q^2 infinite or NaN -> NaN.  Then the
- *      flavour: pid 21 means the gluon, pid 0; a pid absent from the grid -> 0.
+ *      flavour: pid 21 means the gluon, pid 0, in a query and in the grid's
+ *      flavour list; a pid absent from the grid -> 0.
  *   2. Knot derivative of data g on knots z_0..z_{n-1}: one-sided secant at the
  *      first and last knot, mean of the two adjacent secants inside.
  *   3. Cubic Hermite on [z_k, z_{k+1}] with t = (z - z_k)/dz:
@@ -316,11 +317,15 @@ static double eval_uw(const acc_t *a, double u, double w, double *du, double *dw
 
 /* ---------------------------------------------------------------- public */
 
+/* The grid's a-th flavour with the gluon as 0: a grid may list its gluon as
+ * 21 or as 0, and a query may ask for it either way. */
+static int grid_pid(const orc_grid *g, int a) { return g->pids[a] == 21 ? 0 : g->pids[a]; }
+
 static int pid_column(const orc_grid *g, int pid)
 {
     if (pid == 21) pid = 0;
     for (int a = 0; a < g->n_flav; ++a)
-        if (g->pids[a] == pid) return a;
+        if (grid_pid(g, a) == pid) return a;
     return -1;
 }
 
@@ -590,7 +595,7 @@ double orc_lumi_batch(const orc_grid *g, int member, const double *ln_tau, const
         event_uw(ln_tau[e], y[e], flags[e], ln_mu2[e], ln_x1[e], ln_s, &u1, &u2, &w);
         double s = 0.0;
         for (int a = 0; a < g->n_flav; ++a) {
-            int pa = g->pids[a];
+            int pa = grid_pid(g, a);
             double f1 = orc_xfxq2_uw(g, member, pa, u1, w, NULL, NULL);
             double f2 = orc_xfxq2_uw(g, member, -pa, u2, w, NULL, NULL);
             s += f1 * f2;
@@ -615,8 +620,8 @@ void orc_lumi_dgrid(const orc_grid *g, int member, const double *ln_tau, const d
         double uu[2], w;
         event_uw(ln_tau[e], y[e], flags[e], ln_mu2[e], ln_x1[e], ln_s, &uu[0], &uu[1], &w);
         for (int a = 0; a < F; ++a) {
-            f1[a] = orc_xfxq2_uw(g, member, g->pids[a], uu[0], w, NULL, NULL);
-            f2[a] = orc_xfxq2_uw(g, member, g->pids[a], uu[1], w, NULL, NULL);
+            f1[a] = orc_xfxq2_uw(g, member, grid_pid(g, a), uu[0], w, NULL, NULL);
+            f2[a] = orc_xfxq2_uw(g, member, grid_pid(g, a), uu[1], w, NULL, NULL);
         }
         for (int side = 0; side < 2; ++side) {
             const double *other = side == 0 ? f2 : f1;
@@ -630,7 +635,7 @@ void orc_lumi_dgrid(const orc_grid *g, int member, const double *ln_tau, const d
                         /* d(sum_a f_a(x1) f_{-a}(x2)) / d v[.][b]:
                          * side 0 (a = b): weight at x1 times f_{-b}(x2);
                          * side 1 (-a = b): f_{-b}(x1) times weight at x2. */
-                        int cb = pid_column(g, -g->pids[b]);
+                        int cb = pid_column(g, -grid_pid(g, b));
                         if (cb < 0) continue;
                         double t = wt * other[cb] / (double)n;
                         grad[((size_t)r * g->n_x + k) * F + b] += absval ? fabs(t) : t;
@@ -684,7 +689,7 @@ void orc_vegas_sums(const orc_grid *g, int member, double ln_tau_min, double ln_
         double u1 = h + y, u2 = h - y, w = ln_tau + ln_s;
         double lum = 0.0;
         for (int a = 0; a < g->n_flav; ++a) {
-            int pa = g->pids[a];
+            int pa = grid_pid(g, a);
             lum += orc_xfxq2_uw(g, member, pa, u1, w, NULL, NULL) *
                    orc_xfxq2_uw(g, member, -pa, u2, w, NULL, NULL);
         }

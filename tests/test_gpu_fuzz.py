@@ -1,0 +1,120 @@
+"""Randomly shaped grids against the oracle: 2 to 30 x knots with random
+spacing (the last one at x = 1 or below it), 1 to 4 Q subgrids of 2 to 9
+knots each (duplicated threshold rows equal or not), 1 to 14 flavours with
+random distinct pids (the gluon as 0 or 21), 1 to 3 members, every
+interpolation kind with the linear, freeze and error options.  Checked per
+grid: x*f for a pid list with an absent pid, the pointwise form, alpha_s, and
+the adjoint (dL/dx, dL/dQ^2, dL/dgrid, also through the tape)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleGrid
+from paper_2012_08221_gb300 import synth
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N_GRIDS = 36
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _spaced(rng, lo, hi, n):
+    """n ascending values from lo to hi whose neighbouring gaps differ by at
+    most a factor e^1.6 (non-uniform, as real grids are, but not so uneven
+    that the finite-difference slopes become ill-conditioned)."""
+    if n == 1:
+        return np.array([lo])
+    gaps = np.exp(rng.uniform(-0.8, 0.8, n - 1))
+    v = lo + (hi - lo) * np.concatenate([[0.0], np.cumsum(gaps) / np.sum(gaps)])
+    v[-1] = hi
+    return v
+
+
+def random_grid(seed):
+    rng = np.random.default_rng(seed)
+    nx = int(rng.integers(2, 31))
+    u_hi = 0.0 if rng.random() < 0.6 else float(rng.uniform(-3.0, -0.5))
+    x = np.exp(_spaced(rng, float(rng.uniform(-21.0, -8.0)), u_hi, nx))
+    if u_hi == 0.0:
+        x[-1] = 1.0
+    nsub = int(rng.integers(1, 5))
+    bounds = np.exp(_spaced(rng, 0.0, float(rng.uniform(3.0, 11.5)), nsub + 1))
+    nq = rng.integers(2, 10, nsub).astype(np.int32)
+    q = np.concatenate([np.exp(_spaced(rng, math.log(bounds[s]), math.log(bounds[s + 1]), int(nq[s])))
+                        for s in range(nsub)])
+    F = int(rng.integers(1, 15))
+    pids = rng.choice(np.arange(-6, 7), size=min(F, 13), replace=False).astype(np.int32)
+    if rng.random() < 0.5 and 0 in pids:
+        pids[pids == 0] = 21
+    nmem = int(rng.integers(1, 4))
+    rows = q.size
+    v = rng.uniform(-1.0, 2.0, size=(nmem, rows, nx, pids.size))
+    a = rng.uniform(0.1, 0.4, size=rows)
+    if rng.random() < 0.5:                     # equal duplicated threshold rows
+        r = np.cumsum(nq)[:-1]
+        v[:, r] = v[:, r - 1]
+        a[r] = a[r - 1]
+    return synth.Grid(x, nq, q, pids, v, a, f"fuzz{seed}"), rng
+
+
+def _points(g, rng, n):
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    x = np.exp(rng.uniform(U[0] - 2.0, 0.0, n))
+    q2 = np.exp(rng.uniform(W[0] - 2.0, W[-1] + 2.0, n))
+    k = min(n // 4, g.x_knots.size * 4)
+    x[:k] = rng.choice(g.x_knots, k)           # exact knots and thresholds
+    q2[:k] = rng.choice(g.q_knots, k) ** 2
+    return x, q2
+
+
+@pytest.mark.parametrize("seed", range(N_GRIDS))
+def test_random_grid_against_the_oracle(seed):
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    g, rng = random_grid(7000 + seed)
+    interp, extrap = seed % 3, (seed // 3) % 3
+    pdf = PDF.from_grid(g, interp=interp, extrap=extrap)
+    o = OracleGrid.from_synth(g, interp=interp, extrap=extrap)
+    x, q2 = _points(g, rng, 4001)
+    X, Q = cuda(x), cuda(q2)
+    member = int(rng.integers(0, g.values.shape[0]))
+    pids = np.append(rng.permutation(g.pids), 5 if 5 not in g.pids else 6 if 6 not in g.pids else 22)
+    pids = pids.astype(np.int32)
+    got = pdf.xfxQ2(pids, X, Q, member).cpu().numpy()
+    parity.check(got, o.xfxq2_batch(pids, x, q2, member=member), o.kappa(pids, x, q2, member=member),
+                 what=f"fuzz {seed} xfxQ2")
+    pid = rng.choice(pids, x.size).astype(np.int32)
+    got = pdf.xfxQ2_pw(cuda(pid), X, Q, member).cpu().numpy()
+    parity.check(got, o.xfxq2_pw(pid, x, q2, member=member), o.kappa(pid, x, q2, member=member, pointwise=True),
+                 what=f"fuzz {seed} pointwise")
+    ra = o.alphas_batch(q2)
+    parity.check(pdf.alphasQ2(Q).cpu().numpy(), ra, 8 * np.abs(np.nan_to_num(ra)), what=f"fuzz {seed} alpha_s")
+    # the adjoint, pointwise, from scratch and from the tape
+    w = rng.standard_normal(x.size)
+    T = pdf.new_tape(x.size)
+    pdf.xfxQ2_pw(cuda(pid), X, Q, member, tape=T)
+    rdx, rdq = o.grad_pw(pid, x, q2, member=member)
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    vmax = np.max(np.abs(g.values))
+    scale = {"x": np.abs(w) * vmax * 8 / np.min(np.diff(U)),
+             "q": np.abs(w) * vmax * 8 / np.min(np.diff(W)[np.diff(W) > 0])}
+    ref = o.dgrid_pw(pid, x, q2, w)
+    kg = o.dgrid_pw(pid, x, q2, w, absval=True)
+    for tape in (None, T):
+        gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+        gx, gq, _ = pdf.xfxQ2_backward(cuda(pid), X, Q, cuda(w), member=member, pointwise=True,
+                                       grad_values=gv, tape=tape)
+        for got, want, z, sc in ((gx, w * rdx, x, scale["x"]), (gq, w * rdq, q2, scale["q"])):
+            got = got.cpu().numpy()
+            assert np.array_equal(np.isnan(got), np.isnan(want)), seed
+            m = ~np.isnan(want)
+            assert np.all(np.abs(got[m] - want[m]) <= 1e-9 * (np.abs(want[m]) + sc[m] / z[m])), seed
+        if extrap != 2:
+            assert np.all(np.abs(gv.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kg) + 1e-300), seed

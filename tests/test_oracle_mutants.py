@@ -140,6 +140,41 @@ def pin_failures():
     return fails
 
 
+FLAVOUR_MUTANTS = {
+    "a grid's gluon listed as 21 not recognised": (
+        "static int grid_pid(const orc_grid *g, int a) { return g->pids[a] == 21 ? 0 : g->pids[a]; }",
+        "static int grid_pid(const orc_grid *g, int a) { return g->pids[a]; }"),
+    "a query's pid 21 not mapped to the gluon": ("    if (pid == 21) pid = 0;\n", ""),
+}
+
+
+def flavour_pin_fails():
+    """Gluon as 0 or 21, in the query and in the grid's flavour list."""
+    g0 = tiny_two_sub(seed=43)
+    p21 = g0.pids.copy()
+    p21[p21 == 0] = 21
+    g21 = synth.Grid(g0.x_knots, g0.n_q, g0.q_knots, p21, g0.values, g0.alphas, "g21")
+    o0, o21 = O.OracleGrid.from_synth(g0), O.OracleGrid.from_synth(g21)
+    x, q2 = np.array([3e-4, 0.02, 0.5]), np.array([1.5, 4.0, 30.0])
+    ref = o0.xfxq2_batch([0], x, q2)
+    return not (np.array_equal(o0.xfxq2_batch([21], x, q2), ref) and
+                np.array_equal(o21.xfxq2_batch([0], x, q2), ref) and
+                np.array_equal(o21.xfxq2_batch([21], x, q2), ref) and np.any(ref != 0.0))
+
+
+def test_unmodified_oracle_passes_the_flavour_pin():
+    assert not flavour_pin_fails()
+
+
+@pytest.mark.parametrize("name", sorted(FLAVOUR_MUTANTS))
+def test_planted_flavour_mistake_is_caught(name, tmp_path, swap_oracle):
+    old, new = FLAVOUR_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    O._lib = build_variant(str(tmp_path), text.replace(old, new))
+    assert flavour_pin_fails(), f"no pin catches: {name}"
+
+
 @pytest.fixture
 def swap_oracle():
     saved = O._lib

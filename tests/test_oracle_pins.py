@@ -342,6 +342,29 @@ def test_domain_and_flavour_rules(small):
     assert o.xfxq2(1, 1.0, 100.0) == 0.0                # x = 1 knot carries (1-x)^beta = 0
 
 
+def test_gluon_listed_as_21_on_the_grid(nnpdf):
+    """A grid may list its gluon as 21 (the LHAPDF flavour line does): the
+    same values under pid 0 or 21 in a query, the same luminosity (the gluon
+    pairs with itself) and the same gradients as with the gluon listed as 0."""
+    g0 = nnpdf
+    p21 = g0.pids.copy()
+    p21[p21 == 0] = 21
+    g21 = synth.Grid(g0.x_knots, g0.n_q, g0.q_knots, p21, g0.values, g0.alphas, "g21")
+    o0, o21 = orc(g0), orc(g21)
+    x, q2, _ = synth.queries_nnpdf(2000, seed=31)
+    for q in (0, 21):
+        assert np.array_equal(o21.xfxq2_batch([q, 2, -1], x, q2), o0.xfxq2_batch([0, 2, -1], x, q2))
+    assert np.any(o21.xfxq2_batch([21], x, q2) != 0.0)
+    ev = synth.events_lhc(500, seed=32)
+    L0, lum0, _ = o0.lumi(ev)
+    L21, lum21, _ = o21.lumi(ev)
+    assert np.array_equal(lum0, lum21) and L0 == L21
+    assert np.array_equal(o0.lumi_dgrid(ev), o21.lumi_dgrid(ev))
+    pid = np.where(np.arange(x.size) % 2 == 0, 21, 2).astype(np.int32)
+    w = np.ones(x.size)
+    assert np.array_equal(o0.dgrid_pw(pid, x, q2, w), o21.dgrid_pw(pid, x, q2, w))
+
+
 # --------------------------------------------------------------- luminosity
 
 def test_luminosity_constant_grid_closed_form(nnpdf):
