@@ -118,3 +118,30 @@ def test_random_grid_against_the_oracle(seed):
             assert np.all(np.abs(got[m] - want[m]) <= 1e-9 * (np.abs(want[m]) + sc[m] / z[m])), seed
         if extrap != 2:
             assert np.all(np.abs(gv.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kg) + 1e-300), seed
+
+
+@pytest.mark.parametrize("seed", range(0, N_GRIDS, 3))
+def test_random_grid_luminosity_against_the_oracle(seed):
+    """The fused luminosity and its grid gradient on the same random grids
+    (linear and freeze options): per-event values and dL/dvalues against the
+    oracle; a gluon listed as 21 still pairs with itself."""
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity, luminosity_backward
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    g, rng = random_grid(7000 + seed)
+    interp, extrap = seed % 3, (seed // 3) % 2
+    pdf = PDF.from_grid(g, interp=interp, extrap=extrap)
+    o = OracleGrid.from_synth(g, interp=interp, extrap=extrap)
+    ev = synth.events_lhc(3001, seed=8000 + seed)
+    dev = DeviceEvents.from_host(ev)
+    member = int(rng.integers(0, g.values.shape[0]))
+    L, lum, _ = luminosity(pdf, dev, member=member)
+    Lr, lumr, _ = o.lumi(ev, member=member)
+    scale = g.pids.size * np.max(np.abs(g.values)) ** 2
+    assert np.all(np.abs(lum.cpu().numpy() - lumr) <= 1e-11 * (np.abs(lumr) + scale)), seed
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    luminosity_backward(pdf, dev, 1.0, gv, member=member)
+    ref = o.lumi_dgrid(ev, member=member)
+    kap = o.lumi_dgrid(ev, member=member, absval=True)
+    assert np.all(np.abs(gv.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kap) + 1e-300), seed
