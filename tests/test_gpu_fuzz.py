@@ -145,3 +145,34 @@ def test_random_grid_luminosity_against_the_oracle(seed):
     ref = o.lumi_dgrid(ev, member=member)
     kap = o.lumi_dgrid(ev, member=member, absval=True)
     assert np.all(np.abs(gv.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kap) + 1e-300), seed
+
+
+@pytest.mark.parametrize("batch_seed", range(4))
+def test_random_grids_in_one_batched_launch(batch_seed):
+    """Requests over several random grids (and options) in one persistent
+    launch, with and without the shared-memory staging of the knot tables:
+    every request equals its standalone call bit for bit."""
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.batch import Batch
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    rng = np.random.default_rng(9000 + batch_seed)
+    grids = [random_grid(7100 + 10 * batch_seed + k)[0] for k in range(4)]
+    pdfs = [PDF.from_grid(g, interp=k % 3, extrap=(k + batch_seed) % 3) for k, g in enumerate(grids)]
+    reqs = []
+    for r in range(40):
+        k = int(rng.integers(0, len(grids)))
+        g = grids[k]
+        n = int(rng.integers(0, 5000))
+        x, q2 = _points(g, rng, max(n, 1))
+        pids = rng.choice(np.append(g.pids, 7), size=int(rng.integers(1, 4))).astype(np.int32)
+        out = torch.empty((n, pids.size), dtype=torch.float64, device="cuda")
+        reqs.append((pdfs[k], int(rng.integers(0, g.values.shape[0])), pids, cuda(x[:n]), cuda(q2[:n]), out))
+    for tune in (False, True):
+        for r in reqs:
+            r[5].fill_(-7.0)
+        Batch(reqs, autotune=tune).run()
+        torch.cuda.synchronize()
+        for pdf, member, pids, X, Q, out in reqs:
+            ref = pdf.xfxQ2(pids, X, Q, member)
+            assert torch.equal(torch.nan_to_num(out, nan=3.0), torch.nan_to_num(ref, nan=3.0)), (batch_seed, tune)
