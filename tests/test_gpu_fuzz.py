@@ -176,3 +176,34 @@ def test_random_grids_in_one_batched_launch(batch_seed):
         for pdf, member, pids, X, Q, out in reqs:
             ref = pdf.xfxQ2(pids, X, Q, member)
             assert torch.equal(torch.nan_to_num(out, nan=3.0), torch.nan_to_num(ref, nan=3.0)), (batch_seed, tune)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_vegas_maps_against_the_oracle(seed):
+    """The general VEGAS map and accumulation for random dimensions (1 to
+    16), bin counts (2 to 1024) and uneven edges, with uniforms that include
+    0 and values next to 1: bins bit for bit, points and Jacobians to
+    rounding, sums to 1e-12 of their scale."""
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.vegas import Vegas
+    from oracle.oracle import vegas_accumulate, vegas_map
+    build.build()
+    rng = np.random.default_rng(9500 + seed)
+    dim, n_bins = int(rng.integers(1, 17)), int(rng.choice([2, 3, 7, 50, 128, 1024]))
+    widths = np.exp(rng.uniform(-2.0, 2.0, (dim, n_bins)))
+    edges = np.concatenate([np.zeros((dim, 1)), np.cumsum(widths, 1) / widths.sum(1, keepdims=True)], 1)
+    edges[:, -1] = 1.0
+    v = rng.uniform(0, 1, (20_011, dim))
+    v[:3] = np.array([0.0, np.nextafter(1.0, 0.0), 0.5])[:, None]
+    vg = Vegas(dim, n_bins=n_bins)
+    vg.edges = edges
+    r, jac, bins = vg.map(cuda(v))
+    rr, rj, rb = vegas_map(edges, v)
+    assert np.array_equal(bins.cpu().numpy(), rb), seed
+    assert np.allclose(r.cpu().numpy(), rr, rtol=0, atol=1e-15), seed
+    assert np.allclose(jac.cpu().numpy(), rj, rtol=1e-13, atol=0), seed
+    w = rng.standard_normal(v.shape[0]) * np.exp(rng.uniform(-3, 3, v.shape[0]))
+    got = vg.accumulate(cuda(w), cuda(rb))
+    ref = vegas_accumulate(n_bins, w, rb)
+    scale = np.concatenate([[np.abs(w).sum()], ref[1:]])
+    assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300), seed
