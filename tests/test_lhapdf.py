@@ -57,3 +57,22 @@ def test_alpha_s_only_when_on_the_grid_knots(tmp_path):
     info = info.replace("AlphaS_Vals: [", "AlphaS_Vals: [0.6, ")
     (d / "A.info").write_text(info)
     assert lhapdf.read_set(str(d)).alphas is None
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_round_trip_random_grids(tmp_path, seed):
+    """Randomly shaped grids (2 to 30 x knots, x_max = 1 or below, 1 to 4
+    subgrids of 2 to 9 knots, random pids, 1 to 3 members) written as sets
+    read back bit for bit, member by member and all at once."""
+    from tests.tinygrids import random_grid
+    g, _ = random_grid(7200 + seed)
+    d = tmp_path / f"RAND{seed}"
+    lhapdf.write_set(str(d), g)
+    m = g.values.shape[0]
+    r = lhapdf.read_set(str(d), 0, m)
+    assert np.array_equal(r.x_knots, g.x_knots) and np.array_equal(r.n_q, g.n_q)
+    assert np.array_equal(r.q_knots, g.q_knots)
+    assert list(r.pids) == [21 if p == 0 else int(p) for p in g.pids]
+    assert np.array_equal(r.values, g.values) and np.array_equal(r.alphas, g.alphas)
+    for k in range(m):
+        assert np.array_equal(lhapdf.read_set(str(d), k, 1).values[0], g.values[k])
