@@ -169,3 +169,51 @@ def test_random_vegas_maps_against_the_oracle(seed):
     ref = vegas_accumulate(n_bins, w, rb)
     scale = np.concatenate([[np.abs(w).sum()], ref[1:]])
     assert np.all(np.abs(got - ref) <= 1e-12 * scale + 1e-300), seed
+
+
+def _edge_positions(knots_log, z):
+    t = np.zeros_like(z)
+    lo, hi = z < knots_log[0], z > knots_log[-1]
+    t[lo] = (z[lo] - knots_log[0]) / (knots_log[1] - knots_log[0])
+    t[hi] = (z[hi] - knots_log[-2]) / (knots_log[-1] - knots_log[-2])
+    return t
+
+
+@pytest.mark.parametrize("seed", range(0, N_GRIDS, 2))
+def test_random_grid_power_law_continuation(seed):
+    """The power-law continuation on the random grids (whose values change
+    sign, so both the power law and its linear fallback occur): x*f and
+    alpha_s against the oracle with the same option; inside the grid bit for
+    bit the linear option's values.  Outside, the power law raises the edge
+    values' rounding to the power |t| (up to 30 intervals out here, with edge
+    values down to the 1e-3 threshold and results up to 1e19), so the check
+    there is 1e-9 relative to the value or to kappa times the distance
+    (1 + |t_x|)(1 + |t_Q|): a wrong branch, knot or exponent is off by far
+    more."""
+    from paper_2012_08221_gb300 import build
+    from paper_2012_08221_gb300.pdf import PDF
+    build.build()
+    g, rng = random_grid(7000 + seed)
+    interp = seed % 3
+    pc = PDF.from_grid(g, interp=interp, extrap="continuation")
+    pl = PDF.from_grid(g, interp=interp, extrap="linear")
+    oc = OracleGrid.from_synth(g, interp=interp, extrap=3)
+    ol = OracleGrid.from_synth(g, interp=interp, extrap=0)
+    x, q2 = _points(g, rng, 4001)
+    X, Q = cuda(x), cuda(q2)
+    got = pc.xfxQ2(g.pids, X, Q).cpu().numpy()
+    lin = pl.xfxQ2(g.pids, X, Q).cpu().numpy()
+    tu = _edge_positions(np.log(g.x_knots), np.log(x))
+    tw = _edge_positions(np.log(g.q_knots ** 2), np.log(q2))
+    inside = (tu == 0) & (tw == 0)
+    assert np.array_equal(got[inside], lin[inside]), seed
+    grow = ((1 + np.abs(tu)) * (1 + np.abs(tw)))[:, None]
+    ref = oc.xfxq2_batch(g.pids, x, q2)
+    kap = ol.kappa(g.pids, x, q2)
+    parity.check(got[inside], ref[inside], kap[inside], what=f"fuzz {seed} continuation inside")
+    out = ~inside
+    err = np.abs(got[out] - ref[out])
+    assert np.all(err <= 1e-9 * (np.abs(ref[out]) + kap[out] * grow[out])), (seed, float(np.max(err)))
+    ra = oc.alphas_batch(q2)
+    parity.check(pc.alphasQ2(Q).cpu().numpy(), ra, 8 * np.abs(ra) * (1 + np.abs(tw)) ** 2,
+                 what=f"fuzz {seed} alpha_s")
