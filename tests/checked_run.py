@@ -71,6 +71,37 @@ def main():
     vg = Vegas(3, n_bins=20)
     r, jac, bins = vg.map(torch.rand((20_000, 3), dtype=torch.float64, device=dev))
     vg.accumulate(jac, bins)
+    # randomly shaped grids (2-knot subgrids, two x knots, x_max below 1...)
+    from tests.tinygrids import random_grid
+    for seed in range(12):
+        gr, rng = random_grid(7000 + seed)
+        p = PDF.from_grid(gr, interp=seed % 3, extrap=(seed // 3) % 4)
+        U, W = np.log(gr.x_knots), np.log(gr.q_knots ** 2)
+        x = np.exp(rng.uniform(U[0] - 3.0, 0.0, 20_001))
+        q2 = np.exp(rng.uniform(W[0] - 3.0, W[-1] + 3.0, 20_001))
+        X, Q = torch.as_tensor(x, device=dev), torch.as_tensor(q2, device=dev)
+        p.status()
+        res = [p.xfxQ2(gr.pids, X, Q), p.alphasQ2(Q)]
+        pid = torch.as_tensor(rng.choice(gr.pids, x.size).astype(np.int32), device=dev)
+        if (seed // 3) % 4 != 3:
+            T = p.new_tape(x.size)
+            res.append(p.xfxQ2_pw(pid, X, Q, tape=T))
+            gv = torch.zeros(gr.values.shape[1:], dtype=torch.float64, device=dev)
+            gx, gq, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
+                                         pointwise=True, grad_values=gv, tape=T)
+            res += [gx, gq]
+            if gr.pids.size <= 16:
+                ev = DeviceEvents.from_host(synth.events_lhc(5_001, seed=64 + seed))
+                L, lum, als = luminosity(p, ev)
+                res.append(lum)
+                gl = torch.zeros(gr.values.shape[1:], dtype=torch.float64, device=dev)
+                luminosity_backward(p, ev, 1.0, gl)
+        bp = gr.pids[:2].copy()
+        out2 = torch.empty((x.size, bp.size), dtype=torch.float64, device=dev)
+        Batch([(p, 0, bp, X, Q, out2)], autotune=False).run()
+        res.append(out2)
+        torch.cuda.synchronize()
+        out[f"random{seed}"] = {"status": p.status(), "digest": digest(*res)}
     print(json.dumps(out))
     return 0
 

@@ -1,8 +1,8 @@
 """The range-checked library (PDFGPU_CHECKED=1: every table index computed
 on the device is tested before use and a bad one sets PDF_S_BOUNDS) runs
-every form of the hot path, on all four extrapolation options, without a
-single out-of-range index, and gives bit for bit the outputs of the release
-library.  Both run in child processes: the library is chosen at import."""
+every form of the hot path, on all four extrapolation options and on 12
+randomly shaped grids, without a single out-of-range index, and gives bit
+for bit the outputs of the release library.  Both run in child processes: the library is chosen at import."""
 import json
 import os
 import subprocess
@@ -31,3 +31,7 @@ def test_checked_library_finds_no_bad_index_and_changes_nothing():
         assert not chk[extrap]["status"] & 4, extrap                 # PDF_S_BOUNDS never set
         assert chk[extrap]["digest"] == rel[extrap]["digest"], extrap
         assert chk[extrap]["status"] == rel[extrap]["status"], extrap
+    for seed in range(12):                                          # randomly shaped grids
+        k = f"random{seed}"
+        assert not chk[k]["status"] & 4, k
+        assert chk[k]["digest"] == rel[k]["digest"] and chk[k]["status"] == rel[k]["status"], k
