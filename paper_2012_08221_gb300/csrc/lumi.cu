@@ -263,6 +263,36 @@ __global__ void k_scatter(const int *__restrict__ key, int nrec, int *__restrict
     }
 }
 
+// The same scatter with one global atomic per (tile, cell) instead of one
+// per record: a block counts its tile's records per cell in shared memory,
+// reserves a range for each cell present, then places the records in their
+// ranges with shared-memory atomics.  The order inside a cell is free (the
+// accumulation sums the cell's records).  nbins <= kMaxSmemBins.
+constexpr int kScatterTile = 32768;
+
+__global__ void __launch_bounds__(kBlock) k_scatter_tiled(const int *__restrict__ key, int nrec, int nbins,
+                                                          int *__restrict__ cursor, int *__restrict__ perm)
+{
+    extern __shared__ int sc[];
+    const int r0 = blockIdx.x * kScatterTile, r1 = min(nrec, r0 + kScatterTile);
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sc[b] = 0;
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int k = key[r];
+        if (k >= 0) atomicAdd(&sc[k], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const int c = sc[b];
+        if (c) sc[b] = atomicAdd(&cursor[b], c);
+    }
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int k = key[r];
+        if (k >= 0) perm[atomicAdd(&sc[k], 1)] = r;
+    }
+}
+
 // Rebuild an axis from its stored local coordinate (t and range flag).  The
 // stored t is the effective one (0 or 1 when frozen at an edge), for which
 // the outside basis (1, t, t, t) and weights (1 - t, t) are the right ones.
@@ -486,6 +516,8 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     const void *krec = saved_p ? (const void *)k_lumi_rec<false> : (const void *)k_lumi_rec<true>;
     rc = allow_dynamic_smem(krec, hsmem);
     if (rc) return rc;
+    rc = allow_dynamic_smem((const void *)k_scatter_tiled, hsmem);
+    if (rc) return rc;
     for (int64_t e0 = 0; e0 < n; e0 += chunk) {
         const int m = (int)std::min(chunk, n - e0);
         PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
@@ -500,8 +532,13 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
         PDF_CUDA(cudaGetLastError());
         k_scan<<<1, 1024, 0, st>>>(hist, nbins, offs, cursor);
         PDF_CUDA(cudaGetLastError());
-        int gs = wave_grid(g, (const void *)k_scatter, kBlock, 0, 2 * (int64_t)m);
-        k_scatter<<<gs, kBlock, 0, st>>>(key, 2 * m, cursor, perm);
+        if (hsmem) {
+            const int tiles = (int)((2 * (int64_t)m + kScatterTile - 1) / kScatterTile);
+            k_scatter_tiled<<<tiles, kBlock, hsmem, st>>>(key, 2 * m, nbins, cursor, perm);
+        } else {
+            int gs = wave_grid(g, (const void *)k_scatter, kBlock, 0, 2 * (int64_t)m);
+            k_scatter<<<gs, kBlock, 0, st>>>(key, 2 * m, cursor, perm);
+        }
         PDF_CUDA(cudaGetLastError());
         int64_t warps = (2 * (int64_t)m + kSegment - 1) / kSegment;
         int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
