@@ -79,7 +79,12 @@ def test_random_grid_against_the_oracle(seed):
             m = ~np.isnan(want)
             assert np.all(np.abs(got[m] - want[m]) <= 1e-9 * (np.abs(want[m]) + sc[m] / z[m])), seed
         if extrap != 2:
-            assert np.all(np.abs(gv.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kg) + 1e-300), seed
+            # floor: stencil weights that vanish exactly (at the last knot of
+            # an axis the oracle divides, the kernels multiply by the
+            # interval's reciprocal, t = 1 - 1 ulp) leave rounding-size
+            # contributions, at most a few ulp of the point weights
+            floor = 1e-14 * np.abs(w).sum()
+            assert np.all(np.abs(gv.cpu().numpy() - ref) <= 1e-9 * np.maximum(np.abs(ref), kg) + floor), seed
 
 
 @pytest.mark.parametrize("seed", range(0, N_GRIDS, 3))
