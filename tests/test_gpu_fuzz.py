@@ -1,4 +1,4 @@
-"""Randomly shaped grids against the oracle: 2 to 30 x knots with random
+"""120 randomly shaped grids against the oracle: 2 to 30 x knots with random
 spacing (the last one at x = 1 or below it), 1 to 4 Q subgrids of 2 to 9
 knots each (duplicated threshold rows equal or not), 1 to 14 flavours with
 random distinct pids (the gluon as 0 or 21), 1 to 3 members, every
@@ -18,7 +18,7 @@ from tests.tinygrids import random_grid
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N_GRIDS = 36
+N_GRIDS = 120
 
 
 def cuda(a):
