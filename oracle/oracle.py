@@ -99,6 +99,8 @@ def _declare(L):
     L.orc_grad_pw_batch.argtypes = [_G, C.c_int, _I, _D, _D, C.c_int64, _D, _D]
     L.orc_kappa_batch.argtypes = [_G, C.c_int, _I, C.c_int, C.c_int, _D, _D,
                                   C.c_int64, _D]
+    L.orc_alphas_kappa_batch.argtypes = [_G, _D, C.c_int64, _D]
+    L.orc_alphas_kappa_batch.restype = None
     L.orc_dgrid_pw.argtypes = [_G, _I, _D, _D, _D, C.c_int64, _D, C.c_int]
     L.orc_dgrid_batch.argtypes = [_G, _I, C.c_int, _D, _D, _D, C.c_int64, _D, C.c_int]
     U8 = C.POINTER(C.c_ubyte)
@@ -256,6 +258,14 @@ class OracleGrid:
         out = np.empty(shape)
         lib().orc_kappa_batch(self.ptr, member, _i(pids), pids.size, int(pointwise),
                               _d(x), _d(q2), x.size, _d(out))
+        return out
+
+    def alphas_kappa(self, q2):
+        """Sum of |weight * alpha_s knot value| over the knots (tolerance
+        scale of alpha_s, as kappa is for x*f)."""
+        q2 = _f64(q2)
+        out = np.empty(q2.size)
+        lib().orc_alphas_kappa_batch(self.ptr, _d(q2), q2.size, _d(out))
         return out
 
     def dgrid_pw(self, pid, x, q2, gw, absval=False):

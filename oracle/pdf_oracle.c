@@ -522,6 +522,38 @@ void orc_kappa_batch(const orc_grid *g, int member, const int *pids, int n_pid, 
     }
 }
 
+/* kappa of alpha_s at each Q^2: the sum over the alpha_s knots r of
+ * |W_r(w) alpha_r|, W_r the interpolation of the indicator of knot r (step
+ * 8, as for the PDF values; outside the grid under option 3 the indicator
+ * falls back to the straight line, whose weights are used as the scale).
+ * NaN where alpha_s is NaN. */
+void orc_alphas_kappa_batch(const orc_grid *g, const double *q2, int64_t n, double *kappa)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double v = orc_alphas(g, q2[i]);
+        if (v != v) {
+            kappa[i] = NAN;
+            continue;
+        }
+        double w = log(q2[i]);
+        int c0, c1, r0, r1;
+        window(g, g->U[0], w, &c0, &c1, &r0, &r1);
+        double sum = 0.0;
+        for (int r = r0; r <= r1; ++r) {
+            acc_t a;
+            a.g = g;
+            a.base = NULL;
+            a.stride_row = a.stride_k = 0;
+            a.ind_row = r;
+            a.ind_k = 0;
+            xsel_t c = {0, 0.0};
+            sum += fabs(wdir(&a, &c, w, NULL, NULL) * g->alphas[r]);
+        }
+        kappa[i] = sum;
+    }
+}
+
 /* dL/dvalues for L = sum_i gw_i * xf_{pid_i}(x_i, Q^2_i), accumulated into
  * grad[rows][n_x][n_flav] (member's slice).  Serial: the sum order is fixed.
  * absval != 0 accumulates |gw_i * weight| instead: the magnitude of the terms

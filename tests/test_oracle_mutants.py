@@ -300,3 +300,66 @@ def test_planted_continuation_mistake_is_caught(name, tmp_path, swap_oracle):
     O._lib = build_variant(str(tmp_path), text.replace(old, new))
     assert continuation_pins_fail(), f"no pin catches: {name}"
     shutil.rmtree(tmp_path, ignore_errors=True)
+
+
+KAPPA_MUTANTS = {
+    "kappa takes every pid's values from the first pid's column": (
+        "int col = pid_column(g, pointwise ? pids[i] : pids[p]);",
+        "int col = pid_column(g, pointwise ? pids[i] : pids[0]);"),
+    "kappa reads member 0 whatever the member": (
+        "const double *vm = g->values + (size_t)member * g->rows * stride;",
+        "const double *vm = g->values;"),
+    "kappa keeps the sign of negative weights": (
+        "kappa[i * np + p] += fabs(wt * vm[(size_t)r * stride + (size_t)k * g->n_flav + col]);",
+        "kappa[i * np + p] += wt * fabs(vm[(size_t)r * stride + (size_t)k * g->n_flav + col]);"),
+    "kappa scan drops the last stencil knot": (
+        "for (int k = c0; k <= c1; ++k) {\n                double wt = orc_cell_weight_uw(g, r, k, u, w);\n"
+        "                if (wt == 0.0) continue;\n                for (int p = 0; p < np; ++p) {",
+        "for (int k = c0; k < c1; ++k) {\n                double wt = orc_cell_weight_uw(g, r, k, u, w);\n"
+        "                if (wt == 0.0) continue;\n                for (int p = 0; p < np; ++p) {"),
+    "pointwise gradient magnitudes without the point weight": (
+        "double t = gw[i] * wt;\n                grad[((size_t)r * g->n_x + k) * g->n_flav + col] += absval ? fabs(t) : t;",
+        "double t = gw[i] * wt;\n                grad[((size_t)r * g->n_x + k) * g->n_flav + col] += absval ? fabs(wt) : t;"),
+    "matrix-form gradient magnitudes keep the sign": (
+        "double t = gout[i * n_pid + p] * wt;\n                    grad[((size_t)r * g->n_x + k) * g->n_flav + col] "
+        "+= absval ? fabs(t) : t;",
+        "double t = gout[i * n_pid + p] * wt;\n                    grad[((size_t)r * g->n_x + k) * g->n_flav + col] "
+        "+= absval ? t : t;"),
+    "luminosity gradient magnitudes without the partner factor": (
+        "grad[((size_t)r * g->n_x + k) * F + b] += absval ? fabs(t) : t;",
+        "grad[((size_t)r * g->n_x + k) * F + b] += absval ? fabs(wt) : t;"),
+    "alpha_s kappa keeps the sign of negative weights": (
+        "sum += fabs(wdir(&a, &c, w, NULL, NULL) * g->alphas[r]);",
+        "sum += wdir(&a, &c, w, NULL, NULL) * g->alphas[r];"),
+    "alpha_s kappa takes every weight's value from the first knot of the window": (
+        "sum += fabs(wdir(&a, &c, w, NULL, NULL) * g->alphas[r]);",
+        "sum += fabs(wdir(&a, &c, w, NULL, NULL) * g->alphas[r0]);"),
+}
+
+
+def kappa_pins_fail():
+    """The tolerance-scale pins: kappa, alpha_s kappa and the |term| sums of
+    the gradients against exact weights, and kappa at knots."""
+    from tests import test_oracle_kappa as K
+    if K.kappa_vs_exact_weights(K.GRIDS[1], n=6) >= 1e-13:
+        return True
+    try:
+        K.test_kappa_at_knots_is_the_magnitude_of_the_value(K.GRIDS[1])
+    except AssertionError:
+        return True
+    return (K.dgrid_absval_vs_exact(n=6) >= 1e-13 or K.lumi_absval_vs_exact(n=5) >= 1e-13 or
+            K.alphas_kappa_vs_exact(n=16) >= 1e-13)
+
+
+def test_unmodified_oracle_passes_the_kappa_pins():
+    assert not kappa_pins_fail()
+
+
+@pytest.mark.parametrize("name", sorted(KAPPA_MUTANTS))
+def test_planted_kappa_mistake_is_caught(name, tmp_path, swap_oracle):
+    old, new = KAPPA_MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site not unique: {name}"
+    O._lib = build_variant(str(tmp_path), text.replace(old, new))
+    assert kappa_pins_fail(), f"no pin catches: {name}"
+    shutil.rmtree(tmp_path, ignore_errors=True)
