@@ -413,6 +413,15 @@ const char *pdf_last_error(void);
  * independent fused multiply-add chains timed with CUDA events. Synchronous. */
 int pdf_probe_fp64_peak(double *flops);
 
+/* Throughput of sm_103a's FP64 tensor instruction, mma.sync with f64
+ * operands (the only FP64 matrix path of this GPU; tcgen05 has no f64 kind),
+ * in FLOP/s (2 M N K per warp-wide instruction), from a kernel of eight
+ * independent accumulator chains per warp timed with CUDA events.
+ * shape 0: m8n8k4, 1: m16n8k4, 2: m16n8k8, 3: m16n8k16; PDF_E_ARG otherwise.
+ * Measures whether the interpolation's contraction could leave the DFMA pipe
+ * (a question of this GPU, not of the paper).  Synchronous. */
+int pdf_probe_fp64_mma_peak(int32_t shape, double *flops);
+
 /* The kernels' natural log (table-driven argument reduction after
  * P. T. P. Tang, ACM TOMS 16 (1990) 378, with a degree-5 series for
  * ln(1+r), |r| <= 2^-11) applied to n DEVICE doubles: out[i] = ln(in[i]) for

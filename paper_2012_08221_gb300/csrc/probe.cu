@@ -54,3 +54,148 @@ extern "C" int pdf_probe_fp64_peak(double *flops)
     *flops = 2.0 * 8.0 * (double)iters * blocks * block / (best * 1e-3);
     return PDF_OK;
 }
+
+// ------------------------------------------------------------ FP64 MMA probe
+//
+// Throughput of the FP64 tensor instructions (mma.sync with f64 operands, the
+// only FP64 matrix path of sm_103a: tcgen05 has no f64 kind) against the DFMA
+// chains above.  Each warp runs kChains independent accumulator chains of one
+// shape; a warp-wide mma of shape MxNxK counts 2 M N K flops.
+
+namespace {
+
+constexpr int kChains = 8;
+
+template <int SHAPE>
+struct MmaShape;
+template <>
+struct MmaShape<0> {   // m8n8k4: A 1, B 1, C/D 2 doubles per thread
+    static constexpr int M = 8, N = 8, K = 4, NA = 1, NB = 1, NC = 2;
+};
+template <>
+struct MmaShape<1> {   // m16n8k4: A 2, B 1, C/D 4
+    static constexpr int M = 16, N = 8, K = 4, NA = 2, NB = 1, NC = 4;
+};
+template <>
+struct MmaShape<2> {   // m16n8k8: A 4, B 2, C/D 4
+    static constexpr int M = 16, N = 8, K = 8, NA = 4, NB = 2, NC = 4;
+};
+template <>
+struct MmaShape<3> {   // m16n8k16: A 8, B 4, C/D 4
+    static constexpr int M = 16, N = 8, K = 16, NA = 8, NB = 4, NC = 4;
+};
+
+template <int SHAPE>
+__device__ __forceinline__ void mma_f64(double *d, const double *a, const double *b);
+
+template <>
+__device__ __forceinline__ void mma_f64<0>(double *d, const double *a, const double *b)
+{
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                 : "+d"(d[0]), "+d"(d[1])
+                 : "d"(a[0]), "d"(b[0]));
+}
+template <>
+__device__ __forceinline__ void mma_f64<1>(double *d, const double *a, const double *b)
+{
+    asm volatile("mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0, %1, %2, %3}, {%4, %5}, {%6}, "
+                 "{%0, %1, %2, %3};"
+                 : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+                 : "d"(a[0]), "d"(a[1]), "d"(b[0]));
+}
+template <>
+__device__ __forceinline__ void mma_f64<2>(double *d, const double *a, const double *b)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+                 : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
+}
+template <>
+__device__ __forceinline__ void mma_f64<3>(double *d, const double *a, const double *b)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f64.f64.f64.f64 {%0, %1, %2, %3}, "
+                 "{%4, %5, %6, %7, %8, %9, %10, %11}, {%12, %13, %14, %15}, {%0, %1, %2, %3};"
+                 : "+d"(d[0]), "+d"(d[1]), "+d"(d[2]), "+d"(d[3])
+                 : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(a[4]), "d"(a[5]), "d"(a[6]), "d"(a[7]),
+                   "d"(b[0]), "d"(b[1]), "d"(b[2]), "d"(b[3]));
+}
+
+template <int SHAPE>
+__global__ void k_dmma_chains(double *out, int iters)
+{
+    using S = MmaShape<SHAPE>;
+    double a[S::NA], b[S::NB], acc[kChains][S::NC];
+#pragma unroll
+    for (int k = 0; k < S::NA; ++k) a[k] = 1e-3 * (threadIdx.x + k);
+#pragma unroll
+    for (int k = 0; k < S::NB; ++k) b[k] = 0.5 - 1e-4 * k;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+#pragma unroll
+        for (int k = 0; k < S::NC; ++k) acc[c][k] = c + k;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) mma_f64<SHAPE>(acc[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+#pragma unroll
+        for (int k = 0; k < S::NC; ++k) s += acc[c][k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int SHAPE>
+int time_dmma(double *buf, int blocks, int block, double *flops)
+{
+    using S = MmaShape<SHAPE>;
+    const int iters = 2048;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_dmma_chains<SHAPE><<<blocks, block>>>(buf, 32);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0);
+        k_dmma_chains<SHAPE><<<blocks, block>>>(buf, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return pdfgpu::cuda_fail(err, "mma probe kernel");
+    const double warps = (double)blocks * (block / 32);
+    *flops = 2.0 * S::M * S::N * S::K * (double)kChains * iters * warps / (best * 1e-3);
+    return PDF_OK;
+}
+
+}  // namespace
+
+extern "C" int pdf_probe_fp64_mma_peak(int32_t shape, double *flops)
+{
+    PDF_TRACE("pdf_probe_fp64_mma_peak");
+    pdfgpu::clear_error();
+    if (!flops) return pdfgpu::fail(PDF_E_ARG, "null output");
+    if (shape < 0 || shape > 3) return pdfgpu::fail(PDF_E_ARG, "shape must be 0..3");
+    int dev = 0, sms = 0;
+    PDF_CUDA(cudaGetDevice(&dev));
+    PDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int block = 256, per_sm = 4;
+    const int blocks = sms * per_sm;
+    double *buf = nullptr;
+    int rc = pdfgpu::dev_malloc((void **)&buf, (size_t)blocks * block * sizeof(double), "probe buffer");
+    if (rc) return rc;
+    switch (shape) {
+    case 0: rc = time_dmma<0>(buf, blocks, block, flops); break;
+    case 1: rc = time_dmma<1>(buf, blocks, block, flops); break;
+    case 2: rc = time_dmma<2>(buf, blocks, block, flops); break;
+    default: rc = time_dmma<3>(buf, blocks, block, flops); break;
+    }
+    cudaFree(buf);
+    return rc;
+}

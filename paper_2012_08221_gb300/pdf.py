@@ -306,3 +306,15 @@ def fp64_peak() -> float:
     v = C.c_double()
     check("pdf_probe_fp64_peak", lib().pdf_probe_fp64_peak(C.byref(v)))
     return v.value
+
+
+MMA_SHAPES = ("m8n8k4", "m16n8k4", "m16n8k8", "m16n8k16")
+
+
+def fp64_mma_peak(shape: str = "m8n8k4") -> float:
+    """Measured throughput of the FP64 tensor instruction (``mma.sync`` with
+    f64 operands) of one shape on the current GPU, in FLOP/s (2 M N K per
+    warp-wide instruction)."""
+    v = C.c_double()
+    check("pdf_probe_fp64_mma_peak", lib().pdf_probe_fp64_mma_peak(MMA_SHAPES.index(shape), C.byref(v)))
+    return v.value
