@@ -135,8 +135,10 @@ def test_nnpdf_full_size_every_output(nnpdf):
         parity.check(got, ref, o.kappa(g.pids, x[sl], q2[sl]), what=f"nnpdf full size, points {s0}+")
         strict += parity.strict_count(got, ref)
     print(f"\nfull size: plain 1e-12 relative test would reject {strict} of {out.numel()}")
+    assert strict == 0
     ra = o.alphas_batch(q2a)
-    parity.check(a_s, ra, 8 * np.abs(ra), what="alphas full size")
+    parity.check(a_s, ra, o.alphas_kappa(q2a), what="alphas full size")
+    assert parity.strict_count(a_s, ra) == 0
 
 
 def test_alphas_parity(small, nnpdf):
@@ -144,9 +146,7 @@ def test_alphas_parity(small, nnpdf):
         q2 = np.exp(np.random.default_rng(4).uniform(math.log(0.01), math.log(1e12), 200_003))
         got = pdf.alphasQ2(cuda(q2)).cpu().numpy()
         ref = o.alphas_batch(q2)
-        # alpha_s values are O(0.1-1) and positive; the terms are bounded by a
-        # few times the knot values, so kappa = 8 |ref| is a safe term scale
-        parity.check(got, ref, 8 * np.abs(ref), what=f"alphas {g.name}")
+        parity.check(got, ref, o.alphas_kappa(q2), what=f"alphas {g.name}")
 
 
 def test_xfxq_is_xfxq2_of_q_squared(small):
@@ -187,7 +187,7 @@ def test_golden_exact_values(lib_built):
     pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
     got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
     parity.check(got, exp, o.kappa(g.pids, x, q2), what="golden")
-    parity.check(pdf.alphasQ2(cuda(q2)).cpu().numpy(), exp_as, 8 * np.abs(exp_as), what="golden alphas")
+    parity.check(pdf.alphasQ2(cuda(q2)).cpu().numpy(), exp_as, o.alphas_kappa(q2), what="golden alphas")
 
 
 def test_edge_cases(nnpdf):
@@ -401,4 +401,4 @@ def test_more_than_two_to_the_31_outputs(nnpdf):
                           np.arange(na - 200, na)])
     got = a_s[cuda(idx)].cpu().numpy()
     ref = o.alphas_batch(q2[idx % base])
-    parity.check(got, ref, 8 * np.abs(ref), what="alpha_s beyond 2^31 points")
+    parity.check(got, ref, o.alphas_kappa(q2[idx % base]), what="alpha_s beyond 2^31 points")

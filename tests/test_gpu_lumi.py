@@ -50,6 +50,12 @@ def _lum_kappa(g, o, ev, n, member=0):
     return np.sum(k1 * f2[:, anti] + f1 * k2[:, anti] + k1 * k2[:, anti], axis=1)
 
 
+def _as_kappa(o, ev, n):
+    """Term scale of alpha_s at each event's scale (kappa of alpha_s at
+    Q^2 = e^w; one rounding of the exponential moves only the scale)."""
+    return o.alphas_kappa(np.exp(_event_logs(ev, n)[2]))
+
+
 def test_luminosity_parity(lhc):
     from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity
     g, pdf, o = lhc
@@ -60,7 +66,7 @@ def test_luminosity_parity(lhc):
     Lr, lumr, asr = o.lumi(ev)
     kap = _lum_kappa(g, o, ev, n)
     parity.check(lum.cpu().numpy(), lumr, kap, what="lum")
-    parity.check(a_s.cpu().numpy(), asr, 8 * np.abs(asr), what="lumi alpha_s")
+    parity.check(a_s.cpu().numpy(), asr, _as_kappa(o, ev, n), what="lumi alpha_s")
     assert abs(L.item() - Lr) <= 1e-12 * kap.sum() / n
     assert np.sum(ev.flags != 0) > 0.03 * n          # the tail is there
 
@@ -72,7 +78,7 @@ def test_luminosity_tail_only(lhc):
     L, lum, a_s = luminosity(pdf, DeviceEvents.from_host(ev))
     Lr, lumr, asr = o.lumi(ev)
     parity.check(lum.cpu().numpy(), lumr, _lum_kappa(g, o, ev, 4000), what="tail lum")
-    parity.check(a_s.cpu().numpy(), asr, 8 * np.abs(asr), what="tail alpha_s")
+    parity.check(a_s.cpu().numpy(), asr, _as_kappa(o, ev, 4000), what="tail alpha_s")
 
 
 def test_luminosity_gradient_against_oracle(lhc):
@@ -163,7 +169,7 @@ def test_full_size_luminosity_sampled(lhc):
     sub = synth.Events(ev.ln_tau[idx], ev.y[idx], ev.flags[idx], ev.ln_mu2[idx], ev.ln_x1[idx], ev.ln_s)
     Lr, lumr, asr = o.lumi(sub)
     parity.check(lum_h[idx], lumr, _lum_kappa(g, o, sub, idx.size), what="full lum")
-    parity.check(a_s[cuda(idx)].cpu().numpy(), asr, 8 * np.abs(asr), what="full alpha_s")
+    parity.check(a_s[cuda(idx)].cpu().numpy(), asr, _as_kappa(o, sub, idx.size), what="full alpha_s")
     del lum, a_s
     gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
     luminosity_backward(pdf, dev, 1.0, gv)
