@@ -160,8 +160,13 @@ def test_autograd_matches_oracle_gradient(diffgrid):
     got = vals.grad[0].cpu().numpy()
     _check(got, ref, o.dgrid_pw(pid, x, q2, w, absval=True), "autograd grid")
     rdx, rdq = o.grad_pw(pid, x, q2)
-    assert np.allclose(X.grad.cpu().numpy(), w * rdx, rtol=1e-9, atol=1e-9 * np.max(np.abs(w * rdx)))
-    assert np.allclose(Q.grad.cpu().numpy(), w * rdq, rtol=1e-9, atol=1e-9 * np.max(np.abs(w * rdq)))
+    # per-element term scale of the two derivatives, as in the direct adjoint
+    # test above: kappa over the smallest knot spacing, through the chain rule
+    kap = o.kappa(pid, x, q2, pointwise=True)
+    sx = 4 * kap / (np.min(np.diff(np.log(g.x_knots))) * x)
+    sq = 4 * kap / (np.min(np.diff(np.log(g.q_knots ** 2))) * q2)
+    _check(X.grad.cpu().numpy(), w * rdx, np.abs(w) * sx, "autograd dL/dx")
+    _check(Q.grad.cpu().numpy(), w * rdq, np.abs(w) * sq, "autograd dL/dQ2")
 
 
 def test_full_size_sum_rules(diffgrid):
