@@ -338,6 +338,10 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
             release_batch(b);
             return fail(PDF_E_ARG, "bad request " + std::to_string(i));
         }
+        if (D.grid->device != b->device) {
+            release_batch(b);
+            return fail(PDF_E_ARG, "request " + std::to_string(i) + ": grid lives on another device");
+        }
         int gi = -1;
         for (size_t k = 0; k < b->grid_handles.size(); ++k)
             if (b->grid_handles[k] == D.grid) gi = (int)k;
@@ -460,7 +464,12 @@ extern "C" int pdf_batch_run(pdfgpu_batch_t b, pdfgpu_stream_t stream)
     PDF_TRACE("pdf_batch_run");
     clear_error();
     if (!b || !b->exec) return fail(PDF_E_ARG, "batch not prepared");
-    PDF_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    int dev = 0;
+    PDF_CUDA(cudaGetDevice(&dev));
+    if (dev != b->device) PDF_CUDA(cudaSetDevice(b->device));
+    cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (dev != b->device) cudaSetDevice(dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch of the batched launch");
     return PDF_OK;
 }
 
@@ -484,6 +493,9 @@ extern "C" int pdf_batch_info(pdfgpu_batch_t b, int32_t *block, int32_t *qpt, in
 // (256 threads, 2 points per thread), whose scratch -- the tile ticket and
 // the request and grid tables -- lives in one file-scope device array instead
 // of memory allocated per batch.  Nothing here calls cudaMalloc or cudaFree.
+// The tables reach the array by value, as the parameters of small copy
+// kernels launched on the caller's stream ahead of the evaluation, so no
+// host buffer of the library holds a call's tables once the call returns.
 
 namespace {
 
@@ -497,10 +509,47 @@ struct NoAllocScratch {
     BatchReq reqs[kNoAllocMaxRequests];
 };
 
+// Kernel parameters of the copy kernels (each well inside the 32 KB that a
+// launch may carry).
+constexpr int kFillReqs = 384;
+struct NoAllocHead {
+    int ngrids;
+    GridDev grids[kNoAllocMaxGrids];
+};
+struct NoAllocReqs {
+    int first, count;
+    BatchReq reqs[kFillReqs];
+};
+static_assert(sizeof(NoAllocHead) <= 30000 && sizeof(NoAllocReqs) <= 30000, "kernel parameters too large");
+static_assert(sizeof(GridDev) % 8 == 0 && sizeof(BatchReq) % 8 == 0, "tables copied as 8-byte words");
+
+// Resets the ticket and writes the grid table.
+__global__ void k_noalloc_head(const __grid_constant__ NoAllocHead h, NoAllocScratch *S)
+{
+    if (threadIdx.x == 0) S->ticket = 0ull;
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(h.grids);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(S->grids);
+    const int words = h.ngrids * (int)(sizeof(GridDev) / 8);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+// Writes requests [first, first + count) of the request table.
+__global__ void k_noalloc_reqs(const __grid_constant__ NoAllocReqs c, NoAllocScratch *S)
+{
+    const unsigned long long *src = reinterpret_cast<const unsigned long long *>(c.reqs);
+    unsigned long long *dst = reinterpret_cast<unsigned long long *>(S->reqs + c.first);
+    const int words = c.count * (int)(sizeof(BatchReq) / 8);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
 constexpr int kNoAllocDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_dev_addr[kNoAllocDevices];   // device address of the array, per device
-NoAllocScratch g_noalloc_host;               // host staging, static (no heap use)
+// Host-side parameter blocks, static (no heap use, no large stack frame);
+// a launch copies its parameters when it is issued, so they are refilled
+// freely by the next launch.
+NoAllocHead g_noalloc_head;
+NoAllocReqs g_noalloc_reqs;
 
 }  // namespace
 
@@ -520,14 +569,14 @@ extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_d
     PDF_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocDevices) return fail(PDF_E_RANGE, "device ordinal above 63");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    NoAllocScratch &H = g_noalloc_host;
+    NoAllocHead &H = g_noalloc_head;
     int ngrids = 0;
     bool cont = false;                  // some grid uses the continuation extrapolation
     pdfgpu_grid_t handles[kNoAllocMaxGrids];
     int out_stride = 1;
     const int block = 256, qpt = 2;
     const int64_t tile = (int64_t)block * qpt;
-    int64_t ntiles = 0;
+    // first pass: validate every request and build the grid table
     for (int i = 0; i < n_desc; ++i) {
         const pdfgpu_batch_desc &D = descs[i];
         int rc = check_grid(D.grid, true);
@@ -550,20 +599,9 @@ extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_d
         Cols cols;
         rc = resolve_cols(D.grid, D.pids, D.n_pid, &cols);
         if (rc) return rc;
-        BatchReq &r = H.reqs[i];
-        r.grid = gi;
-        r.member = D.member;
-        r.npid = D.n_pid;
-        for (int a = 0; a < kMaxReqPids; ++a) r.cols[a] = a < D.n_pid ? cols.c[a] : -1;
-        r.x = D.x;
-        r.q2 = D.q2;
-        r.out = D.out;
-        r.n = D.n;
-        r.tile0 = ntiles;
-        ntiles += (D.n + tile - 1) / tile;
         out_stride = std::max(out_stride, (int)D.n_pid);
     }
-    H.ticket = 0;                      // the array keeps the previous call's ticket
+    H.ngrids = ngrids;
     if (!g_noalloc_dev_addr[dev]) {
         // once per device, with that device current
         void *p = nullptr;
@@ -573,11 +611,38 @@ extern "C" int pdf_batch_run_noalloc(const pdfgpu_batch_desc *descs, int32_t n_d
     }
     NoAllocScratch *S = reinterpret_cast<NoAllocScratch *>(g_noalloc_dev_addr[dev]);
     cudaStream_t st = (cudaStream_t)stream;
-    // header + grid table + the used part of the request table; a copy from
-    // pageable memory returns once the source has been staged, so the static
-    // host buffer may be refilled by the next call
-    size_t bytes = offsetof(NoAllocScratch, reqs) + (size_t)n_desc * sizeof(BatchReq);
-    PDF_CUDA(cudaMemcpyAsync(S, &H, bytes, cudaMemcpyHostToDevice, st));
+    k_noalloc_head<<<1, 256, 0, st>>>(H, S);
+    PDF_CUDA(cudaGetLastError());
+    // second pass: the request table, in chunks that fit a launch's parameters
+    int64_t ntiles = 0;
+    for (int c0 = 0; c0 < n_desc; c0 += kFillReqs) {
+        NoAllocReqs &R = g_noalloc_reqs;
+        R.first = c0;
+        R.count = std::min(kFillReqs, n_desc - c0);
+        for (int j = 0; j < R.count; ++j) {
+            const pdfgpu_batch_desc &D = descs[c0 + j];
+            int gi = 0;
+            for (int k = 0; k < ngrids; ++k)
+                if (handles[k] == D.grid) gi = k;
+            Cols cols;
+            int rc = resolve_cols(D.grid, D.pids, D.n_pid, &cols);
+            if (rc) return rc;
+            BatchReq &r = R.reqs[j];
+            r = BatchReq{};
+            r.grid = gi;
+            r.member = D.member;
+            r.npid = D.n_pid;
+            for (int a = 0; a < kMaxReqPids; ++a) r.cols[a] = a < D.n_pid ? cols.c[a] : -1;
+            r.x = D.x;
+            r.q2 = D.q2;
+            r.out = D.out;
+            r.n = D.n;
+            r.tile0 = ntiles;
+            ntiles += (D.n + tile - 1) / tile;
+        }
+        k_noalloc_reqs<<<1, 256, 0, st>>>(R, S);
+        PDF_CUDA(cudaGetLastError());
+    }
     if (ntiles == 0) return PDF_OK;
     KernelFn k = kernel_for(Shape{block, qpt, 0}, cont);
     size_t smem = (size_t)block * out_stride * sizeof(double);
