@@ -9,13 +9,24 @@
 // cubics with finite-difference slopes (the interpolant is linear in v, so
 // these weights are exactly its derivative).  Outside the grid the same
 // formulas with the linear basis give the derivatives of the linear
-// continuation.  The grid gradient is accumulated with FP64 atomics, either
-// into a shared-memory copy per CTA (flushed once at the end) when the
-// member's gradient fits, or straight into global memory.  Given the tape of
-// the forward pass over the same points, the adjoint rebuilds each point's
-// cells and local coordinates from it instead of searching the knots and
-// taking the two logarithms again; the arithmetic that follows is the same.
+// continuation.  Given the tape of the forward pass over the same points,
+// the adjoint rebuilds each point's cells and local coordinates from it
+// instead of searching the knots and taking the two logarithms again; the
+// arithmetic that follows is the same.
+//
+// Grid gradient of the pointwise form (one flavour per point): the points
+// are counting-sorted by (cell, flavour) and the gradient is accumulated per
+// bin in the monomial basis of the patch,
+//   G[n][m] = sum over the bin's points of g bq_n bx_m,
+// one FMA per term with no stencil weights, then mapped back to the 16
+// stencil values once per bin run: dL/dv[j][i] = sum_n,m Mq[n][j] G[n][m]
+// Mx[m][i] (the transpose of the map that builds the patch from the
+// values, so the result is the same derivative).  The matrix form (a shared
+// pid list) scatters the 16 stencil weights per flavour with FP64 atomics,
+// into a shared-memory copy per CTA when the member's gradient fits, or
+// straight into global memory.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 
@@ -136,20 +147,353 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
     }
 }
 
+// ------------------------------------------- sorted pointwise grid gradient
+
+constexpr int kMaxSmemBins = 12 * 1024;   // histogram / tile counters in shared memory
+constexpr int kPlaceTile = 32768;         // points per block of the placing pass
+constexpr int kAccWarps = 4;
+constexpr int kSegment = 1024;            // sorted points per warp of the accumulation
+constexpr int64_t kSortChunk = (int64_t)1 << 24;
+
+// Per point (chunk-local index k of point i0 + k): dL/dx and dL/dQ^2 as in
+// k_bwd, the bin key (cell * F + flavour column) and the bin histogram.  The
+// key is -1 for a point that adds nothing (a domain error, outside the grid
+// under the error option, or an absent pid) and for a point outside the
+// knot range on either axis: such a point adds its exact stencil weights of
+// the extrapolation, (1 - t, t) on the edge cell's two knots, to the
+// gradient here with global atomics (rare points; through the monomial
+// basis the two knots that carry no weight would receive rounding-sized
+// terms instead of zeros).  Without a forward tape the point's tape record
+// is written to `tape_out` (chunk-local) for the placing pass.
+template <bool TAPE>
+__global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const int *__restrict__ pid,
+                                                    const double *__restrict__ x,
+                                                    const double *__restrict__ q2, int64_t i0, int m,
+                                                    const double *__restrict__ tape,
+                                                    double *__restrict__ tape_out,
+                                                    const double *__restrict__ gout,
+                                                    double *__restrict__ gx, double *__restrict__ gq,
+                                                    double *__restrict__ gval, int *__restrict__ key,
+                                                    int *__restrict__ hist, int nbins)
+{
+    extern __shared__ int shist[];
+    const bool sh = nbins <= kMaxSmemBins;
+    if (sh) {
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x) shist[k] = 0;
+        __syncthreads();
+    }
+    const size_t cell_stride = (size_t)g.nflav * 16;
+    const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const int64_t i = i0 + k;
+        const double xi = x[i], qi = q2[i];
+        Axis X, Q;
+        bool bad;
+        if (TAPE) {
+            bad = tape_get(g, tape, i, X, Q);
+        } else {
+            bad = !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
+            double u, w;
+            X = axis_x(g, bad ? 0.5 : xi, &u);
+            Q = axis_q2(g, bad ? 10.0 : qi, &w);
+            bad |= out_of_range(g, X, Q);
+            tape_put(tape_out, k, X, Q, bad);
+        }
+        key[k] = -1;
+        if (bad) {
+            if (gx) gx[i] = qnan();
+            if (gq) gq[i] = qnan();
+            continue;
+        }
+        const int col = pid_col(g, pid[i]);
+        if (col < 0) {
+            if (gx) gx[i] = 0.0;
+            if (gq) gq[i] = 0.0;
+            continue;
+        }
+        const double ga = gout[i];
+        if (gx || gq) {
+            double dx2 = X.in ? 2.0 * X.t : 1.0, dx3 = X.in ? 3.0 * X.t * X.t : 1.0;
+            double dq2 = Q.in ? 2.0 * Q.t : 1.0, dq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
+            double dtx, dtq;
+            patch_d(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q, dx2, dx3, dq2, dq3,
+                    &dtx, &dtq);
+            if (!X.in && g.extrap == PDF_EXTRAP_FREEZE) dtx = 0.0;
+            if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dtq = 0.0;
+            if (gx) gx[i] = ga * dtx * g.xcell[X.cell].y * __drcp_rn(xi);
+            if (gq) gq[i] = ga * dtq * g.qcell[Q.cell].y * __drcp_rn(qi);
+        }
+        if (!(X.in && Q.in)) {
+            double Wx[4], Wq[4];
+            stencil_weights(g.mx + (size_t)X.cell * 16, X, Wx);
+            stencil_weights(g.mq + (size_t)Q.cell * 16, Q, Wq);
+            const int qmask = g.qmask[Q.cell], r0 = g.qrow[Q.cell] - 1, k0 = X.cell - 1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!((qmask >> j) & 1)) continue;
+                const double gj = ga * Wq[j];
+                const int row = checked_index(g.status, r0 + j, g.nrows);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int kk = k0 + c;
+                    const double t = gj * Wx[c];
+                    if (kk >= 0 && kk < g.nx && (dbits(t) << 1))
+                        atomicAdd(gval + ((size_t)row * g.nx + kk) * g.nflav + col, t);
+                }
+            }
+            continue;
+        }
+        const int b = checked_index(g.status, (Q.cell * g.nxc + X.cell) * g.nflav + col, nbins);
+        key[k] = b;
+        if (sh) atomicAdd(&shist[b], 1);
+        else atomicAdd(&hist[b], 1);
+    }
+    if (sh) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+            if (shist[k]) atomicAdd(&hist[k], shist[k]);
+    }
+}
+
+// Sorted record of one point (32 bytes): t of the x axis, t of the Q axis
+// (as the tape holds them), g = dL/d(x*f) of the point, and the bits of
+// key (low 32) | x inside (bit 32) | Q inside (bit 33).
+__device__ __forceinline__ void put_rec(double *__restrict__ rec, int pos, const D4 &t, double ga, int b)
+{
+    const unsigned f = (unsigned)dbits(t.w);
+    const uint64_t bits = (uint64_t)(uint32_t)b | ((uint64_t)(f & 1u) << 32) | ((uint64_t)((f >> 2) & 1u) << 33);
+    double2 *d = reinterpret_cast<double2 *>(rec + 4 * (size_t)pos);
+    d[0] = make_double2(t.x, t.y);
+    d[1] = make_double2(ga, dfrom(bits));
+}
+
+// Places the records of a tile of kPlaceTile points in bin order: counts
+// them per bin in shared memory, reserves one range per bin present with a
+// single global atomic, then writes each record into its bin's range (the
+// order inside a bin is free: the accumulation sums it).  nbins <=
+// kMaxSmemBins.  `tape` and `gout` are the chunk's views.
+__global__ void __launch_bounds__(kBlock) k_bwd_place_tiled(const int *__restrict__ key, int m, int nbins,
+                                                            int *__restrict__ cursor,
+                                                            const double *__restrict__ tape,
+                                                            const double *__restrict__ gout,
+                                                            double *__restrict__ rec)
+{
+    extern __shared__ int sc[];
+    const int r0 = blockIdx.x * kPlaceTile, r1 = min(m, r0 + kPlaceTile);
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sc[b] = 0;
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int b = key[r];
+        if (b >= 0) atomicAdd(&sc[b], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+        const int c = sc[b];
+        if (c) sc[b] = atomicAdd(&cursor[b], c);
+    }
+    __syncthreads();
+    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const int b = key[r];
+        if (b >= 0) put_rec(rec, atomicAdd(&sc[b], 1), ld4(tape + 4 * (size_t)r), gout[r], b);
+    }
+}
+
+// The same with one global atomic per record (histograms too large for
+// shared memory).
+__global__ void __launch_bounds__(kBlock) k_bwd_place(const int *__restrict__ key, int m,
+                                                      int *__restrict__ cursor, const double *__restrict__ tape,
+                                                      const double *__restrict__ gout, double *__restrict__ rec)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        const int b = key[r];
+        if (b >= 0) put_rec(rec, atomicAdd(&cursor[b], 1), ld4(tape + 4 * (size_t)r), gout[r], b);
+    }
+}
+
+// Accumulation over the sorted records.  Each warp takes a segment of
+// kSegment records and each half-warp half of it, in steps of 16: lane s of
+// the half stages record p + s (g times the Q basis, and the x basis) in
+// shared memory, then, for each of the 16 staged records in order, lane
+// s = 4 n + m adds g bq_n bx_m to its accumulator G[n][m] of the current
+// bin (one FMA).  When the bin changes the half-warp maps its 16
+// accumulators back to the 16 stencil values, lane (j, i) computing
+// sum_n,m Mq[n][j] G[n][m] Mx[m][i] and adding it to the gradient with one
+// atomic.
+__global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum(GridDev g, const double *__restrict__ rec,
+                                                              const int *__restrict__ offs, int nbins,
+                                                              double *__restrict__ gval)
+{
+    __shared__ double sV[kAccWarps][32][9];      // per staged record: g bq[4], bx[4] (padded)
+    __shared__ int sK[kAccWarps][32];
+    __shared__ double sG[kAccWarps][32];         // accumulators handed over at a flush
+    const int F = g.nflav;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nvalid = offs[nbins];
+    const int64_t wbeg = ((int64_t)blockIdx.x * kAccWarps + wid) * kSegment;
+    if (wbeg >= nvalid) return;
+    const int wend = (int)min((int64_t)nvalid, wbeg + kSegment);
+    const int h = lane >> 4, s = lane & 15, sn = s >> 2, sm = s & 3;
+    const unsigned hmask = 0xFFFFu << (16 * h);
+    const int half = (wend - (int)wbeg + 1) / 2;
+    const int beg = (int)wbeg + h * half;
+    const int end = h ? wend : (int)wbeg + half;
+    const int row0 = h * 16;
+    double acc = 0.0;
+    int cur = -1;
+    auto flush = [&](int b) {
+        sG[wid][row0 + s] = acc;
+        acc = 0.0;
+        __syncwarp(hmask);
+        const int cell = b / F, col = b - cell * F;
+        const int qc = cell / g.nxc, xc = cell - qc * g.nxc;
+        const double *Mq = g.mq + (size_t)qc * 16, *Mx = g.mx + (size_t)xc * 16;
+        // lane (j, i) = (sn, sm)
+        double dv = 0.0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            double hm = 0.0;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) hm = fma(Mq[n * 4 + sn], sG[wid][row0 + n * 4 + m], hm);
+            dv = fma(hm, Mx[m * 4 + sm], dv);
+        }
+        __syncwarp(hmask);
+        const int kk = xc - 1 + sm;
+        if (((g.qmask[qc] >> sn) & 1) && kk >= 0 && kk < g.nx && (dbits(dv) << 1)) {
+            const int row = checked_index(g.status, g.qrow[qc] - 1 + sn, g.nrows);
+            atomicAdd(gval + ((size_t)row * g.nx + kk) * F + col, dv);
+        }
+    };
+    const int steps = (half + 15) / 16;
+    for (int step = 0; step < steps; ++step) {
+        const int p = beg + step * 16;
+        const int r = p + s;
+        int kr = -1;
+        if (r < end) {
+            const D4 t = ld4(rec + 4 * (size_t)r);
+            const uint64_t bits = dbits(t.w);
+            kr = (int)(uint32_t)bits;
+            const bool xin = (bits >> 32) & 1, qin = (bits >> 33) & 1;
+            const double tx2 = t.x * t.x, tq2 = t.y * t.y;
+            const double gq1 = t.z * t.y;
+            double *v = sV[wid][row0 + s];
+            v[0] = t.z;
+            v[1] = gq1;
+            v[2] = qin ? gq1 * t.y : gq1;
+            v[3] = qin ? gq1 * tq2 : gq1;
+            v[4] = 1.0;
+            v[5] = t.x;
+            v[6] = xin ? tx2 : t.x;
+            v[7] = xin ? tx2 * t.x : t.x;
+        }
+        sK[wid][row0 + s] = kr;
+        __syncwarp();
+        const int nb = min(16, end - p);
+        for (int q = 0; q < nb; ++q) {
+            const int kq = sK[wid][row0 + q];
+            if (kq != cur) {
+                if (cur >= 0) flush(cur);
+                cur = kq;
+            }
+            acc = fma(sV[wid][row0 + q][sn], sV[wid][row0 + q][4 + sm], acc);
+        }
+        __syncwarp();
+    }
+    if (cur >= 0) flush(cur);
+}
+
+int backward_sorted(pdfgpu_grid *g, int member, const int *pid, const double *x, const double *q2, int64_t n,
+                    const double *tape, const double *gout, double *gx, double *gq, double *gval,
+                    cudaStream_t st)
+{
+    const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * g->d.nflav;
+    if (nbins64 >= (int64_t)1 << 30) return fail(PDF_E_RANGE, "grid too large for the sorted adjoint");
+    const int nbins = (int)nbins64;
+    // points per round of record, sort and accumulation ($PDFGPU_SORT_CHUNK
+    // overrides the default; the scratch grows with it)
+    int64_t chunk_max = kSortChunk;
+    if (const char *e = getenv("PDFGPU_SORT_CHUNK")) {
+        long long v = atoll(e);
+        if (v > 0) chunk_max = std::min<int64_t>(v, (int64_t)1 << 30);
+    }
+    const int64_t chunk = std::min<int64_t>(n, chunk_max);
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const size_t bkey = al((size_t)chunk * sizeof(int));
+    const size_t brec = al((size_t)chunk * 32);
+    const size_t btape = tape ? 0 : brec;
+    const size_t bbins = al((size_t)(nbins + 1) * sizeof(int));
+    const size_t need = bkey + brec + btape + 3 * bbins;
+    if (g->bwd_scratch_bytes < need) {
+        if (g->bwd_scratch) cudaFree(g->bwd_scratch);
+        g->bwd_scratch = nullptr;
+        g->bwd_scratch_bytes = 0;
+        if (dev_malloc(&g->bwd_scratch, need, "sorted adjoint scratch")) return PDF_E_NOMEM;
+        g->bwd_scratch_bytes = need;
+    }
+    char *base = (char *)g->bwd_scratch;
+    int *key = (int *)base;
+    double *rec = (double *)(base + bkey);
+    double *tape_s = tape ? nullptr : (double *)(base + bkey + brec);
+    int *hist = (int *)(base + bkey + brec + btape);
+    int *offs = (int *)(base + bkey + brec + btape + bbins);
+    int *cursor = (int *)(base + bkey + brec + btape + 2 * bbins);
+    const size_t hsmem = nbins <= kMaxSmemBins ? (size_t)nbins * sizeof(int) : 0;
+    const void *krec = tape ? (const void *)k_bwd_rec<true> : (const void *)k_bwd_rec<false>;
+    int rc = allow_dynamic_smem(krec, hsmem);
+    if (rc) return rc;
+    rc = allow_dynamic_smem((const void *)k_bwd_place_tiled, hsmem);
+    if (rc) return rc;
+    for (int64_t i0 = 0; i0 < n; i0 += chunk) {
+        const int m = (int)std::min(chunk, n - i0);
+        PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
+        const int grid = wave_grid(g, krec, kBlock, hsmem, m);
+        if (tape)
+            k_bwd_rec<true><<<grid, kBlock, hsmem, st>>>(g->d, member, pid, x, q2, i0, m, tape, nullptr, gout, gx,
+                                                          gq, gval, key, hist, nbins);
+        else
+            k_bwd_rec<false><<<grid, kBlock, hsmem, st>>>(g->d, member, pid, x, q2, i0, m, nullptr, tape_s, gout,
+                                                           gx, gq, gval, key, hist, nbins);
+        PDF_CUDA(cudaGetLastError());
+        rc = exclusive_scan(hist, nbins, offs, cursor, st);
+        if (rc) return rc;
+        const double *tv = tape ? tape + 4 * i0 : tape_s;
+        if (hsmem) {
+            const int tiles = (m + kPlaceTile - 1) / kPlaceTile;
+            k_bwd_place_tiled<<<tiles, kBlock, hsmem, st>>>(key, m, nbins, cursor, tv, gout + i0, rec);
+        } else {
+            const int gp = wave_grid(g, (const void *)k_bwd_place, kBlock, 0, m);
+            k_bwd_place<<<gp, kBlock, 0, st>>>(key, m, cursor, tv, gout + i0, rec);
+        }
+        PDF_CUDA(cudaGetLastError());
+        const int64_t warps = (m + kSegment - 1) / kSegment;
+        const int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
+        k_bwd_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, rec, offs, nbins, gval);
+        PDF_CUDA(cudaGetLastError());
+    }
+    return PDF_OK;
+}
+
 template <bool PW, bool TAPE>
 int launch(pdfgpu_grid *g, const Cols &cols, int npid, int member, const int *pid, const double *x,
            const double *q2, int64_t n, const double *tape, const double *gout, double *gx, double *gq,
            double *gval, cudaStream_t s)
 {
+    if constexpr (PW) {
+        if (gval) return backward_sorted(g, member, pid, x, q2, n, tape, gout, gx, gq, gval, s);
+    }
     size_t gbytes = (size_t)g->d.nrows * g->d.nx * g->d.nflav * sizeof(double);
-    if (gval && gbytes <= kSmemGradMax) {
-        const void *kern = (const void *)k_bwd<PW, true, TAPE>;
-        int rc = allow_dynamic_smem(kern, gbytes);
-        if (rc) return rc;
-        int grid = wave_grid(g, kern, kBlock, gbytes, n);
-        k_bwd<PW, true, TAPE><<<grid, kBlock, gbytes, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape, gout,
-                                                            gx, gq, gval);
-    } else {
+    if constexpr (!PW) {
+        if (gval && gbytes <= kSmemGradMax) {
+            const void *kern = (const void *)k_bwd<PW, true, TAPE>;
+            int rc = allow_dynamic_smem(kern, gbytes);
+            if (rc) return rc;
+            int grid = wave_grid(g, kern, kBlock, gbytes, n);
+            k_bwd<PW, true, TAPE><<<grid, kBlock, gbytes, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape,
+                                                                gout, gx, gq, gval);
+            PDF_CUDA(cudaGetLastError());
+            return PDF_OK;
+        }
+    }
+    {
         const void *kern = (const void *)k_bwd<PW, false, TAPE>;
         int grid = wave_grid(g, kern, kBlock, 0, n);
         k_bwd<PW, false, TAPE><<<grid, kBlock, 0, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape, gout, gx,

@@ -264,6 +264,7 @@ static void release_grid(pdfgpu_grid *g)
     for (void *p : g->blocks) cudaFree(p);
     if (g->partials) cudaFree(g->partials);
     if (g->lumi_scratch) cudaFree(g->lumi_scratch);
+    if (g->bwd_scratch) cudaFree(g->bwd_scratch);
     for (int s = 0; s < 3; ++s) {
         for (int k = 0; k < 3; ++k)
             if (g->stage[s][k]) cudaFree(g->stage[s][k]);

@@ -140,7 +140,7 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 //   1. k_lumi_rec: per event the two partons' F values (the partner factors)
 //      and, per parton, its cell key, local coordinates and range flags;
 //      a histogram of the keys;
-//   2. k_scan: bin offsets;  3. k_scatter: parton ids in cell order;
+//   2. exclusive_scan: bin offsets;  3. k_scatter: parton ids in cell order;
 //   4. k_lumi_accum: each half-warp walks half of a warp's run of cell-sorted
 //      partons in batches of 16 (one parton per lane computes its 16 stencil
 //      weights and paired partner factors into shared memory); lane s of a
@@ -221,37 +221,6 @@ __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
         for (int k = threadIdx.x; k < nbins; k += blockDim.x)
             if (shist[k]) atomicAdd(&hist[k], shist[k]);
     }
-}
-
-// Exclusive scan of hist[0..nbins) into offs and cursor; offs[nbins] = total.
-__global__ void k_scan(const int *__restrict__ hist, int nbins, int *__restrict__ offs,
-                       int *__restrict__ cursor)
-{
-    __shared__ int part[1024];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < nbins; base += blockDim.x) {
-        int k = base + threadIdx.x;
-        int v = k < nbins ? hist[k] : 0;
-        part[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-            int t = (int)threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-            __syncthreads();
-            part[threadIdx.x] += t;
-            __syncthreads();
-        }
-        int excl = carry + part[threadIdx.x] - v;
-        if (k < nbins) {
-            offs[k] = excl;
-            cursor[k] = excl;
-        }
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) offs[nbins] = carry;
 }
 
 __global__ void k_scatter(const int *__restrict__ key, int nrec, int *__restrict__ cursor,
@@ -530,8 +499,8 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
             k_lumi_rec<true><<<grid, kBlock, hsmem, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
                                                           e0, m, key, tx, tq, fin, P, hist, nbins);
         PDF_CUDA(cudaGetLastError());
-        k_scan<<<1, 1024, 0, st>>>(hist, nbins, offs, cursor);
-        PDF_CUDA(cudaGetLastError());
+        rc = exclusive_scan(hist, nbins, offs, cursor, st);
+        if (rc) return rc;
         if (hsmem) {
             const int tiles = (int)((2 * (int64_t)m + kScatterTile - 1) / kScatterTile);
             k_scatter_tiled<<<tiles, kBlock, hsmem, st>>>(key, 2 * m, nbins, cursor, perm);

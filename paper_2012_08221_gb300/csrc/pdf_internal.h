@@ -27,6 +27,9 @@ struct pdfgpu_grid {
     // scratch of the luminosity adjoint (event records, cell-sorted order)
     void *lumi_scratch = nullptr;
     size_t lumi_scratch_bytes = 0;
+    // scratch of the sorted pointwise grid gradient (keys, records, bins)
+    void *bwd_scratch = nullptr;
+    size_t bwd_scratch_bytes = 0;
     // staging for the host-buffer entry point
     std::mutex host_mu;
     cudaStream_t hs[3] = {nullptr, nullptr, nullptr};
@@ -84,6 +87,11 @@ struct Cols {
     signed char c[PDF_MAX_PIDS];
 };
 int resolve_cols(const pdfgpu_grid *g, const int32_t *pids, int32_t n_pid, Cols *cols);
+
+// Exclusive scan of a bin histogram (one block on `s`): offs[k] = cursor[k] =
+// sum of hist[0..k), offs[nbins] = the total.  offs and cursor hold nbins + 1
+// and nbins ints.
+int exclusive_scan(const int *hist, int nbins, int *offs, int *cursor, cudaStream_t s);
 
 // Shared argument checks.
 int check_grid(const pdfgpu_grid *g, bool need_values);
