@@ -23,13 +23,16 @@ __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000
 // output is [n][npid] row-major): one bulk copy issued by lane 0 when the run
 // is 16-byte aligned and a multiple of 16 bytes long, else coalesced stores
 // by the whole warp.  Only warp-level synchronisation, no block barriers in
-// the loop.  With TAPE each point's adjoint tape record is written as well.
-template <bool Q_IS_Q, bool CONT, bool TAPE>
+// the loop.  With TAPE each point's adjoint tape record is written as well;
+// with AS alpha_s at the point's Q^2 goes to as_out[i], from the same Q
+// search and logarithm as the PDFs (a point whose x alone is out of the
+// domain still gets its alpha_s, as alphasQ2 would give it).
+template <bool Q_IS_Q, bool CONT, bool TAPE, bool AS = false>
 __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid, int member,
                                                   const double *__restrict__ x,
                                                   const double *__restrict__ q,
                                                   int64_t n, double *__restrict__ out,
-                                                  double *__restrict__ tape)
+                                                  double *__restrict__ tape, double *__restrict__ as_out = nullptr)
 {
     extern __shared__ __align__(16) double sout[];
     __shared__ signed char scol[PDF_MAX_PIDS];
@@ -49,11 +52,12 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         double xi = live ? x[i] : 0.5;
         double qi = live ? q[i] : 10.0;
         if (Q_IS_Q) qi = qi * qi;
-        bool bad = live && !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
+        const bool qbad = !q2_ok(dbits(qi));
+        bool bad = live && !(x_ok(dbits(xi)) && !qbad);
         flag_status(g, bad);
         if (bad) {
             xi = 0.5;
-            qi = 10.0;
+            if (!AS || qbad) qi = 10.0;
         }
         double u, w;
         Axis X = axis_x(g, xi, &u);
@@ -62,6 +66,10 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2(GridDev g, Cols cols, int npid
         flag_status(g, oor, PDF_S_RANGE);
         bad |= oor;
         if (TAPE && live) tape_put(tape, i, X, Q, bad);
+        if (AS && live) {
+            const double a = alphas_any(g, ld4(g.acoef + (size_t)Q.cell * 4), Q);
+            as_out[i] = (qbad || (g.extrap == PDF_EXTRAP_ERROR && !Q.in)) ? qnan() : a;
+        }
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
         double *srow = wbuf + lane * npid;
         warp_run_reuse(lane);                 // the previous run has left the slice
@@ -248,10 +256,12 @@ int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n
     if (rc) return rc;
     if (n == 0) return PDF_OK;
     if (!x || !q || !out) return fail(PDF_E_ARG, "null array");
-    using Kern = void (*)(GridDev, Cols, int, int, const double *, const double *, int64_t, double *, double *);
+    using PairKern = void (*)(GridDev, Cols, int, int, const double *, const double *, int64_t, double *, double *);
+    using Kern = void (*)(GridDev, Cols, int, int, const double *, const double *, int64_t, double *, double *,
+                          double *);
     const bool cont = g->d.extrap == PDF_EXTRAP_CONTINUATION;
     if (n * n_pid <= kPairMax) {
-        Kern k = tape ? k_xfxq2_pairs<false, false, true>
+        PairKern k = tape ? k_xfxq2_pairs<false, false, true>
                  : q_is_q ? (cont ? k_xfxq2_pairs<true, true, false> : k_xfxq2_pairs<true, false, false>)
                           : (cont ? k_xfxq2_pairs<false, true, false> : k_xfxq2_pairs<false, false, false>);
         int grid = wave_grid(g, (const void *)k, kBlock, 0, n * n_pid);
@@ -279,7 +289,42 @@ int launch_matrix(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n
         }
     }
     int grid = wave_grid(g, (const void *)k, block, smem, n);
-    k<<<grid, block, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out, tape);
+    k<<<grid, block, smem, s>>>(g->d, cols, n_pid, member, x, q, n, out, tape, nullptr);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
+// x*f and alpha_s at the same points in one launch of the per-point kernel.
+int launch_xf_alphas(pdfgpu_grid *g, int32_t member, const int32_t *pids, int32_t n_pid, const double *x,
+                     const double *q2, int64_t n, double *out, double *alphas, cudaStream_t s)
+{
+    clear_error();
+    int rc = check_grid(g, true);
+    if (rc) return rc;
+    if (!g->has_alphas) return fail(PDF_E_DESC, "grid has no alpha_s values");
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
+    Cols cols;
+    rc = resolve_cols(g, pids, n_pid, &cols);
+    if (rc) return rc;
+    if (n == 0) return PDF_OK;
+    if (!x || !q2 || !out || !alphas) return fail(PDF_E_ARG, "null array");
+    const bool cont = g->d.extrap == PDF_EXTRAP_CONTINUATION;
+    auto k = cont ? k_xfxq2<false, true, false, true> : k_xfxq2<false, false, false, true>;
+    size_t smem = (size_t)kBlock * n_pid * sizeof(double);
+    rc = allow_dynamic_smem((const void *)k, smem);
+    if (rc) return rc;
+    int block = kBlock;
+    for (int b : {32, 64, 128}) {
+        const size_t sb = (size_t)b * n_pid * sizeof(double);
+        if ((n + b - 1) / b <= (int64_t)g->sm_count * occupancy((const void *)k, b, sb)) {
+            block = b;
+            smem = sb;
+            break;
+        }
+    }
+    int grid = wave_grid(g, (const void *)k, block, smem, n);
+    k<<<grid, block, smem, s>>>(g->d, cols, n_pid, member, x, q2, n, out, nullptr, alphas);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
@@ -324,6 +369,14 @@ int launch_pw(pdfgpu_grid *g, int32_t member, const int32_t *pid, const double *
 }
 
 }  // namespace
+
+extern "C" int xfxQ2_alphasQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                              const double *x, const double *q2, int64_t n, double *out, double *alphas,
+                              pdfgpu_stream_t stream)
+{
+    PDF_TRACE("xfxQ2_alphasQ2");
+    return launch_xf_alphas(g, member, pids, n_pid, x, q2, n, out, alphas, (cudaStream_t)stream);
+}
 
 extern "C" int xfxQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                      const double *x, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)

@@ -137,6 +137,22 @@ class PDF:
     def xfxQ(self, pids, x, q, member=0, out=None):
         return self._matrix("xfxQ", pids, x, q, member, out)
 
+    def xfxQ2_alphasQ2(self, pids, x, q2, member=0, out=None, alphas=None):
+        """x*f for every pid in ``pids`` and alpha_s at the same points, in
+        one launch that shares the Q^2 search: ``([n][len(pids)], [n])``."""
+        arr, pp = _pids_host(pids)
+        x = _f64_cuda(x, self.device)
+        q2 = _f64_cuda(q2, self.device)
+        n = x.numel()
+        assert q2.numel() == n, "x and Q^2 arrays differ in length"
+        if out is None:
+            out = torch.empty((n, arr.size), dtype=torch.float64, device=self.device)
+        if alphas is None:
+            alphas = torch.empty(n, dtype=torch.float64, device=self.device)
+        check("xfxQ2_alphasQ2", lib().xfxQ2_alphasQ2(self.handle, int(member), pp, arr.size, _ptr(x), _ptr(q2), n,
+                                                     _ptr(out), _ptr(alphas), _stream(self.device)))
+        return out, alphas
+
     py_xfxQ2 = xfxQ2
     py_xfxQ = xfxQ
 

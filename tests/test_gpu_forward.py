@@ -402,3 +402,27 @@ def test_more_than_two_to_the_31_outputs(nnpdf):
     got = a_s[cuda(idx)].cpu().numpy()
     ref = o.alphas_batch(q2[idx % base])
     parity.check(got, ref, o.alphas_kappa(q2[idx % base]), what="alpha_s beyond 2^31 points")
+
+
+def test_xf_and_alphas_in_one_launch(nnpdf):
+    """xfxQ2_alphasQ2 gives what xfxQ2 and alphasQ2 give on the same arrays,
+    bit for bit, and matches the oracle: a ragged 3e5-point query with domain
+    errors on x alone (alpha_s stays valid), on Q^2, NaN, and points outside
+    the grid; also on a grid with the error option and on a short query."""
+    from paper_2012_08221_gb300.pdf import PDF
+    g, pdf, o = nnpdf
+    x, q2, _ = synth.queries_nnpdf(300_001, seed=61)
+    x[:6] = [-1.0, 0.3, np.nan, 2.0, 1e-12, 0.01]
+    q2[:6] = [50.0, -4.0, 10.0, 1e3, 1e14, 0.2]
+    for p, n in ((pdf, x.size), (PDF.from_grid(g, extrap="error"), x.size), (pdf, 777)):
+        X, Q = cuda(x[:n]), cuda(q2[:n])
+        out, a_s = p.xfxQ2_alphasQ2(g.pids, X, Q)
+        # bit for bit, NaNs included (compared as 64-bit integers)
+        assert torch.equal(out.view(torch.int64), p.xfxQ2(g.pids, X, Q).view(torch.int64))
+        assert torch.equal(a_s.view(torch.int64), p.alphasQ2(Q).view(torch.int64))
+    out, a_s = pdf.xfxQ2_alphasQ2(g.pids, cuda(x), cuda(q2))
+    assert pdf.status() == 1
+    parity.check(out.cpu().numpy(), o.xfxq2_batch(g.pids, x, q2), o.kappa(g.pids, x, q2), what="combined x*f")
+    ra = o.alphas_batch(q2)
+    assert not np.isnan(ra[0]) and np.isnan(ra[1])
+    parity.check(a_s.cpu().numpy(), ra, o.alphas_kappa(q2), what="combined alpha_s")
