@@ -144,15 +144,24 @@ typedef struct {
 int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out);
 
 /* (Re)build the per-cell bicubic coefficients of ALL members from a DEVICE
- * array `dev_values` laid out as the description's `values`.  Used when the
- * values live in a device tensor that changes (a fit).  The array is read on
- * `stream` during the call and not kept.  Asynchronous on `stream`. */
+ * array `dev_values` laid out as the description's `values` (beyond the
+ * paper: the differentiation form, where the knot values are the
+ * parameters a PDF fit moves -- PDFFlow Sec. 1 names the fitting
+ * collaborations that produce the grids -- and live in a device tensor).
+ * The array is read on `stream` during the call and not kept.  Asynchronous
+ * on `stream`.  The coefficients are ONE table per grid handle: a call
+ * replaces them for every later call on the handle, on any stream, so two
+ * rebinds of one handle with different values from two streams (for example
+ * two differentiable evaluations, each of which rebinds) race; use one
+ * handle per stream, or order the streams. */
 int pdf_bind_values(pdfgpu_grid_t g, const double *dev_values, pdfgpu_stream_t stream);
 
-/* Free every device allocation of the grid.  Synchronises the device. */
+/* Free every device allocation of the grid (the end of the life of the PDF
+ * object of PDFFlow Sec. 2.1 `mkPDF`).  Synchronises the device. */
 int pdf_free_grid(pdfgpu_grid_t g);
 
-/* Sizes of a loaded grid (any pointer may be NULL). */
+/* Sizes of a loaded grid, as in the grid description of PDFFlow Sec. 4 (any
+ * pointer may be NULL). */
 int pdf_grid_info(pdfgpu_grid_t g, int32_t *n_x, int32_t *n_rows, int32_t *n_flav,
                   int32_t *n_members, int32_t *has_alphas);
 
@@ -169,10 +178,24 @@ int xfxQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
 int xfxQ(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
          const double *x, const double *q, int64_t n, double *out, pdfgpu_stream_t stream);
 
-/* Pointwise form: one pid per point.
+/* Pointwise form: one pid per point (beyond the paper's shared flavour set
+ * of Sec. 2.1; it serves the differentiation workload, where every point
+ * asks for one flavour, and a Monte Carlo integrand that needs one flavour
+ * per phase-space point, Sec. 3.1).
  *   pid DEVICE [n], x, q2 DEVICE [n], out DEVICE [n]                         */
 int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
              const double *q2, int64_t n, double *out, pdfgpu_stream_t stream);
+
+/* x*f and alpha_s at the same points in one launch (PDFFlow Sec. 2.1 `xfxQ2`
+ * and `py_alphasQ`; Sec. 3.1-3.2: an integrand asks for both at the
+ * factorisation scale of each phase-space point).  The Q^2 search and
+ * logarithm are shared.  Arguments as for xfxQ2, plus alphas DEVICE [n]:
+ * alpha_s(q2[i]).  The outputs equal those of xfxQ2 and alphasQ2 on the same
+ * arrays bit for bit (alpha_s stays valid where only x is out of the domain).
+ * PDF_E_DESC if the grid has no alpha_s values. */
+int xfxQ2_alphasQ2(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
+                   const double *x, const double *q2, int64_t n, double *out, double *alphas,
+                   pdfgpu_stream_t stream);
 
 /* alpha_s(Q^2) (PDFFlow Sec. 2.1, `py_alphasQ`).  q2, out DEVICE [n].
  * PDF_E_DESC if the grid was loaded without alpha_s values. */
@@ -181,11 +204,14 @@ int alphasQ(pdfgpu_grid_t g, const double *q, int64_t n, double *out, pdfgpu_str
 
 /* alpha_s(Q^2) and its derivative d alpha_s / d Q^2 (the derivative of the
  * same piecewise cubic in ln Q^2, divided by Q^2; zero across a frozen edge).
+ * Beyond the paper: the differentiation form applied to the alpha_s
+ * interpolation of Sec. 2.1.
  * q2, dq2 DEVICE [n]; out DEVICE [n] or NULL. */
 int alphasQ2_grad(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, double *dq2,
                   pdfgpu_stream_t stream);
 
-/* End-to-end form of xfxQ2 for HOST buffers: x, q2 HOST [n], out HOST
+/* End-to-end form of xfxQ2 for HOST buffers (PDFFlow Sec. 2.1: arrays in,
+ * an array out, as a host program holds them): x, q2 HOST [n], out HOST
  * [n][n_pid].  The library streams the points through device staging buffers
  * it owns (chunks of 2^18 points, or $PDFGPU_HOST_CHUNK read at the first
  * call, overlapped on three internal streams), and returns when `out` is
@@ -197,7 +223,10 @@ int alphasQ2_grad(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, dou
 int xfxQ2_host(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                const double *x, const double *q2, int64_t n, double *out);
 
-/* Adjoint of xfxQ2 / xfxQ2_pw (the derivative PDF fits need).
+/* Adjoint of xfxQ2 / xfxQ2_pw.  Beyond the paper: the differentiation form,
+ * d(x*f)/dx, d(x*f)/dQ^2 and d(x*f)/d(knot values) of the interpolant of
+ * Sec. 2.1, the last being what a fit of the grid values needs (Sec. 1:
+ * PDFs come from fits).
  * For L = sum_i sum_p grad_out[i][p] * xf_{pid_p}(x_i, Q^2_i):
  *   pointwise == 0: pids HOST [n_pid] (shared), grad_out DEVICE [n][n_pid]
  *   pointwise != 0: pids DEVICE [n] (one per point, n_pid ignored), grad_out DEVICE [n]
@@ -232,7 +261,7 @@ int xfxQ2_pw_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const dou
                   const double *q2, int64_t n, double *out, double *tape, pdfgpu_stream_t stream);
 
 /* xfxQ2_backward from the tape a forward call wrote for the same grid and the
- * same points (x and q2 are still read, for the chain rule of grad_x and
+ * same points (beyond the paper: the differentiation form, as above) (x and q2 are still read, for the chain rule of grad_x and
  * grad_q2).  Same arguments and results as xfxQ2_backward, bit for bit in
  * grad_x and grad_q2.  A tape of other points or another grid gives wrong
  * numbers; its cells are clamped into the grid's tables, so no access leaves
@@ -267,11 +296,15 @@ typedef struct {
 int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc, int32_t autotune,
                       pdfgpu_stream_t stream, pdfgpu_batch_t *out);
 
-/* Replay the captured launch on `stream`: evaluates every request. */
+/* Replay the captured launch on `stream`: evaluates every request (the
+ * traced graph's execution, PDFFlow Sec. 2.1).  Makes the batch's device
+ * current for the launch; the caller's current device is restored. */
 int pdf_batch_run(pdfgpu_batch_t b, pdfgpu_stream_t stream);
 
 /* Chosen launch shape: threads per block, points per thread, staging flag,
- * persistent CTAs, and the tuned time of one launch (ms). */
+ * persistent CTAs, and the tuned time of one launch (ms); and the release
+ * of a prepared batch.  Beyond the paper: the batching form's autotuner and
+ * its lifetime (PDFFlow's `trace()` of Sec. 2.1 has no such handle). */
 int pdf_batch_info(pdfgpu_batch_t b, int32_t *block, int32_t *qpt, int32_t *stage,
                    int32_t *ctas, float *ms);
 int pdf_batch_free(pdfgpu_batch_t b);
@@ -316,7 +349,8 @@ int pdf_lumi(pdfgpu_grid_t g, int32_t member, const double *ln_tau, const double
              int64_t n, double *lum, double *alphas, double *L, double *save_p,
              pdfgpu_stream_t stream);
 
-/* dL/dvalues of `member` for L of pdf_lumi, times the HOST scalar dL:
+/* dL/dvalues of `member` for L of pdf_lumi, times the HOST scalar dL (beyond
+ * the paper: the differentiation form of the Sec. 3.1-3.2 luminosity):
  * grad_values DEVICE [n_rows][n_x][n_flav], ACCUMULATED (+=) with FP64
  * atomics (summation order not fixed).  saved_p: the save_p array of the
  * forward call on the same events and values (DEVICE, read only), or NULL to
@@ -342,8 +376,12 @@ int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *ln_tau, con
  * with Jacobian n (e_{i+1} - e_i).
  * pdf_vegas_lumi_iteration evaluates one iteration:
  *   edges DEVICE [2][n_bins + 1], v DEVICE [n][2] uniforms in [0, 1),
- *   sums DEVICE [2 + 2 n_bins] (overwritten): sum w, sum w^2, then per bin
- *   the sum of w^2 for dimension 0 and for dimension 1, w = F(r) x Jacobian.
+ *   shift HOST scalar c (finite; PDF_E_ARG otherwise),
+ *   sums DEVICE [2 + 2 n_bins] (overwritten): sum w, sum (w - c)^2, then per
+ *   bin the sum of w^2 for dimension 0 and for dimension 1, w = F(r) x
+ *   Jacobian.  With c near the mean (the previous iteration's estimate) the
+ *   variance (sum (w - c)^2 / n - (mean - c)^2) / (n - 1) is a sum of small
+ *   squares instead of the difference of two nearly equal sums.
  * 2 <= n_bins <= 1024, ln_tau_min < 0.  Uses the grid handle's scratch for
  * block partial sums (calls on one grid must not overlap).  Asynchronous.
  * pdf_vegas_refine moves one dimension's HOST edges [n_bins + 1] from its
@@ -352,7 +390,7 @@ int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *ln_tau, con
  * give every bin an equal share of sum r_i.  Host only. */
 int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double ln_tau_min, double ln_s,
                              int32_t n_bins, const double *edges, const double *v, int64_t n,
-                             double *sums, pdfgpu_stream_t stream);
+                             double shift, double *sums, pdfgpu_stream_t stream);
 int pdf_vegas_refine(const double *bin_w2, int32_t n_bins, double alpha, double *edges);
 
 /* LHAPDF grid files (PDFFlow Sec. 1 and 4 keep the community "lhagrid1"
@@ -377,7 +415,8 @@ int pdf_lhapdf_desc(pdfgpu_lhapdf_t h, pdfgpu_grid_desc *desc);
 int pdf_lhapdf_close(pdfgpu_lhapdf_t h);
 
 /* Read and clear the grid's status word (PDF_S_* bits).  Synchronises
- * `stream` first. */
+ * `stream` first.  Beyond the paper: failure detection for the batched
+ * calls of Sec. 2.1, whose per-element domain errors do not fail a call. */
 int pdf_get_status(pdfgpu_grid_t g, pdfgpu_stream_t stream, uint32_t *bits);
 
 /* General VEGAS (Lepage, J. Comput. Phys. 27 (1978) 192) around an
@@ -395,20 +434,24 @@ int pdf_get_status(pdfgpu_grid_t g, pdfgpu_stream_t stream, uint32_t *bits);
  *   out.
  * pdf_vegas_accumulate: w DEVICE [n] weights, bins DEVICE [n][dim] as from
  *   pdf_vegas_map (entries outside [0, n_bins) are left out of the per-bin
- *   sums), sums DEVICE [2 + dim n_bins] (overwritten): sum w, sum w^2, then
- *   per dimension the per-bin sums of w^2.  Summation order is not fixed.
+ *   sums), shift HOST scalar c (finite), sums DEVICE [2 + dim n_bins]
+ *   (overwritten): sum w, sum (w - c)^2, then per dimension the per-bin sums
+ *   of w^2.  Summation order is not fixed.
  * 1 <= dim <= 16, 2 <= n_bins <= 1024.  Asynchronous on `stream`; no grid
  * handle and no library-owned scratch, so calls on different streams are
  * independent.  The library has no counterpart of the caller's integrand. */
 int pdf_vegas_map(int32_t dim, int32_t n_bins, const double *edges, const double *v, int64_t n, double *r,
                   double *jac, int32_t *bins, pdfgpu_stream_t stream);
 int pdf_vegas_accumulate(int32_t dim, int32_t n_bins, const double *w, const int32_t *bins, int64_t n,
-                         double *sums, pdfgpu_stream_t stream);
+                         double shift, double *sums, pdfgpu_stream_t stream);
 
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread ("" if none).  Beyond the
+ * paper: the error channel of this C interface (the paper's interface is
+ * Python, Sec. 2.1). */
 const char *pdf_last_error(void);
 
-/* Measurement helpers (not part of the interpolation):
+/* Measurement helpers (not part of the interpolation; beyond the paper, the
+ * denominators of this GPU's FP64 roofline):
  * FP64 FMA throughput of this GPU in FLOP/s (2 per FMA), from a kernel of
  * independent fused multiply-add chains timed with CUDA events. Synchronous. */
 int pdf_probe_fp64_peak(double *flops);
@@ -418,11 +461,11 @@ int pdf_probe_fp64_peak(double *flops);
  * in FLOP/s (2 M N K per warp-wide instruction), from a kernel of eight
  * independent accumulator chains per warp timed with CUDA events.
  * shape 0: m8n8k4, 1: m16n8k4, 2: m16n8k8, 3: m16n8k16; PDF_E_ARG otherwise.
- * Measures whether the interpolation's contraction could leave the DFMA pipe
- * (a question of this GPU, not of the paper).  Synchronous. */
+ * Beyond the paper: measures whether the interpolation's contraction could
+ * leave the DFMA pipe of this GPU.  Synchronous. */
 int pdf_probe_fp64_mma_peak(int32_t shape, double *flops);
 
-/* The kernels' natural log (table-driven argument reduction after
+/* (Beyond the paper: a test hook.)  The kernels' natural log (table-driven argument reduction after
  * P. T. P. Tang, ACM TOMS 16 (1990) 378, with a degree-5 series for
  * ln(1+r), |r| <= 2^-11) applied to n DEVICE doubles: out[i] = ln(in[i]) for
  * positive finite in[i].  Exposed for tests. */

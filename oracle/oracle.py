@@ -110,11 +110,11 @@ def _declare(L):
     L.orc_lumi_dgrid.argtypes = [_G, C.c_int, _D, _D, U8, _D, _D, C.c_double,
                                  C.c_int64, _D, C.c_int]
     L.orc_vegas_sums.argtypes = [_G, C.c_int, C.c_double, C.c_double, C.c_int, _D, _D,
-                                 C.c_int64, _D]
+                                 C.c_int64, C.c_double, _D]
     L.orc_vegas_refine.argtypes = [_D, C.c_int, C.c_double, _D]
     L.orc_vegas_map.argtypes = [C.c_int, C.c_int, _D, _D, C.c_int64, _D, _D, C.POINTER(C.c_int)]
     L.orc_vegas_map.restype = None
-    L.orc_vegas_accumulate.argtypes = [C.c_int, C.c_int, _D, C.POINTER(C.c_int), C.c_int64, _D]
+    L.orc_vegas_accumulate.argtypes = [C.c_int, C.c_int, _D, C.POINTER(C.c_int), C.c_int64, C.c_double, _D]
     L.orc_vegas_accumulate.restype = None
 
 
@@ -328,24 +328,26 @@ def vegas_map(edges, v):
     return r, jac, bins
 
 
-def vegas_accumulate(n_bins, w, bins):
-    """[sum w, sum w^2, per-dimension per-bin sums of w^2] of weights w [n]
-    with their bins [n][dim]."""
+def vegas_accumulate(n_bins, w, bins, shift=0.0):
+    """[sum w, sum (w - shift)^2, per-dimension per-bin sums of w^2] of
+    weights w [n] with their bins [n][dim]."""
     w = _f64(w)
     bins = np.ascontiguousarray(bins, dtype=np.int32)
     dim = bins.shape[1]
     out = np.empty(2 + dim * n_bins)
-    lib().orc_vegas_accumulate(dim, n_bins, _d(w), bins.ctypes.data_as(C.POINTER(C.c_int)), w.size, _d(out))
+    lib().orc_vegas_accumulate(dim, n_bins, _d(w), bins.ctypes.data_as(C.POINTER(C.c_int)), w.size,
+                               float(shift), _d(out))
     return out
 
 
-def vegas_sums(grid: "OracleGrid", member, ln_tau_min, ln_s, edges, v):
+def vegas_sums(grid: "OracleGrid", member, ln_tau_min, ln_s, edges, v, shift=0.0):
     """Sums of one VEGAS iteration of the luminosity integral (see the C
-    file): [sum w, sum w^2, per-bin w^2 of dimension 0, of dimension 1]."""
+    file): [sum w, sum (w - shift)^2, per-bin w^2 of dimension 0, of
+    dimension 1]."""
     e = _f64(edges)
     n_bins = e.shape[1] - 1
     v = _f64(v)
     out = np.empty(2 + 2 * n_bins)
     lib().orc_vegas_sums(grid.ptr, member, float(ln_tau_min), float(ln_s), n_bins, _d(e), _d(v),
-                         v.shape[0], _d(out))
+                         v.shape[0], float(shift), _d(out))
     return out

@@ -694,11 +694,15 @@ void orc_lumi_dgrid(const orc_grid *g, int member, const double *ln_tau, const d
  * r = e_i + d (e_{i+1} - e_i), with Jacobian n (e_{i+1} - e_i).
  */
 
-/* Sums of one iteration: out[0] = sum w, out[1] = sum w^2, then for each of
- * the two dimensions the sum of w^2 over the points in each bin, where
- * w = F(r) J(v) is the weight of the point drawn with uniforms v[i][0..1]. */
+/* Sums of one iteration: out[0] = sum w, out[1] = sum (w - shift)^2 (the
+ * sample variance about a shift near the mean, normally the previous
+ * iteration's estimate: sum (w - c)^2 / n - (mean - c)^2 is the variance of w
+ * for any c, and with c near the mean it is a sum of small squares instead of
+ * the difference of two nearly equal numbers), then for each of the two
+ * dimensions the sum of w^2 over the points in each bin, where w = F(r) J(v)
+ * is the weight of the point drawn with uniforms v[i][0..1]. */
 void orc_vegas_sums(const orc_grid *g, int member, double ln_tau_min, double ln_s, int n_bins,
-                    const double *edges, const double *v, int64_t n, double *out)
+                    const double *edges, const double *v, int64_t n, double shift, double *out)
 {
     for (int k = 0; k < 2 + 2 * n_bins; ++k) out[k] = 0.0;
     for (int64_t i = 0; i < n; ++i) {
@@ -728,7 +732,7 @@ void orc_vegas_sums(const orc_grid *g, int member, double ln_tau_min, double ln_
         double f = (-ln_tau_min) * (-ln_tau) * lum;
         double wt = f * jac;
         out[0] += wt;
-        out[1] += wt * wt;
+        out[1] += (wt - shift) * (wt - shift);
         out[2 + bin[0]] += wt * wt;
         out[2 + n_bins + bin[1]] += wt * wt;
     }
@@ -760,15 +764,16 @@ void orc_vegas_map(int dim, int n_bins, const double *edges, const double *v, in
 }
 
 /* Sums of one iteration from the weights w_i = f(r_i) J_i: out[0] = sum w,
- * out[1] = sum w^2, then for each dimension d the per-bin sums of w^2,
- * out[2 + d n + b].  Serial, in point order. */
-void orc_vegas_accumulate(int dim, int n_bins, const double *w, const int *bins, int64_t n_pts, double *out)
+ * out[1] = sum (w - shift)^2, then for each dimension d the per-bin sums of
+ * w^2, out[2 + d n + b].  Serial, in point order. */
+void orc_vegas_accumulate(int dim, int n_bins, const double *w, const int *bins, int64_t n_pts, double shift,
+                          double *out)
 {
     for (int k = 0; k < 2 + dim * n_bins; ++k) out[k] = 0.0;
     for (int64_t i = 0; i < n_pts; ++i) {
         double wi = w[i];
         out[0] += wi;
-        out[1] += wi * wi;
+        out[1] += (wi - shift) * (wi - shift);
         for (int d = 0; d < dim; ++d) out[2 + d * n_bins + bins[i * dim + d]] += wi * wi;
     }
 }

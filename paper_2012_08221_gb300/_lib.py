@@ -54,6 +54,7 @@ SIGNATURES = {
     "xfxQ2": [c_grid, C.c_int32, _I, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP],
     "xfxQ": [c_grid, C.c_int32, _I, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP],
     "xfxQ2_pw": [c_grid, C.c_int32, _VP, _VP, _VP, C.c_int64, _VP, _VP],
+    "xfxQ2_alphasQ2": [c_grid, C.c_int32, _I, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP, _VP],
     "xfxQ2_tape": [c_grid, C.c_int32, _I, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP, _VP],
     "xfxQ2_pw_tape": [c_grid, C.c_int32, _VP, _VP, _VP, C.c_int64, _VP, _VP, _VP],
     "alphasQ2": [c_grid, _VP, C.c_int64, _VP, _VP],
@@ -75,10 +76,10 @@ SIGNATURES = {
                           C.c_double, _VP, _VP, _VP],
     "pdf_get_status": [c_grid, _VP, C.POINTER(C.c_uint32)],
     "pdf_vegas_lumi_iteration": [c_grid, C.c_int32, C.c_double, C.c_double, C.c_int32, _VP, _VP,
-                                 C.c_int64, _VP, _VP],
+                                 C.c_int64, C.c_double, _VP, _VP],
     "pdf_vegas_refine": [_D, C.c_int32, C.c_double, _D],
     "pdf_vegas_map": [C.c_int32, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP, _VP, _VP],
-    "pdf_vegas_accumulate": [C.c_int32, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP],
+    "pdf_vegas_accumulate": [C.c_int32, C.c_int32, _VP, _VP, C.c_int64, C.c_double, _VP, _VP],
     "pdf_lhapdf_open": [C.c_char_p, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)],
     "pdf_lhapdf_desc": [C.c_void_p, C.POINTER(GridDesc)],
     "pdf_lhapdf_close": [C.c_void_p],

@@ -10,9 +10,11 @@
 // per dimension n_bins bins with edges e_0 = 0 < ... < e_n = 1; a uniform v
 // lands in bin i = floor(v n) at fraction d = v n - i and is mapped to
 // r = e_i + d (e_{i+1} - e_i) with Jacobian n (e_{i+1} - e_i).  One kernel
-// launch evaluates an iteration's points and accumulates sum w, sum w^2 and
-// the per-bin sums of w^2 that drive the next grid; the refinement itself is
-// a few hundred flops on the host.
+// launch evaluates an iteration's points and accumulates sum w, the sum of
+// (w - c)^2 about a shift c the caller passes (the previous iteration's
+// estimate, so that the variance is a sum of small squares rather than the
+// difference of two large sums) and the per-bin sums of w^2 that drive the
+// next grid; the refinement itself is a few hundred flops on the host.
 #include <math.h>
 
 #include <algorithm>
@@ -30,7 +32,7 @@ constexpr int kMaxBins = 1024;
 template <bool CONT>
 __global__ void __launch_bounds__(kBlock) k_vegas(GridDev g, Cols anti, int member, double ln_tau_min,
                                                   double ln_s, int n_bins, const double *__restrict__ edges,
-                                                  const double *__restrict__ v, int64_t n,
+                                                  const double *__restrict__ v, int64_t n, double shift,
                                                   double *__restrict__ partials, double *__restrict__ bins)
 {
     extern __shared__ double sbin[];          // [2][n_bins] sums of w^2
@@ -76,8 +78,9 @@ __global__ void __launch_bounds__(kBlock) k_vegas(GridDev g, Cols anti, int memb
             lum = fma(patch_any<CONT>(g, c1 + a * 16, X1, Q), patch_any<CONT>(g, c2 + b * 16, X2, Q), lum);
         }
         const double w = (-ln_tau_min) * (-ln_tau) * lum * jac;
+        const double dw = w - shift;
         s1 += w;
-        s2 = fma(w, w, s2);
+        s2 = fma(dw, dw, s2);
         atomicAdd(&sbin[bin[0]], w * w);
         atomicAdd(&sbin[n_bins + bin[1]], w * w);
     }
@@ -155,11 +158,11 @@ __global__ void __launch_bounds__(kBlock) k_vegas_map(int dim, int n_bins, const
 }
 
 // Sums of one iteration from the caller's weights: per block, sum w and
-// sum w^2 by shuffles and the per-bin sums of w^2 in shared memory, then
-// one atomic per nonzero block total.
+// sum (w - shift)^2 by shuffles and the per-bin sums of w^2 in shared
+// memory, then one atomic per nonzero block total.
 __global__ void __launch_bounds__(kBlock) k_vegas_accumulate(int dim, int n_bins, const double *__restrict__ w,
                                                              const int *__restrict__ bins, int64_t n,
-                                                             double *__restrict__ sums)
+                                                             double shift, double *__restrict__ sums)
 {
     extern __shared__ double sb[];           // [dim][n_bins]
     __shared__ double red[2][kBlock / 32];
@@ -169,9 +172,9 @@ __global__ void __launch_bounds__(kBlock) k_vegas_accumulate(int dim, int n_bins
     double s1 = 0.0, s2 = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double wi = w[i], w2 = wi * wi;
+        const double wi = w[i], w2 = wi * wi, dw = wi - shift;
         s1 += wi;
-        s2 += w2;
+        s2 = fma(dw, dw, s2);
         for (int d = 0; d < dim; ++d) {
             int b = bins[i * dim + d];
             if (b >= 0 && b < n_bins) atomicAdd(&sb[d * n_bins + b], w2);
@@ -211,7 +214,7 @@ int vegas_grid(int64_t n)
 
 extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double ln_tau_min, double ln_s,
                                         int32_t n_bins, const double *edges, const double *v, int64_t n,
-                                        double *sums, pdfgpu_stream_t stream)
+                                        double shift, double *sums, pdfgpu_stream_t stream)
 {
     PDF_TRACE("pdf_vegas_lumi_iteration");
     clear_error();
@@ -220,6 +223,7 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
     if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
     if (n_bins < 2 || n_bins > kMaxBins) return fail(PDF_E_RANGE, "n_bins must be in [2, 1024]");
     if (!(ln_tau_min < 0.0)) return fail(PDF_E_ARG, "ln_tau_min must be negative");
+    if (!(shift > -INFINITY && shift < INFINITY)) return fail(PDF_E_ARG, "shift must be finite");
     if (n < 0) return fail(PDF_E_ARG, "negative n");
     if (!edges || !sums || (n > 0 && !v)) return fail(PDF_E_ARG, "null array");
     if (g->d.nflav > PDF_MAX_PIDS) return fail(PDF_E_RANGE, "too many flavours");
@@ -244,8 +248,8 @@ extern "C" int pdf_vegas_lumi_iteration(pdfgpu_grid_t g, int32_t member, double 
         if (rc) return rc;
         g->partials_cap = 2 * grid;
     }
-    k<<<grid, kBlock, smem, s>>>(g->d, anti, member, ln_tau_min, ln_s, n_bins, edges, v, n, g->partials,
-                                       sums + 2);
+    k<<<grid, kBlock, smem, s>>>(g->d, anti, member, ln_tau_min, ln_s, n_bins, edges, v, n, shift,
+                                 g->partials, sums + 2);
     PDF_CUDA(cudaGetLastError());
     k_vegas_final<<<1, 256, 0, s>>>(g->partials, grid, sums);
     PDF_CUDA(cudaGetLastError());
@@ -306,7 +310,7 @@ extern "C" int pdf_vegas_map(int32_t dim, int32_t n_bins, const double *edges, c
 }
 
 extern "C" int pdf_vegas_accumulate(int32_t dim, int32_t n_bins, const double *w, const int32_t *bins,
-                                    int64_t n, double *sums, pdfgpu_stream_t stream)
+                                    int64_t n, double shift, double *sums, pdfgpu_stream_t stream)
 {
     PDF_TRACE("pdf_vegas_accumulate");
     clear_error();
@@ -314,13 +318,14 @@ extern "C" int pdf_vegas_accumulate(int32_t dim, int32_t n_bins, const double *w
     if (n_bins < 2 || n_bins > kMaxBins) return fail(PDF_E_RANGE, "n_bins must be in [2, 1024]");
     if (n < 0) return fail(PDF_E_ARG, "negative n");
     if (!sums || (n > 0 && (!w || !bins))) return fail(PDF_E_ARG, "null array");
+    if (!(shift > -INFINITY && shift < INFINITY)) return fail(PDF_E_ARG, "shift must be finite");
     cudaStream_t s = (cudaStream_t)stream;
     PDF_CUDA(cudaMemsetAsync(sums, 0, (2 + (size_t)dim * n_bins) * sizeof(double), s));
     if (n == 0) return PDF_OK;
     size_t smem = (size_t)dim * n_bins * sizeof(double);
     int rc = allow_dynamic_smem((const void *)k_vegas_accumulate, smem);
     if (rc) return rc;
-    k_vegas_accumulate<<<vegas_grid(n), kBlock, smem, s>>>(dim, n_bins, w, bins, n, sums);
+    k_vegas_accumulate<<<vegas_grid(n), kBlock, smem, s>>>(dim, n_bins, w, bins, n, shift, sums);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }

@@ -10,7 +10,10 @@ dimension (`pdf_vegas_refine`).  ``VegasLumi`` is the fused special case of
 the parton luminosity, evaluated with the map in one kernel
 (`pdf_vegas_lumi_iteration`).  Uniforms come from a torch generator on the
 device or from arrays the caller passes; iterations are combined with
-weights 1/sigma^2.
+weights 1/sigma^2.  The variance of an iteration is taken about the previous
+iteration's estimate (``shift``): the library sums (w - shift)^2, so that a
+nearly flat adapted integrand does not lose its variance to the cancellation
+of E[w^2] - E[w]^2.
 """
 from __future__ import annotations
 
@@ -41,21 +44,24 @@ class VegasLumi:
         self.ln_tau_min, self.ln_s = float(ln_tau_min), float(ln_s)
         self.n_bins, self.alpha = int(n_bins), float(alpha)
         self.edges = np.tile(np.linspace(0.0, 1.0, self.n_bins + 1), (2, 1))
+        self.shift = 0.0               # previous estimate: the variance is taken about it
         self._sums = torch.empty(2 + 2 * self.n_bins, dtype=torch.float64, device=pdf.device)
 
     def iteration(self, v: torch.Tensor, refine: bool = True):
         """One iteration on the uniforms ``v`` ([n][2] float64 on the device).
-        Returns (estimate, error, raw sums)."""
+        Returns (estimate, error, raw sums); the raw sums hold
+        sum (w - shift)^2 with the shift in effect before the call."""
         dev = self.pdf.device
         v = v.to(device=dev, dtype=torch.float64).contiguous()
         n = v.shape[0]
         e = torch.as_tensor(self.edges, device=dev)
         check("pdf_vegas_lumi_iteration", lib().pdf_vegas_lumi_iteration(
             self.pdf.handle, self.member, self.ln_tau_min, self.ln_s, self.n_bins, _ptr(e), _ptr(v), n,
-            _ptr(self._sums), _stream(dev)))
+            float(self.shift), _ptr(self._sums), _stream(dev)))
         s = self._sums.cpu().numpy()
-        mean = s[0] / n
-        var = max(s[1] / n - mean * mean, 0.0) / max(n - 1, 1)
+        mean, err = _mean_and_error(s, n, self.shift)
+        if n:
+            self.shift = mean
         if refine:
             for d in range(2):
                 b = np.ascontiguousarray(s[2 + d * self.n_bins: 2 + (d + 1) * self.n_bins])
@@ -64,7 +70,7 @@ class VegasLumi:
                     b.ctypes.data_as(C.POINTER(C.c_double)), self.n_bins, self.alpha,
                     ed.ctypes.data_as(C.POINTER(C.c_double))))
                 self.edges[d] = ed
-        return mean, math.sqrt(var), s
+        return mean, err, s
 
     def integrate(self, n_iter: int = 5, n_per_iter: int = 1_000_000, seed: int = 0,
                   uniforms=None, warmup: int = 0) -> VegasResult:
@@ -79,6 +85,14 @@ class VegasLumi:
             if it >= warmup:
                 ests.append((est, err))
         return _combine(ests, self.edges.copy())
+
+
+def _mean_and_error(s, n, shift):
+    """Estimate and its standard error from [sum w, sum (w - shift)^2, ...]."""
+    mean = s[0] / n
+    d = mean - shift
+    var = max(s[1] / n - d * d, 0.0) / max(n - 1, 1)
+    return mean, math.sqrt(var)
 
 
 def _combine(ests, edges):
@@ -101,6 +115,7 @@ class Vegas:
         self.dim, self.n_bins, self.alpha = int(dim), int(n_bins), float(alpha)
         self.device = torch.device(device)
         self.edges = np.tile(np.linspace(0.0, 1.0, self.n_bins + 1), (self.dim, 1))
+        self.shift = 0.0               # previous estimate: the variance is taken about it
         self._sums = torch.empty(2 + self.dim * self.n_bins, dtype=torch.float64, device=self.device)
 
     def map(self, v: torch.Tensor):
@@ -115,10 +130,11 @@ class Vegas:
                                                    _ptr(jac), _ptr(bins), _stream(self.device)))
         return r, jac, bins
 
-    def accumulate(self, w: torch.Tensor, bins: torch.Tensor) -> np.ndarray:
+    def accumulate(self, w: torch.Tensor, bins: torch.Tensor, shift: float = 0.0) -> np.ndarray:
+        """[sum w, sum (w - shift)^2, per-dimension per-bin sums of w^2]."""
         w = w.to(device=self.device, dtype=torch.float64).contiguous()
         check("pdf_vegas_accumulate", lib().pdf_vegas_accumulate(self.dim, self.n_bins, _ptr(w), _ptr(bins),
-                                                                 w.numel(), _ptr(self._sums),
+                                                                 w.numel(), float(shift), _ptr(self._sums),
                                                                  _stream(self.device)))
         return self._sums.cpu().numpy()
 
@@ -135,13 +151,14 @@ class Vegas:
         """One iteration on the uniforms v [n][dim]: (estimate, error, sums)."""
         r, jac, bins = self.map(v)
         w = integrand(r) * jac
-        s = self.accumulate(w, bins)
+        s = self.accumulate(w, bins, self.shift)
         n = r.shape[0]
-        mean = s[0] / n
-        var = max(s[1] / n - mean * mean, 0.0) / max(n - 1, 1)
+        mean, err = _mean_and_error(s, n, self.shift)
+        if n:
+            self.shift = mean
         if refine:
             self.refine(s)
-        return mean, math.sqrt(var), s
+        return mean, err, s
 
     def integrate(self, integrand, n_iter: int = 5, n_per_iter: int = 1_000_000, seed: int = 0,
                   uniforms=None, warmup: int = 0) -> VegasResult:

@@ -180,9 +180,10 @@ def test_user_integrand_in_lock_step_with_the_oracle(nn):
     rng = np.random.default_rng(22)
     for it in range(3):
         v = rng.uniform(0, 1, (40_000, 3))
+        shift = vg.shift
         est, err, s = vg.iteration(lambda r: single_top_like(r, gpu_xf, torch), torch.as_tensor(v, device="cuda"))
         r, jac, bins = vegas_map(edges, v)
-        ref = vegas_accumulate(30, single_top_like(r, cpu_xf, np) * jac, bins)
+        ref = vegas_accumulate(30, single_top_like(r, cpu_xf, np) * jac, bins, shift=shift)
         assert np.all(np.abs(s - ref) <= 1e-10 * np.abs(ref)), it
         for d in range(3):
             edges[d] = vegas_refine(ref[2 + 30 * d: 32 + 30 * d], 1.5, edges[d])
@@ -203,3 +204,28 @@ def test_user_integrand_converges():
                                         n_iter=5, n_per_iter=200_000, seed=3, warmup=3)
     assert abs(res.integral - exact) < 4 * res.error
     assert res.error < 2e-3 * exact
+
+
+def test_nearly_flat_integrand_variance_matches_the_oracle():
+    """Weights 1 + 1e-7 g(r): the second iteration takes its variance about
+    the first estimate, on the GPU and in the oracle alike; the two agree to
+    1e-9 and both agree with a two-pass variance of the same weights (about
+    0, E[w^2] - E[w]^2 would cancel to the last digits)."""
+    from paper_2012_08221_gb300.vegas import Vegas
+    rng = np.random.default_rng(23)
+    vg = Vegas(2, n_bins=16)                      # uniform edges: every Jacobian is 1
+    f_gpu = lambda r: 1.0 + 1e-7 * torch.sin(6.0 * r[:, 0]) * torch.cos(5.0 * r[:, 1])
+    n = 1_000_000
+    for it in range(2):
+        v = rng.uniform(0, 1, (n, 2))
+        shift = vg.shift
+        est, err, s = vg.iteration(f_gpu, torch.as_tensor(v, device="cuda"), refine=False)
+    r, jac, bins = vegas_map(vg.edges, v)
+    w = (1.0 + 1e-7 * np.sin(6.0 * r[:, 0]) * np.cos(5.0 * r[:, 1])) * jac
+    ref = vegas_accumulate(16, w, bins, shift=shift)
+    mean_r = ref[0] / n
+    err_r = math.sqrt(max(ref[1] / n - (mean_r - shift) ** 2, 0.0) / (n - 1))
+    assert abs(shift) > 0.5                       # the second iteration ran about the first estimate
+    assert abs(err - err_r) <= 1e-9 * err_r, (err, err_r)
+    two_pass = math.sqrt(math.fsum((w - math.fsum(w) / n) ** 2) / n / (n - 1))
+    assert abs(err - two_pass) <= 1e-6 * two_pass, (err, two_pass)

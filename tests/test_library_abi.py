@@ -28,6 +28,26 @@ def test_header_declares_the_boundary():
         assert must in names, must
 
 
+def test_every_declaration_cites_its_passage():
+    """Each entry point of include/*.h is documented by the comment right
+    before it, and that comment cites the passage of the paper that defines
+    the operation (a "Sec." reference) or says that the call goes beyond the
+    paper (or that the paper has no counterpart)."""
+    decl = re.compile(r"^\s*(?:const\s+)?[A-Za-z_]\w*\s*\**\s*([A-Za-z_]\w*)\s*\(([^;{]*?)\)\s*;", re.M)
+    missing = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        for m in decl.finditer(text):
+            before = text[:m.start()]
+            comment = before[before.rfind("/*"):before.rfind("*/")]
+            low = comment.lower()
+            if not ("Sec." in comment or "beyond the paper" in low or "no counterpart" in low):
+                missing.append(m.group(1))
+    assert not missing, missing
+
+
 def test_library_builds_loads_and_exports_every_symbol():
     from paper_2012_08221_gb300 import build
     path = build.build()

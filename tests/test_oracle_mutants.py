@@ -61,6 +61,9 @@ VEGAS_MUTANTS = {
                                                   "out[2 + d * n_bins + bins[i * dim + d]] += wi;"),
     "VEGAS tau mapped the other way": ("double ln_tau = (1.0 - r[0]) * ln_tau_min;",
                                        "double ln_tau = r[0] * ln_tau_min;"),
+    "VEGAS second moment ignores the shift": ("out[1] += (wt - shift) * (wt - shift);", "out[1] += wt * wt;"),
+    "general VEGAS second moment ignores the shift": ("out[1] += (wi - shift) * (wi - shift);",
+                                                      "out[1] += wi * wi;"),
 }
 
 
@@ -230,6 +233,7 @@ def vegas_pins_fail():
         V.test_non_uniform_map_midpoint_rule_is_exact()
         V.test_general_map_midpoint_lattice_is_exact_for_multilinear_integrands()
         V.test_general_map_and_accumulate_reproduce_the_fused_luminosity_sums()
+        V.test_second_moment_about_a_shift()
     except AssertionError:
         return True
     return False

@@ -139,3 +139,44 @@ def test_general_map_and_accumulate_reproduce_the_fused_luminosity_sums():
     w = (-LN_TAU_MIN) * (-ln_tau) * lum * jac
     split = vegas_accumulate(nb, w, bins)
     assert np.allclose(split, fused, rtol=1e-13, atol=0)
+
+
+def test_second_moment_about_a_shift():
+    """sum (w - c)^2 is the exactly rounded sum of the squared deviations,
+    and for the fused luminosity it obeys the identity
+    sum (w - c)^2 = sum w^2 - 2 c sum w + n c^2 (to rounding)."""
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal(20_000) * 3.0 + 7.0
+    bins = rng.integers(0, 16, (w.size, 2)).astype(np.int32)
+    for c in (0.0, 7.0, -2.5):
+        s = vegas_accumulate(16, w, bins, shift=c)
+        want = math.fsum((w - c) ** 2)
+        assert abs(s[1] - want) <= 1e-13 * want
+        assert abs(s[0] - math.fsum(w)) <= 1e-13 * math.fsum(np.abs(w))
+        # the per-bin sums stay sums of w^2 whatever the shift
+        assert np.array_equal(s[2:], vegas_accumulate(16, w, bins)[2:])
+    o = OracleGrid.from_synth(synth.grid_nnpdf())
+    v = rng.uniform(0, 1, (3000, 2))
+    edges = np.tile(np.linspace(0, 1, 11), (2, 1))
+    s0 = vegas_sums(o, 0, LN_TAU_MIN, LN_S, edges, v)
+    c = s0[0] / v.shape[0]
+    sc = vegas_sums(o, 0, LN_TAU_MIN, LN_S, edges, v, shift=c)
+    assert sc[0] == s0[0] and np.array_equal(sc[2:], s0[2:])
+    assert abs(sc[1] - (s0[1] - 2 * c * s0[0] + v.shape[0] * c * c)) <= 1e-10 * s0[1]
+    assert sc[1] < 0.9 * s0[1]
+
+
+def test_variance_of_a_nearly_flat_integrand():
+    """Weights 1 + 1e-7 g: about the mean, the variance comes out to full
+    precision (against a two-pass sum of exact deviations); about 0 it is
+    the difference of two sums of ~1 that agree to 1e-14, and is lost."""
+    rng = np.random.default_rng(6)
+    n = 200_000
+    w = 1.0 + 1e-7 * np.sin(2 * np.pi * rng.uniform(0, 1, n))
+    bins = np.zeros((n, 1), dtype=np.int32)
+    mean = math.fsum(w) / n
+    exact = math.fsum((w - mean) ** 2) / n
+    s = vegas_accumulate(4, w, bins, shift=mean)
+    assert abs((s[1] / n - (s[0] / n - mean) ** 2) - exact) <= 1e-9 * exact
+    s = vegas_accumulate(4, w, bins, shift=1.0)          # a shift near, not at, the mean
+    assert abs((s[1] / n - (s[0] / n - 1.0) ** 2) - exact) <= 1e-6 * exact
