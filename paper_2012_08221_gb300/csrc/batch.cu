@@ -372,6 +372,14 @@ extern "C" int pdf_batch_prepare(const pdfgpu_batch_desc *descs, int32_t n_desc,
         evals += D.n * D.n_pid;
     }
     b->nreq = n_desc;
+    // Tiles are handed out in table order: grouping the requests by (grid,
+    // member) makes the CTAs that run at one time read one member's
+    // coefficient table, which then stays in L2, instead of every member of
+    // every set at once (the outputs go to each request's own array, so the
+    // order changes no result).
+    std::stable_sort(b->host_reqs.begin(), b->host_reqs.end(), [](const BatchReq &a, const BatchReq &c) {
+        return a.grid != c.grid ? a.grid < c.grid : a.member < c.member;
+    });
     BTRY(dev_malloc((void **)&b->d_grids, gd.size() * sizeof(GridDev), "batch grid table"));
     BTRY(dev_malloc((void **)&b->d_reqs, b->host_reqs.size() * sizeof(BatchReq), "batch request table"));
     BTRY(dev_malloc((void **)&b->d_ticket, sizeof(unsigned long long), "batch ticket"));
