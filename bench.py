@@ -443,12 +443,20 @@ def main():
     evals = npts * g.n_flav
     value = whole_job_rate(evals, world, ms)
     flops_launch = npts * work.xfxq2_point_flops(g.n_flav)
+    flops_matrix = npts * work.xfxq2_point_flops_matrix_form(g.n_flav)
     bytes_launch = npts * work.xfxq2_point_bytes(g.n_flav)
     achieved = flops_launch / (k_ms * 1e-3)
     traffic = measured_traffic("k_xfxq2", npts)
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": "k_xfxq2",
                 "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak,
+                "flops_per_point": work.xfxq2_point_flops(g.n_flav),
+                "frac_matrix_form": flops_matrix / (k_ms * 1e-3) / peak,
+                "flops_per_point_matrix_form": work.xfxq2_point_flops_matrix_form(g.n_flav),
+                "frac_note": "frac counts the flops of the patch form the kernel runs (15 FMA per flavour, "
+                             "table log); frac_matrix_form counts 40 F + 50 flops per point, the separable-"
+                             "weight form (20 FMA per flavour + weights), which does more arithmetic than the "
+                             "kernel and so can exceed 1; the headroom left is 100 - ncu_fp64_pipe_active_pct",
                 "peak_source": f"derived: {sms} SMs x {DFMA_PER_SM_CLK} DFMA/clk x 2 flop x {peak_mhz:.0f} MHz "
                                f"(max SM clock)",
                 "probe": {"value": probe / 1e12, "unit": "TFLOP/s",
@@ -496,8 +504,28 @@ def main():
             del Xs, Qs, Os, graph
 
     forms = {}
-    want = set(["small", "fwdbwd", "batched", "lumi", "vegas", "vegas_user"] if args.forms == "all" else
+    want = set(["small", "combined", "fwdbwd", "batched", "lumi", "vegas", "vegas_user"] if args.forms == "all" else
                ([] if args.forms == "none" else args.forms.split(",")))
+
+    # ------------- x*f and alpha_s at the same Q^2: one launch against two
+    if "combined" in want:
+        OUTc = torch.empty_like(OUT)
+        ASc = torch.empty_like(AS)
+
+        def two_calls():
+            pdf.xfxQ2(pids, X, Q, out=OUTc)
+            pdf.alphasQ2(Q, out=ASc)
+
+        ms_two, _ = timed(two_calls, args.steps, args.warmup)
+        ms_one, _ = timed(lambda: pdf.xfxQ2_alphasQ2(pids, X, Q, out=OUTc, alphas=ASc), args.steps, args.warmup)
+        forms["combined"] = {
+            "workload": "NNPDF-shaped grid, 1e7 points x 13 flavours and alpha_s at the same Q^2 (as an "
+                        "integrand needs them at each point's factorisation scale)",
+            "value": whole_job_rate(evals + npts, world, ms_one), "unit": "evals/s (x*f and alpha_s)",
+            "ms_per_step": ms_one, "kernel": "k_xfxq2 with alpha_s (xfxQ2_alphasQ2)",
+            "two_calls": {"ms_per_step": ms_two, "what": "xfxQ2 then alphasQ2 on the same arrays"},
+            "fp64_frac": npts * (work.xfxq2_point_flops(g.n_flav) + 6) / (ms_one * 1e-3) / peak}
+        del OUTc, ASc
 
     # ------------------------- the small grid: 50 x 20 knots, 11 flavours
     if "small" in want:

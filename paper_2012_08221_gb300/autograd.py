@@ -8,6 +8,11 @@ into dL/dvalues (the derivative a PDF fit needs).  The forward keeps a
 32-byte adjoint tape per point (cells, local coordinates, flags), so that the
 backward does not search the knots or take logarithms again.  ``LumiFn`` does the same
 for the fused luminosity workload, L = (1/n) sum_e sum_a f_a(x1) f_-a(x2).
+
+The coefficients live in ONE table per PDF handle, rebuilt by every forward and
+backward call from the values tensor it is given: two differentiable
+evaluations with different values on one handle, from two streams at once,
+race on that table.  Use one handle per stream (or order the streams).
 """
 from __future__ import annotations
 

@@ -25,6 +25,17 @@ def xfxq2_point_flops(n_flav: int) -> int:
     return 2 * LOG_FLOPS + 2 * AXIS_FLOPS + PATCH_FLOPS * n_flav
 
 
+def xfxq2_point_flops_matrix_form(n_flav: int) -> int:
+    """The same point counted in the separable-weight (matrix) form of the
+    method: per axis 4 Hermite weights from the basis and the
+    finite-difference coefficients (about 50 flops for both axes), then per
+    flavour the contraction sum_j Wq_j sum_i Wx_i v_ij, 20 FMA; the two logs
+    counted apart.  The kernels evaluate the same interpolant from
+    precomputed patch coefficients in 15 FMA per flavour, so this count is
+    larger than the work they do: a fraction on it can exceed 1."""
+    return 40 * n_flav + 50
+
+
 def xfxq2_point_bytes(n_flav: int) -> int:
     return 16 + 8 * n_flav            # x, Q^2 in; F outputs
 
