@@ -15,8 +15,10 @@
 // arithmetic that follows is the same.
 //
 // Grid gradient of the pointwise form (one flavour per point): the points
-// are counting-sorted by (cell, flavour) and the gradient is accumulated per
-// bin in the monomial basis of the patch,
+// are counting-sorted by (cell, flavour) -- a counting pass over the tape's
+// cells (the forward's tape, or one made here), a scan, and the record pass
+// placing each point's record in its bin -- and the gradient is accumulated
+// per bin in the monomial basis of the patch,
 //   G[n][m] = sum over the bin's points of g bq_n bx_m,
 // one FMA per term with no stencil weights, then mapped back to the 16
 // stencil values once per bin run: dL/dv[j][i] = sum_n,m Mq[n][j] G[n][m]
@@ -90,10 +92,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
                 continue;
             }
         }
-        // derivative bases: (0, 1, 2t, 3t^2) inside; outside (0, 1, 1, 1) for
-        // the linear continuation, and no derivative across a frozen edge
-        double dx2 = X.in ? 2.0 * X.t : 1.0, dx3 = X.in ? 3.0 * X.t * X.t : 1.0;
-        double dq2 = Q.in ? 2.0 * Q.t : 1.0, dq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
+        // derivatives of the patch: (0, 1, 2t, 3t^2) inside; outside (0, 1, 1, 1)
+        // for the linear continuation, and none across a frozen edge
         const bool fzx = !X.in && g.extrap == PDF_EXTRAP_FREEZE;
         const bool fzq = !Q.in && g.extrap == PDF_EXTRAP_FREEZE;
         const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
             if (col < 0) continue;
             double ga = PW ? gout[i] : gout[i * npid + a];
             double dtx, dtq;
-            patch_d(cell + col * 16, X, Q, dx2, dx3, dq2, dq3, &dtx, &dtq);
+            patch_d_horner(cell + col * 16, X, Q, &dtx, &dtq);
             if (fzx) dtx = 0.0;
             if (fzq) dtq = 0.0;
             sx = fma(ga, dtx, sx);
@@ -149,32 +149,61 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
 
 // ------------------------------------------- sorted pointwise grid gradient
 
-constexpr int kMaxSmemBins = 12 * 1024;   // histogram / tile counters in shared memory
-constexpr int kPlaceTile = 32768;         // points per block of the placing pass
+constexpr int kMaxSmemBins = 12 * 1024;   // bin counters in shared memory
+constexpr int kCountBlock = 1024;         // one such block per SM counts
+constexpr int kCountIlp = 4;
 constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;            // sorted points per warp of the accumulation
 constexpr int64_t kSortChunk = (int64_t)1 << 24;
 
-// Per point (chunk-local index k of point i0 + k): dL/dx and dL/dQ^2 as in
-// k_bwd, the bin key (cell * F + flavour column) and the bin histogram.  The
-// key is -1 for a point that adds nothing (a domain error, outside the grid
-// under the error option, or an absent pid) and for a point outside the
-// knot range on either axis: such a point adds its exact stencil weights of
-// the extrapolation, (1 - t, t) on the edge cell's two knots, to the
-// gradient here with global atomics (rare points; through the monomial
-// basis the two knots that carry no weight would receive rounding-sized
-// terms instead of zeros).  Without a forward tape the point's tape record
-// is written to `tape_out` (chunk-local) for the placing pass.
-template <bool TAPE>
-__global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const int *__restrict__ pid,
-                                                    const double *__restrict__ x,
-                                                    const double *__restrict__ q2, int64_t i0, int m,
-                                                    const double *__restrict__ tape,
-                                                    double *__restrict__ tape_out,
-                                                    const double *__restrict__ gout,
-                                                    double *__restrict__ gx, double *__restrict__ gq,
-                                                    double *__restrict__ gval, int *__restrict__ key,
-                                                    int *__restrict__ hist, int nbins)
+// Sorted record of one point (32 bytes): t of the x axis, t of the Q axis
+// (as the tape holds them), g = dL/d(x*f) of the point, and the bits of
+// bin (low 32) | x inside (bit 32) | Q inside (bit 33).
+__device__ __forceinline__ void put_rec(double *__restrict__ rec, int pos, double tx, double tq, double ga,
+                                        int b, bool xin, bool qin)
+{
+    const uint64_t bits = (uint64_t)(uint32_t)b | ((uint64_t)xin << 32) | ((uint64_t)qin << 33);
+    double2 *d = reinterpret_cast<double2 *>(rec + 4 * (size_t)pos);
+    d[0] = make_double2(tx, tq);
+    d[1] = make_double2(ga, dfrom(bits));
+}
+
+// Bin of a point in the sorted accumulation (cell * F + flavour column), or
+// -1 for a point that adds nothing there: a domain error, outside the grid
+// under the error option, an absent pid, or outside the knot range on either
+// axis (see k_bwd_rec).  The counting pass and the record pass both decide
+// through this one function, so that every record placed was counted.
+__device__ __forceinline__ int sorted_bin(const GridDev &g, const Axis &X, const Axis &Q, bool bad, int col,
+                                          int nbins)
+{
+    if (bad || col < 0 || !(X.in && Q.in)) return -1;
+    return checked_index(g.status, (Q.cell * g.nxc + X.cell) * g.nflav + col, nbins);
+}
+
+// Without a forward tape: the tape records of the chunk's points (domain
+// check, both knot searches and logarithms), into chunk-local scratch.
+__global__ void __launch_bounds__(kBlock) k_bwd_axes(GridDev g, const double *__restrict__ x,
+                                                     const double *__restrict__ q2, int64_t i0, int m,
+                                                     double *__restrict__ tape)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const double xi = x[i0 + k], qi = q2[i0 + k];
+        bool bad = !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
+        double u, w;
+        Axis X = axis_x(g, bad ? 0.5 : xi, &u);
+        Axis Q = axis_q2(g, bad ? 10.0 : qi, &w);
+        bad |= out_of_range(g, X, Q);
+        tape_put(tape, k, X, Q, bad);
+    }
+}
+
+// Histogram of the chunk's bins from the tape's cells and flags and the pids
+// (12 bytes read per point, no FP64 work).  One block of kCountBlock threads
+// per SM, so that flushing the shared-memory counters costs one pass over
+// the bins per SM, not per small block.  `tape` is the chunk's view.
+__global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int *__restrict__ pid,
+                                                           const double *__restrict__ tape, int64_t i0, int m,
+                                                           int *__restrict__ hist, int nbins)
 {
     extern __shared__ int shist[];
     const bool sh = nbins <= kMaxSmemBins;
@@ -182,25 +211,59 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const
         for (int k = threadIdx.x; k < nbins; k += blockDim.x) shist[k] = 0;
         __syncthreads();
     }
+    // kCountIlp points per thread at a time: the pass is bound by memory
+    // latency, so each thread keeps that many loads in flight
+    const int stride = gridDim.x * blockDim.x;
+    for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < m; k0 += kCountIlp * stride) {
+        int b[kCountIlp];
+#pragma unroll
+        for (int u = 0; u < kCountIlp; ++u) {
+            const int k = k0 + u * stride;
+            b[u] = -1;
+            if (k < m) {
+                Axis X, Q;
+                const bool bad = tape_get_cells(g, tape, k, X, Q);
+                b[u] = sorted_bin(g, X, Q, bad, bad ? -1 : pid_col(g, pid[i0 + k]), nbins);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kCountIlp; ++u) {
+            if (b[u] < 0) continue;
+            if (sh) atomicAdd(&shist[b[u]], 1);
+            else atomicAdd(&hist[b[u]], 1);
+        }
+    }
+    if (sh) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+            if (shist[k]) atomicAdd(&hist[k], shist[k]);
+    }
+}
+
+// Per point (chunk-local index k of point i0 + k, tape record k of the
+// chunk's view): dL/dx and dL/dQ^2 as in k_bwd, and the point's record,
+// placed in the next free slot of its bin (cursor[b], from the scan of
+// k_bwd_count's histogram): the scattered store overlaps the FP64 work.  A
+// point outside the knot range on either axis has no record: it adds its
+// exact stencil weights of the extrapolation, (1 - t, t) on the edge cell's
+// two knots, to the gradient here with global atomics (rare points; through
+// the monomial basis the two knots that carry no weight would receive
+// rounding-sized terms instead of zeros).
+__global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const int *__restrict__ pid,
+                                                    const double *__restrict__ x,
+                                                    const double *__restrict__ q2, int64_t i0, int m,
+                                                    const double *__restrict__ tape,
+                                                    const double *__restrict__ gout,
+                                                    double *__restrict__ gx, double *__restrict__ gq,
+                                                    double *__restrict__ gval, int nbins,
+                                                    int *__restrict__ cursor, double *__restrict__ rec)
+{
     const size_t cell_stride = (size_t)g.nflav * 16;
     const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
         const int64_t i = i0 + k;
-        const double xi = x[i], qi = q2[i];
         Axis X, Q;
-        bool bad;
-        if (TAPE) {
-            bad = tape_get(g, tape, i, X, Q);
-        } else {
-            bad = !(x_ok(dbits(xi)) && q2_ok(dbits(qi)));
-            double u, w;
-            X = axis_x(g, bad ? 0.5 : xi, &u);
-            Q = axis_q2(g, bad ? 10.0 : qi, &w);
-            bad |= out_of_range(g, X, Q);
-            tape_put(tape_out, k, X, Q, bad);
-        }
-        key[k] = -1;
-        if (bad) {
+        if (tape_get(g, tape, k, X, Q)) {
             if (gx) gx[i] = qnan();
             if (gq) gq[i] = qnan();
             continue;
@@ -213,15 +276,12 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const
         }
         const double ga = gout[i];
         if (gx || gq) {
-            double dx2 = X.in ? 2.0 * X.t : 1.0, dx3 = X.in ? 3.0 * X.t * X.t : 1.0;
-            double dq2 = Q.in ? 2.0 * Q.t : 1.0, dq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
             double dtx, dtq;
-            patch_d(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q, dx2, dx3, dq2, dq3,
-                    &dtx, &dtq);
+            patch_d_horner(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q, &dtx, &dtq);
             if (!X.in && g.extrap == PDF_EXTRAP_FREEZE) dtx = 0.0;
             if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dtq = 0.0;
-            if (gx) gx[i] = ga * dtx * g.xcell[X.cell].y * __drcp_rn(xi);
-            if (gq) gq[i] = ga * dtq * g.qcell[Q.cell].y * __drcp_rn(qi);
+            if (gx) gx[i] = ga * dtx * g.xcell[X.cell].y * __drcp_rn(x[i]);
+            if (gq) gq[i] = ga * dtq * g.qcell[Q.cell].y * __drcp_rn(q2[i]);
         }
         if (!(X.in && Q.in)) {
             double Wx[4], Wq[4];
@@ -243,70 +303,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const
             }
             continue;
         }
-        const int b = checked_index(g.status, (Q.cell * g.nxc + X.cell) * g.nflav + col, nbins);
-        key[k] = b;
-        if (sh) atomicAdd(&shist[b], 1);
-        else atomicAdd(&hist[b], 1);
-    }
-    if (sh) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < nbins; k += blockDim.x)
-            if (shist[k]) atomicAdd(&hist[k], shist[k]);
-    }
-}
-
-// Sorted record of one point (32 bytes): t of the x axis, t of the Q axis
-// (as the tape holds them), g = dL/d(x*f) of the point, and the bits of
-// key (low 32) | x inside (bit 32) | Q inside (bit 33).
-__device__ __forceinline__ void put_rec(double *__restrict__ rec, int pos, const D4 &t, double ga, int b)
-{
-    const unsigned f = (unsigned)dbits(t.w);
-    const uint64_t bits = (uint64_t)(uint32_t)b | ((uint64_t)(f & 1u) << 32) | ((uint64_t)((f >> 2) & 1u) << 33);
-    double2 *d = reinterpret_cast<double2 *>(rec + 4 * (size_t)pos);
-    d[0] = make_double2(t.x, t.y);
-    d[1] = make_double2(ga, dfrom(bits));
-}
-
-// Places the records of a tile of kPlaceTile points in bin order: counts
-// them per bin in shared memory, reserves one range per bin present with a
-// single global atomic, then writes each record into its bin's range (the
-// order inside a bin is free: the accumulation sums it).  nbins <=
-// kMaxSmemBins.  `tape` and `gout` are the chunk's views.
-__global__ void __launch_bounds__(kBlock) k_bwd_place_tiled(const int *__restrict__ key, int m, int nbins,
-                                                            int *__restrict__ cursor,
-                                                            const double *__restrict__ tape,
-                                                            const double *__restrict__ gout,
-                                                            double *__restrict__ rec)
-{
-    extern __shared__ int sc[];
-    const int r0 = blockIdx.x * kPlaceTile, r1 = min(m, r0 + kPlaceTile);
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) sc[b] = 0;
-    __syncthreads();
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const int b = key[r];
-        if (b >= 0) atomicAdd(&sc[b], 1);
-    }
-    __syncthreads();
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
-        const int c = sc[b];
-        if (c) sc[b] = atomicAdd(&cursor[b], c);
-    }
-    __syncthreads();
-    for (int r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-        const int b = key[r];
-        if (b >= 0) put_rec(rec, atomicAdd(&sc[b], 1), ld4(tape + 4 * (size_t)r), gout[r], b);
-    }
-}
-
-// The same with one global atomic per record (histograms too large for
-// shared memory).
-__global__ void __launch_bounds__(kBlock) k_bwd_place(const int *__restrict__ key, int m,
-                                                      int *__restrict__ cursor, const double *__restrict__ tape,
-                                                      const double *__restrict__ gout, double *__restrict__ rec)
-{
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
-        const int b = key[r];
-        if (b >= 0) put_rec(rec, atomicAdd(&cursor[b], 1), ld4(tape + 4 * (size_t)r), gout[r], b);
+        const int b = sorted_bin(g, X, Q, false, col, nbins);
+        put_rec(rec, atomicAdd(&cursor[b], 1), X.t, Q.t, ga, b, X.in, Q.in);
     }
 }
 
@@ -408,7 +406,7 @@ int backward_sorted(pdfgpu_grid *g, int member, const int *pid, const double *x,
     const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * g->d.nflav;
     if (nbins64 >= (int64_t)1 << 30) return fail(PDF_E_RANGE, "grid too large for the sorted adjoint");
     const int nbins = (int)nbins64;
-    // points per round of record, sort and accumulation ($PDFGPU_SORT_CHUNK
+    // points per round of count, records and accumulation ($PDFGPU_SORT_CHUNK
     // overrides the default; the scratch grows with it)
     int64_t chunk_max = kSortChunk;
     if (const char *e = getenv("PDFGPU_SORT_CHUNK")) {
@@ -417,11 +415,10 @@ int backward_sorted(pdfgpu_grid *g, int member, const int *pid, const double *x,
     }
     const int64_t chunk = std::min<int64_t>(n, chunk_max);
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    const size_t bkey = al((size_t)chunk * sizeof(int));
     const size_t brec = al((size_t)chunk * 32);
-    const size_t btape = tape ? 0 : brec;
+    const size_t btape = tape ? 0 : brec;        // tape records made here when the caller has none
     const size_t bbins = al((size_t)(nbins + 1) * sizeof(int));
-    const size_t need = bkey + brec + btape + 3 * bbins;
+    const size_t need = brec + btape + 3 * bbins;
     if (g->bwd_scratch_bytes < need) {
         if (g->bwd_scratch) cudaFree(g->bwd_scratch);
         g->bwd_scratch = nullptr;
@@ -430,39 +427,30 @@ int backward_sorted(pdfgpu_grid *g, int member, const int *pid, const double *x,
         g->bwd_scratch_bytes = need;
     }
     char *base = (char *)g->bwd_scratch;
-    int *key = (int *)base;
-    double *rec = (double *)(base + bkey);
-    double *tape_s = tape ? nullptr : (double *)(base + bkey + brec);
-    int *hist = (int *)(base + bkey + brec + btape);
-    int *offs = (int *)(base + bkey + brec + btape + bbins);
-    int *cursor = (int *)(base + bkey + brec + btape + 2 * bbins);
+    double *rec = (double *)base;
+    double *tape_s = tape ? nullptr : (double *)(base + brec);
+    int *hist = (int *)(base + brec + btape);
+    int *offs = (int *)(base + brec + btape + bbins);
+    int *cursor = (int *)(base + brec + btape + 2 * bbins);
     const size_t hsmem = nbins <= kMaxSmemBins ? (size_t)nbins * sizeof(int) : 0;
-    const void *krec = tape ? (const void *)k_bwd_rec<true> : (const void *)k_bwd_rec<false>;
-    int rc = allow_dynamic_smem(krec, hsmem);
-    if (rc) return rc;
-    rc = allow_dynamic_smem((const void *)k_bwd_place_tiled, hsmem);
+    int rc = allow_dynamic_smem((const void *)k_bwd_count, hsmem);
     if (rc) return rc;
     for (int64_t i0 = 0; i0 < n; i0 += chunk) {
         const int m = (int)std::min(chunk, n - i0);
+        const double *tv = tape ? tape + 4 * i0 : tape_s;     // the chunk's tape records
+        if (!tape) {
+            k_bwd_axes<<<wave_grid(g, (const void *)k_bwd_axes, kBlock, 0, m), kBlock, 0, st>>>(g->d, x, q2, i0, m,
+                                                                                                tape_s);
+            PDF_CUDA(cudaGetLastError());
+        }
         PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
-        const int grid = wave_grid(g, krec, kBlock, hsmem, m);
-        if (tape)
-            k_bwd_rec<true><<<grid, kBlock, hsmem, st>>>(g->d, member, pid, x, q2, i0, m, tape, nullptr, gout, gx,
-                                                          gq, gval, key, hist, nbins);
-        else
-            k_bwd_rec<false><<<grid, kBlock, hsmem, st>>>(g->d, member, pid, x, q2, i0, m, nullptr, tape_s, gout,
-                                                           gx, gq, gval, key, hist, nbins);
+        const int gc = std::min(g->sm_count, std::max(1, (m + kCountIlp * kCountBlock - 1) / (kCountIlp * kCountBlock)));
+        k_bwd_count<<<gc, kCountBlock, hsmem, st>>>(g->d, pid, tv, i0, m, hist, nbins);
         PDF_CUDA(cudaGetLastError());
         rc = exclusive_scan(hist, nbins, offs, cursor, st);
         if (rc) return rc;
-        const double *tv = tape ? tape + 4 * i0 : tape_s;
-        if (hsmem) {
-            const int tiles = (m + kPlaceTile - 1) / kPlaceTile;
-            k_bwd_place_tiled<<<tiles, kBlock, hsmem, st>>>(key, m, nbins, cursor, tv, gout + i0, rec);
-        } else {
-            const int gp = wave_grid(g, (const void *)k_bwd_place, kBlock, 0, m);
-            k_bwd_place<<<gp, kBlock, 0, st>>>(key, m, cursor, tv, gout + i0, rec);
-        }
+        k_bwd_rec<<<wave_grid(g, (const void *)k_bwd_rec, kBlock, 0, m), kBlock, 0, st>>>(
+            g->d, member, pid, x, q2, i0, m, tv, gout, gx, gq, gval, nbins, cursor, rec);
         PDF_CUDA(cudaGetLastError());
         const int64_t warps = (m + kSegment - 1) / kSegment;
         const int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);

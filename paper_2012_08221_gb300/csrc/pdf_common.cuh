@@ -341,22 +341,24 @@ __device__ __forceinline__ double alphas_any(const GridDev &g, const D4 &a, cons
     return horner(Q, a.x, a.y, a.z, a.w);
 }
 
-// Patch value and its derivatives with respect to tx and tq.
-// (1, dx2, dx3) and (1, dq2, dq3) are the derivative bases of the two axes:
-// (1, 2t, 3t^2) inside the knot range, (1, 1, 1) for the linear continuation.
-__device__ __forceinline__ void patch_d(const double *__restrict__ C, const Axis &X, const Axis &Q,
-                                        double dx2, double dx3, double dq2, double dq3,
-                                        double *dtx, double *dtq)
+// Derivatives of a patch with respect to tx and tq, by Horner's rule along
+// both axes with no powers of t: the rows' values i[n] = c0 + t (c1 + h (c2 + h c3)) and tx-derivatives
+// j[n] = c1 + t2 c2 + t3 c3 with (t2, t3) = (2t, 3t^2) inside and (1, 1)
+// outside; dP/dtx = horner over tq of j[n], dP/dtq = i1 + q2 i2 + q3 i3.
+__device__ __forceinline__ void patch_d_horner(const double *__restrict__ C, const Axis &X, const Axis &Q,
+                                               double *dtx, double *dtq)
 {
+    const double tx2 = X.in ? X.t + X.t : 1.0, tx3 = X.in ? 3.0 * X.t * X.t : 1.0;
+    const double tq2 = Q.in ? Q.t + Q.t : 1.0, tq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
     double i[4], j[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
         D4 r = ld4(C + 4 * n);
-        i[n] = fma(X.b3, r.w, fma(X.b2, r.z, fma(X.t, r.y, r.x)));
-        j[n] = fma(dx3, r.w, fma(dx2, r.z, r.y));
+        i[n] = horner(X, r.x, r.y, r.z, r.w);
+        j[n] = fma(tx3, r.w, fma(tx2, r.z, r.y));
     }
-    *dtx = fma(Q.b3, j[3], fma(Q.b2, j[2], fma(Q.t, j[1], j[0])));
-    *dtq = fma(dq3, i[3], fma(dq2, i[2], i[1]));
+    *dtx = horner(Q, j[0], j[1], j[2], j[3]);
+    *dtq = fma(tq3, i[3], fma(tq2, i[2], i[1]));
 }
 
 // Stencil weights W_i = sum_m M[m][i] b_m of one axis (i <-> knot cell-1+i);
@@ -462,23 +464,41 @@ __device__ __forceinline__ int tape_cell(unsigned *status, uint32_t v, int n)
 #endif
 }
 
-// Rebuilds the two axes of point i from its tape record; returns whether the
-// point is bad.
-__device__ __forceinline__ bool tape_get(const GridDev &g, const double *__restrict__ tape, int64_t i, Axis &X,
-                                         Axis &Q)
+// Cells and range flags of a tape record from its second half (cells, flag
+// bits); returns whether the point is bad.
+__device__ __forceinline__ bool tape_decode(const GridDev &g, double cells_bits, double flag_bits, Axis &X,
+                                            Axis &Q)
 {
-    const D4 r = ld4(tape + 4 * i);
-    const uint64_t cells = dbits(r.z);
-    const unsigned f = (unsigned)dbits(r.w);
+    const uint64_t cells = dbits(cells_bits);
+    const unsigned f = (unsigned)dbits(flag_bits);
     X.cell = tape_cell(g.status, (uint32_t)cells, g.nxc);
     Q.cell = tape_cell(g.status, (uint32_t)(cells >> 32), g.nqc);
     X.in = f & 1u;
     X.below = f & 2u;
     Q.in = f & 4u;
     Q.below = f & 8u;
+    return f & kTapeBad;
+}
+
+// Rebuilds the two axes of point i from its tape record; returns whether the
+// point is bad.
+__device__ __forceinline__ bool tape_get(const GridDev &g, const double *__restrict__ tape, int64_t i, Axis &X,
+                                         Axis &Q)
+{
+    const D4 r = ld4(tape + 4 * i);
+    const bool bad = tape_decode(g, r.z, r.w, X, Q);
     make_basis(X, r.x, g.extrap);
     make_basis(Q, r.y, g.extrap);
-    return f & kTapeBad;
+    return bad;
+}
+
+// Only the cells and flags of point i's tape record (a 16-byte load): the
+// axes' cells and range flags, without local coordinates.
+__device__ __forceinline__ bool tape_get_cells(const GridDev &g, const double *__restrict__ tape, int64_t i,
+                                               Axis &X, Axis &Q)
+{
+    const double2 r = __ldg(reinterpret_cast<const double2 *>(tape + 4 * i + 2));
+    return tape_decode(g, r.x, r.y, X, Q);
 }
 
 __device__ __forceinline__ int pid_col(const GridDev &g, int pid)
