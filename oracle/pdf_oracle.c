@@ -132,16 +132,19 @@ static double fd_deriv(int k, int n, const double *z, double gm, double g0, doub
 static double hermite(double t, double dz, double g0, double g1, double d0, double d1,
                       double *ddz)
 {
-    double t2 = t * t, t3 = t2 * t;
-    double h00 = 2.0 * t3 - 3.0 * t2 + 1.0;
-    double h10 = t3 - 2.0 * t2 + t;
-    double h01 = -2.0 * t3 + 3.0 * t2;
-    double h11 = t3 - t2;
+    /* the four basis polynomials in factored form, (2t^3 - 3t^2 + 1) =
+     * (1-t)^2 (1+2t) and so on: the same cubics, each accurate to rounding
+     * relative to itself near both knots (no cancellation of O(1) terms) */
+    double s = 1.0 - t, t2 = t * t, s2 = s * s;
+    double h00 = s2 * (1.0 + 2.0 * t);
+    double h10 = t * s2;
+    double h01 = t2 * (3.0 - 2.0 * t);
+    double h11 = -t2 * s;
     if (ddz) {
-        double e00 = 6.0 * t2 - 6.0 * t;
-        double e10 = 3.0 * t2 - 4.0 * t + 1.0;
-        double e01 = -6.0 * t2 + 6.0 * t;
-        double e11 = 3.0 * t2 - 2.0 * t;
+        double e00 = -6.0 * t * s;
+        double e10 = s * (1.0 - 3.0 * t);
+        double e01 = 6.0 * t * s;
+        double e11 = t * (3.0 * t - 2.0);
         *ddz = (e00 * g0 + e10 * dz * d0 + e01 * g1 + e11 * dz * d1) / dz;
     }
     return h00 * g0 + h10 * dz * d0 + h01 * g1 + h11 * dz * d1;

@@ -20,8 +20,10 @@ from tests.tinygrids import fill, tiny_two_sub
 SRC = os.path.join(os.path.dirname(O.__file__), "pdf_oracle.c")
 
 MUTANTS = {
-    "hermite h10 sign": ("double h10 = t3 - 2.0 * t2 + t;", "double h10 = t3 - 2.0 * t2 - t;"),
-    "hermite h01 coefficient": ("double h01 = -2.0 * t3 + 3.0 * t2;", "double h01 = -2.0 * t3 + 2.0 * t2;"),
+    "hermite h10 sign": ("double h10 = t * s2;", "double h10 = -t * s2;"),
+    "hermite h01 coefficient": ("double h01 = t2 * (3.0 - 2.0 * t);", "double h01 = t2 * (2.0 - 2.0 * t);"),
+    "hermite h00 factor": ("double h00 = s2 * (1.0 + 2.0 * t);", "double h00 = s2 * (1.0 + t);"),
+    "hermite derivative e10 sign": ("double e10 = s * (1.0 - 3.0 * t);", "double e10 = s * (1.0 + 3.0 * t);"),
     "hermite derivative dropped": ("return h00 * g0 + h10 * dz * d0 + h01 * g1 + h11 * dz * d1;",
                                    "return h00 * g0 + h10 * dz * d0 + h01 * g1;"),
     "interior slope one-sided": (
