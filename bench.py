@@ -620,26 +620,46 @@ def main():
             L3 = (ad_xfxQ2_pw(p3, VA, P3, XA, QA3) * W3).sum()
             L3.backward()
 
+        # the matrix form through autograd: every flavour at each point
+        from paper_2012_08221_gb300.autograd import xfxQ2 as ad_xfxQ2
+        nm = 1_000_000
+        VM = V3.clone().requires_grad_(True)
+        XM, QM = X3[:nm].clone().requires_grad_(True), Q3[:nm].clone().requires_grad_(True)
+        WM = torch.as_tensor(np.random.default_rng(7).standard_normal((nm, gs.n_flav)), device=dev)
+
+        def step3m():
+            VM.grad = XM.grad = QM.grad = None
+            (ad_xfxQ2(p3, VM, gs.pids, XM, QM) * WM).sum().backward()
+
         ms3a, _ = timed(step3a, args.steps, args.warmup)
         ms3, kb = timed(step3, args.steps, args.warmup, kstep3)
         ms3n, _ = timed(step3n, max(3, args.steps // 2), args.warmup)
+        ms3m, _ = timed(step3m, args.steps, args.warmup)
         n3 = x3.size
-        fl = n3 * (work.pw_fwd_point_flops() + work.pw_bwd_tape_point_flops())
+        fl = n3 * (work.pw_fwd_point_flops() + work.pw_bwd_sorted_point_flops())
         forms["fwd_bwd"] = {
             "workload": "pointwise x*f and its adjoint (dL/dx, dL/dQ^2, dL/dgrid) at 1e7 points, "
                         "50x20 grid, 13 flavours, L = sum w_i xf_{a_i}, through torch.autograd",
             "value": world * n3 / (ms3a * 1e-3), "unit": "evals/s (fwd+bwd)", "ms_per_step": ms3a,
             "fp64_frac": (fl / (ms3a * 1e-3)) / peak,
-            "bwd_kernel": {"kernel": "k_bwd (from the tape)", "ms": kb,
-                           "frac": n3 * work.pw_bwd_tape_point_flops() / (kb * 1e-3) / peak},
+            "fp64_frac_survey_count": n3 * work.pw_fwd_bwd_point_flops_survey() / (ms3a * 1e-3) / peak,
+            "flops_per_point": {"fwd": work.pw_fwd_point_flops(), "bwd": work.pw_bwd_sorted_point_flops(),
+                                "survey_fwd_bwd": work.pw_fwd_bwd_point_flops_survey()},
+            "bwd_kernel": {"kernels": "k_bwd_count, k_scan, k_bwd_rec, k_bwd_accum (from the tape; grid "
+                                      "gradient sorted by cell and flavour)", "ms": kb,
+                           "frac": n3 * work.pw_bwd_sorted_point_flops() / (kb * 1e-3) / peak},
             "tape": "the forward pass writes 32 bytes per point (cells, local coordinates, flags) that the "
                     "adjoint reads instead of searching the knots and taking logarithms again",
             "direct_calls": {"ms_per_step": ms3, "value": world * n3 / (ms3 * 1e-3),
                              "what": "the same two library calls without autograd (no torch "
                                      "multiply, sum or gradient accumulation)"},
             "without_tape": {"ms_per_step": ms3n, "value": world * n3 / (ms3n * 1e-3),
-                             "what": "direct calls, the adjoint recomputing the coordinates"}}
-        del P3, X3, Q3, W3, O3, T3, VA, XA, QA3
+                             "what": "direct calls, the adjoint recomputing the coordinates"},
+            "matrix_form": {"workload": "1e6 points x all 13 flavours, L = sum w_ia xf_a(x_i, Q^2_i), "
+                                        "through torch.autograd (xfxQ2 with the pid list)",
+                            "value": world * nm * gs.n_flav / (ms3m * 1e-3), "unit": "evals/s (fwd+bwd)",
+                            "ms_per_step": ms3m}}
+        del P3, X3, Q3, W3, O3, T3, VA, XA, QA3, VM, XM, QM, WM
 
     # ------------------------------------------------------------- batched
     if "batched" in want:

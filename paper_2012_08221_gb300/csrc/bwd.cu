@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
 
 // ------------------------------------------- sorted pointwise grid gradient
 
-constexpr int kMaxSmemBins = 12 * 1024;   // bin counters in shared memory
+constexpr int kMaxSmemBins = 50 * 1024;   // bin counters in shared memory (200 KB, one block per SM)
 constexpr int kCountBlock = 1024;         // one such block per SM counts
 constexpr int kCountIlp = 4;
 constexpr int kAccWarps = 4;
@@ -168,16 +168,44 @@ __device__ __forceinline__ void put_rec(double *__restrict__ rec, int pos, doubl
     d[1] = make_double2(ga, dfrom(bits));
 }
 
-// Bin of a point in the sorted accumulation (cell * F + flavour column), or
-// -1 for a point that adds nothing there: a domain error, outside the grid
-// under the error option, an absent pid, or outside the knot range on either
-// axis (see k_bwd_rec).  The counting pass and the record pass both decide
-// through this one function, so that every record placed was counted.
+// Half of a cell a point lies in along each axis: bit 0 set when t_x > 1/2,
+// bit 1 when t_q > 1/2.  In an upper half the accumulation runs in powers of
+// s = 1 - t (and maps back with the cell's matrix in s), so that the weights
+// that vanish at the near knot come out of small powers, not of cancelling
+// ones: a bin holds the points of one cell (and flavour) and one half pair.
+// (Inside the knot range t lies in [0, 1], so t > 1/2 is an integer compare
+// of its bit pattern, which keeps the FP64 pipe free.)
+__device__ __forceinline__ bool upper_half(double t) { return dbits(t) > 0x3FE0000000000000ull; }
+
+__device__ __forceinline__ int half_pair(const Axis &X, const Axis &Q)
+{
+    return (upper_half(X.t) ? 1 : 0) | (upper_half(Q.t) ? 2 : 0);
+}
+
+// The local coordinate the accumulation uses: t, or 1 - t in an upper half
+// (exact: t lies in [1/2, 1] there).
+__device__ __forceinline__ double near_coord(double t) { return upper_half(t) ? 1.0 - t : t; }
+
+// Bin of a point in the sorted accumulation, ((cell * F + flavour column) * 4
+// + half pair), or -1 for a point that adds nothing there: a domain error,
+// outside the grid under the error option, an absent pid, or outside the
+// knot range on either axis (see k_bwd_rec).  The counting pass and the
+// record pass both decide through this one function, on the same tape
+// values, so that every record placed was counted.
 __device__ __forceinline__ int sorted_bin(const GridDev &g, const Axis &X, const Axis &Q, bool bad, int col,
                                           int nbins)
 {
     if (bad || col < 0 || !(X.in && Q.in)) return -1;
-    return checked_index(g.status, (Q.cell * g.nxc + X.cell) * g.nflav + col, nbins);
+    return checked_index(g.status, ((Q.cell * g.nxc + X.cell) * g.nflav + col) * 4 + half_pair(X, Q), nbins);
+}
+
+// Bin of a point in the matrix form's sorted accumulation: its cell and
+// half pair (all the call's flavours accumulate together), (cell * 4 + half
+// pair), or -1 as for sorted_bin.
+__device__ __forceinline__ int sorted_cell(const GridDev &g, const Axis &X, const Axis &Q, bool bad, int nbins)
+{
+    if (bad || !(X.in && Q.in)) return -1;
+    return checked_index(g.status, (Q.cell * g.nxc + X.cell) * 4 + half_pair(X, Q), nbins);
 }
 
 // Without a forward tape: the tape records of the chunk's points (domain
@@ -197,10 +225,11 @@ __global__ void __launch_bounds__(kBlock) k_bwd_axes(GridDev g, const double *__
     }
 }
 
-// Histogram of the chunk's bins from the tape's cells and flags and the pids
-// (12 bytes read per point, no FP64 work).  One block of kCountBlock threads
+// Histogram of the chunk's bins from the tape records and the pids (36 bytes
+// read per point, no FP64 work).  One block of kCountBlock threads
 // per SM, so that flushing the shared-memory counters costs one pass over
 // the bins per SM, not per small block.  `tape` is the chunk's view.
+template <bool PW>
 __global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int *__restrict__ pid,
                                                            const double *__restrict__ tape, int64_t i0, int m,
                                                            int *__restrict__ hist, int nbins)
@@ -222,8 +251,9 @@ __global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int 
             b[u] = -1;
             if (k < m) {
                 Axis X, Q;
-                const bool bad = tape_get_cells(g, tape, k, X, Q);
-                b[u] = sorted_bin(g, X, Q, bad, bad ? -1 : pid_col(g, pid[i0 + k]), nbins);
+                const bool bad = tape_get(g, tape, k, X, Q);
+                b[u] = PW ? sorted_bin(g, X, Q, bad, bad ? -1 : pid_col(g, pid[i0 + k]), nbins)
+                          : sorted_cell(g, X, Q, bad, nbins);
             }
         }
 #pragma unroll
@@ -304,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const
             continue;
         }
         const int b = sorted_bin(g, X, Q, false, col, nbins);
-        put_rec(rec, atomicAdd(&cursor[b], 1), X.t, Q.t, ga, b, X.in, Q.in);
+        put_rec(rec, atomicAdd(&cursor[b], 1), near_coord(X.t), near_coord(Q.t), ga, b, X.in, Q.in);
     }
 }
 
@@ -342,9 +372,10 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum(GridDev g, const d
         sG[wid][row0 + s] = acc;
         acc = 0.0;
         __syncwarp(hmask);
-        const int cell = b / F, col = b - cell * F;
+        const int cb = b >> 2, cell = cb / F, col = cb - cell * F;
         const int qc = cell / g.nxc, xc = cell - qc * g.nxc;
-        const double *Mq = g.mq + (size_t)qc * 16, *Mx = g.mx + (size_t)xc * 16;
+        const double *Mq = ((b & 2) ? g.mqs : g.mq) + (size_t)qc * 16;
+        const double *Mx = ((b & 1) ? g.mxs : g.mx) + (size_t)xc * 16;
         // lane (j, i) = (sn, sm)
         double dv = 0.0;
 #pragma unroll
@@ -399,11 +430,244 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum(GridDev g, const d
     if (cur >= 0) flush(cur);
 }
 
-int backward_sorted(pdfgpu_grid *g, int member, const int *pid, const double *x, const double *q2, int64_t n,
-                    const double *tape, const double *gout, double *gx, double *gq, double *gval,
-                    cudaStream_t st)
+// ------------------------------------------ sorted matrix-form grid gradient
+//
+// The matrix form (a shared list of up to kMaxSortedPids flavour columns,
+// gout [n][npid]) sorts the points by cell only: every column of a point
+// accumulates in the same bin, lane 4n + m of a half-warp keeping
+// G_a[n][m] for every column a.  dL/dx and dL/dQ^2 take the derivative of
+// one combined patch, sum_a g_a C_a (16 FMA per column), instead of one
+// derivative per column (the result is linear in the coefficients).
+
+constexpr int kMaxSortedPids = 16;
+
+// Derivatives of a patch held in registers (as patch_d_horner).
+__device__ __forceinline__ void patch_d_regs(const double C[16], const Axis &X, const Axis &Q, double *dtx,
+                                             double *dtq)
 {
-    const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * g->d.nflav;
+    const double tx2 = X.in ? X.t + X.t : 1.0, tx3 = X.in ? 3.0 * X.t * X.t : 1.0;
+    const double tq2 = Q.in ? Q.t + Q.t : 1.0, tq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
+    double i[4], j[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        i[n] = horner(X, C[4 * n], C[4 * n + 1], C[4 * n + 2], C[4 * n + 3]);
+        j[n] = fma(tx3, C[4 * n + 3], fma(tx2, C[4 * n + 2], C[4 * n + 1]));
+    }
+    *dtx = horner(Q, j[0], j[1], j[2], j[3]);
+    *dtq = fma(tq3, i[3], fma(tq2, i[2], i[1]));
+}
+
+// Per point: dL/dx and dL/dQ^2 from the combined patch, and the point's
+// record (t_x, t_q, bits of cell | x inside << 32 | Q inside << 33, point
+// index) placed in its cell's range; points outside the knot range add
+// their exact extrapolation weights per column with global atomics.
+__global__ void __launch_bounds__(kBlock) k_bwd_rec_m(GridDev g, Cols cols, int npid, int member,
+                                                      const double *__restrict__ x,
+                                                      const double *__restrict__ q2, int64_t i0, int m,
+                                                      const double *__restrict__ tape,
+                                                      const double *__restrict__ gout,
+                                                      double *__restrict__ gx, double *__restrict__ gq,
+                                                      double *__restrict__ gval, int nbins,
+                                                      int *__restrict__ cursor, double *__restrict__ rec)
+{
+    __shared__ signed char scol[PDF_MAX_PIDS];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < PDF_MAX_PIDS; ++k) scol[k] = cols.c[k];
+    }
+    __syncthreads();
+    const size_t cell_stride = (size_t)g.nflav * 16;
+    const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const int64_t i = i0 + k;
+        Axis X, Q;
+        if (tape_get(g, tape, k, X, Q)) {
+            if (gx) gx[i] = qnan();
+            if (gq) gq[i] = qnan();
+            continue;
+        }
+        const double *cell = cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride;
+        const double *go = gout + (size_t)i * npid;
+        if (gx || gq) {
+            double C[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) C[c] = 0.0;
+            for (int a = 0; a < npid; ++a) {
+                int col = scol[a];
+                if (col < 0) continue;
+                col = checked_index(g.status, col, g.nflav);
+                const double ga = go[a];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const D4 v = ld4(cell + col * 16 + 4 * r);
+                    C[4 * r] = fma(ga, v.x, C[4 * r]);
+                    C[4 * r + 1] = fma(ga, v.y, C[4 * r + 1]);
+                    C[4 * r + 2] = fma(ga, v.z, C[4 * r + 2]);
+                    C[4 * r + 3] = fma(ga, v.w, C[4 * r + 3]);
+                }
+            }
+            double dtx, dtq;
+            patch_d_regs(C, X, Q, &dtx, &dtq);
+            if (!X.in && g.extrap == PDF_EXTRAP_FREEZE) dtx = 0.0;
+            if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dtq = 0.0;
+            if (gx) gx[i] = dtx * g.xcell[X.cell].y * __drcp_rn(x[i]);
+            if (gq) gq[i] = dtq * g.qcell[Q.cell].y * __drcp_rn(q2[i]);
+        }
+        if (!(X.in && Q.in)) {
+            double Wx[4], Wq[4];
+            stencil_weights(g.mx + (size_t)X.cell * 16, X, Wx);
+            stencil_weights(g.mq + (size_t)Q.cell * 16, Q, Wq);
+            const int qmask = g.qmask[Q.cell], r0 = g.qrow[Q.cell] - 1, k0 = X.cell - 1;
+            for (int a = 0; a < npid; ++a) {
+                int col = scol[a];
+                if (col < 0) continue;
+                col = checked_index(g.status, col, g.nflav);
+                const double ga = go[a];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (!((qmask >> j) & 1)) continue;
+                    const double gj = ga * Wq[j];
+                    const int row = checked_index(g.status, r0 + j, g.nrows);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int kk = k0 + c;
+                        const double t = gj * Wx[c];
+                        if (kk >= 0 && kk < g.nx && (dbits(t) << 1))
+                            atomicAdd(gval + ((size_t)row * g.nx + kk) * g.nflav + col, t);
+                    }
+                }
+            }
+            continue;
+        }
+        const int b = sorted_cell(g, X, Q, false, nbins);
+        const int pos = atomicAdd(&cursor[b], 1);
+        const uint64_t bits = (uint64_t)(uint32_t)b | ((uint64_t)X.in << 32) | ((uint64_t)Q.in << 33);
+        double2 *d = reinterpret_cast<double2 *>(rec + 4 * (size_t)pos);
+        d[0] = make_double2(near_coord(X.t), near_coord(Q.t));
+        d[1] = make_double2(dfrom(bits), dfrom((uint64_t)i));
+    }
+}
+
+// Accumulation over the cell-sorted records of the matrix form: as
+// k_bwd_accum, but each staged record carries the point's whole gout row,
+// and lane 4n + m adds w g_a to G_a[n][m] for every column a, with
+// w = bq_n bx_m (one multiply and npid FMAs per record).  At a cell change
+// the half-warp maps G_a back to the 16 stencil values of column a, one
+// column after another.
+__global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum_m(GridDev g, Cols cols, int npid,
+                                                                const double *__restrict__ rec,
+                                                                const int *__restrict__ offs, int nbins,
+                                                                const double *__restrict__ gout,
+                                                                double *__restrict__ gval)
+{
+    __shared__ double sV[kAccWarps][32][9];                   // bq[4], bx[4] (padded)
+    __shared__ double sGo[kAccWarps][32][kMaxSortedPids + 1]; // the record's gout row (padded)
+    __shared__ int sK[kAccWarps][32];
+    __shared__ double sG[kAccWarps][32];
+    __shared__ signed char scol[PDF_MAX_PIDS];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < PDF_MAX_PIDS; ++k) scol[k] = cols.c[k];
+    }
+    __syncthreads();
+    const int F = g.nflav;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nvalid = offs[nbins];
+    const int64_t wbeg = ((int64_t)blockIdx.x * kAccWarps + wid) * kSegment;
+    if (wbeg >= nvalid) return;
+    const int wend = (int)min((int64_t)nvalid, wbeg + kSegment);
+    const int h = lane >> 4, s = lane & 15, sn = s >> 2, sm = s & 3;
+    const unsigned hmask = 0xFFFFu << (16 * h);
+    const int half = (wend - (int)wbeg + 1) / 2;
+    const int beg = (int)wbeg + h * half;
+    const int end = h ? wend : (int)wbeg + half;
+    const int row0 = h * 16;
+    double acc[kMaxSortedPids];
+#pragma unroll
+    for (int a = 0; a < kMaxSortedPids; ++a) acc[a] = 0.0;
+    int cur = -1;
+    auto flush = [&](int b) {
+        const int cell = b >> 2, qc = cell / g.nxc, xc = cell - qc * g.nxc;
+        const double *Mq = ((b & 2) ? g.mqs : g.mq) + (size_t)qc * 16;
+        const double *Mx = ((b & 1) ? g.mxs : g.mx) + (size_t)xc * 16;
+        const int kk = xc - 1 + sm;
+        const bool ok = ((g.qmask[qc] >> sn) & 1) && kk >= 0 && kk < g.nx;
+        const int row = ok ? checked_index(g.status, g.qrow[qc] - 1 + sn, g.nrows) : 0;
+#pragma unroll
+        for (int a = 0; a < kMaxSortedPids; ++a) {
+            if (a < npid && scol[a] >= 0) {
+                sG[wid][row0 + s] = acc[a];
+                __syncwarp(hmask);
+                double dv = 0.0;
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm) {
+                    double hm = 0.0;
+#pragma unroll
+                    for (int n = 0; n < 4; ++n) hm = fma(Mq[n * 4 + sn], sG[wid][row0 + n * 4 + mm], hm);
+                    dv = fma(hm, Mx[mm * 4 + sm], dv);
+                }
+                __syncwarp(hmask);
+                if (ok && (dbits(dv) << 1)) {
+                    const int col = checked_index(g.status, scol[a], F);
+                    atomicAdd(gval + ((size_t)row * g.nx + kk) * F + col, dv);
+                }
+            }
+            acc[a] = 0.0;
+        }
+    };
+    const int steps = (half + 15) / 16;
+    for (int step = 0; step < steps; ++step) {
+        const int p = beg + step * 16;
+        const int r = p + s;
+        int kr = -1;
+        if (r < end) {
+            const D4 t = ld4(rec + 4 * (size_t)r);
+            const uint64_t bits = dbits(t.z);
+            const int64_t i = (int64_t)dbits(t.w);
+            kr = (int)(uint32_t)bits;
+            const bool xin = (bits >> 32) & 1, qin = (bits >> 33) & 1;
+            const double tx2 = t.x * t.x, tq2 = t.y * t.y;
+            double *v = sV[wid][row0 + s];
+            v[0] = 1.0;
+            v[1] = t.y;
+            v[2] = qin ? tq2 : t.y;
+            v[3] = qin ? tq2 * t.y : t.y;
+            v[4] = 1.0;
+            v[5] = t.x;
+            v[6] = xin ? tx2 : t.x;
+            v[7] = xin ? tx2 * t.x : t.x;
+            const double *go = gout + (size_t)i * npid;
+            for (int a = 0; a < npid; ++a) sGo[wid][row0 + s][a] = go[a];
+        }
+        sK[wid][row0 + s] = kr;
+        __syncwarp();
+        const int nb = min(16, end - p);
+        for (int q = 0; q < nb; ++q) {
+            const int kq = sK[wid][row0 + q];
+            if (kq != cur) {
+                if (cur >= 0) flush(cur);
+                cur = kq;
+            }
+            const double w = sV[wid][row0 + q][sn] * sV[wid][row0 + q][4 + sm];
+#pragma unroll
+            for (int a = 0; a < kMaxSortedPids; ++a)
+                if (a < npid) acc[a] = fma(w, sGo[wid][row0 + q][a], acc[a]);
+        }
+        __syncwarp();
+    }
+    if (cur >= 0) flush(cur);
+}
+
+// The sorted adjoint, pointwise (PW: bins by cell and flavour) or matrix
+// form (bins by cell, up to kMaxSortedPids columns): per chunk of points, the
+// coordinates (without a forward tape), the counting pass, the scan, the
+// record pass and the accumulation.
+template <bool PW>
+int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, const int *pid, const double *x,
+                    const double *q2, int64_t n, const double *tape, const double *gout, double *gx, double *gq,
+                    double *gval, cudaStream_t st)
+{
+    const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * (PW ? g->d.nflav : 1) * 4;
     if (nbins64 >= (int64_t)1 << 30) return fail(PDF_E_RANGE, "grid too large for the sorted adjoint");
     const int nbins = (int)nbins64;
     // points per round of count, records and accumulation ($PDFGPU_SORT_CHUNK
@@ -433,7 +697,7 @@ int backward_sorted(pdfgpu_grid *g, int member, const int *pid, const double *x,
     int *offs = (int *)(base + brec + btape + bbins);
     int *cursor = (int *)(base + brec + btape + 2 * bbins);
     const size_t hsmem = nbins <= kMaxSmemBins ? (size_t)nbins * sizeof(int) : 0;
-    int rc = allow_dynamic_smem((const void *)k_bwd_count, hsmem);
+    int rc = allow_dynamic_smem((const void *)k_bwd_count<PW>, hsmem);
     if (rc) return rc;
     for (int64_t i0 = 0; i0 < n; i0 += chunk) {
         const int m = (int)std::min(chunk, n - i0);
@@ -445,16 +709,23 @@ int backward_sorted(pdfgpu_grid *g, int member, const int *pid, const double *x,
         }
         PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
         const int gc = std::min(g->sm_count, std::max(1, (m + kCountIlp * kCountBlock - 1) / (kCountIlp * kCountBlock)));
-        k_bwd_count<<<gc, kCountBlock, hsmem, st>>>(g->d, pid, tv, i0, m, hist, nbins);
+        k_bwd_count<PW><<<gc, kCountBlock, hsmem, st>>>(g->d, pid, tv, i0, m, hist, nbins);
         PDF_CUDA(cudaGetLastError());
         rc = exclusive_scan(hist, nbins, offs, cursor, st);
         if (rc) return rc;
-        k_bwd_rec<<<wave_grid(g, (const void *)k_bwd_rec, kBlock, 0, m), kBlock, 0, st>>>(
-            g->d, member, pid, x, q2, i0, m, tv, gout, gx, gq, gval, nbins, cursor, rec);
-        PDF_CUDA(cudaGetLastError());
         const int64_t warps = (m + kSegment - 1) / kSegment;
         const int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
-        k_bwd_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, rec, offs, nbins, gval);
+        if constexpr (PW) {
+            k_bwd_rec<<<wave_grid(g, (const void *)k_bwd_rec, kBlock, 0, m), kBlock, 0, st>>>(
+                g->d, member, pid, x, q2, i0, m, tv, gout, gx, gq, gval, nbins, cursor, rec);
+            PDF_CUDA(cudaGetLastError());
+            k_bwd_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, rec, offs, nbins, gval);
+        } else {
+            k_bwd_rec_m<<<wave_grid(g, (const void *)k_bwd_rec_m, kBlock, 0, m), kBlock, 0, st>>>(
+                g->d, cols, npid, member, x, q2, i0, m, tv, gout, gx, gq, gval, nbins, cursor, rec);
+            PDF_CUDA(cudaGetLastError());
+            k_bwd_accum_m<<<blocks, kAccWarps * 32, 0, st>>>(g->d, cols, npid, rec, offs, nbins, gout, gval);
+        }
         PDF_CUDA(cudaGetLastError());
     }
     return PDF_OK;
@@ -465,9 +736,8 @@ int launch(pdfgpu_grid *g, const Cols &cols, int npid, int member, const int *pi
            const double *q2, int64_t n, const double *tape, const double *gout, double *gx, double *gq,
            double *gval, cudaStream_t s)
 {
-    if constexpr (PW) {
-        if (gval) return backward_sorted(g, member, pid, x, q2, n, tape, gout, gx, gq, gval, s);
-    }
+    if (gval && (PW || npid <= kMaxSortedPids))
+        return backward_sorted<PW>(g, member, cols, npid, pid, x, q2, n, tape, gout, gx, gq, gval, s);
     size_t gbytes = (size_t)g->d.nrows * g->d.nx * g->d.nflav * sizeof(double);
     if constexpr (!PW) {
         if (gval && gbytes <= kSmemGradMax) {

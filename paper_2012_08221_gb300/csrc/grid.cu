@@ -151,13 +151,27 @@ static void make_log_tables(std::vector<LogEntry> &tab, std::vector<double2> &et
 // assembled into M[m][i]: monomial coefficient m of the interval cubic in
 // t = (z - z_k)/dz_k from stencil value i (i <-> knot k-1+i).  With `linear`
 // the interval polynomial is the straight line between its two knots.
-static void cell_matrix(const double *z, int n, int k, double M[16], bool linear)
+//
+// In Hermite form the weights are W(t) = e_k h00(t) + P h10(t) + e_k+1 h01(t)
+// + Q h11(t), with P = (p0, p1, p2, 0), Q = (0, q0, q1, q2) and e_k, e_k+1
+// the unit rows of the cell's two knots.  Ms is the same cubic as a
+// polynomial in s = 1 - t (the distance to the upper knot): with
+// h00(t) = h01(s), h01(t) = h00(s), h10(t) = -h11(s), h11(t) = -h10(s),
+//   W = e_k+1 h00(s) + e_k h01(s) - P h11(s) - Q h10(s),
+// so that its constant and linear rows are exact (e_k+1 and -Q): near the
+// upper knot the weights that vanish there come out of small powers of s,
+// not of a cancellation between the rows of M.
+static void cell_matrix(const double *z, int n, int k, double M[16], bool linear, double Ms[16])
 {
     if (linear) {
         // straight line between the interval's two knots: c0 = g_k, c1 = g_{k+1} - g_k
         const double m[16] = {0.0, 1.0, 0.0, 0.0, 0.0, -1.0, 1.0, 0.0,
                               0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        // in s: g_{k+1} + s (g_k - g_{k+1})
+        const double ms[16] = {0.0, 0.0, 1.0, 0.0, 0.0, 1.0, -1.0, 0.0,
+                               0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         memcpy(M, m, sizeof(m));
+        memcpy(Ms, ms, sizeof(ms));
         return;
     }
     double dz = z[k + 1] - z[k];
@@ -180,6 +194,14 @@ static void cell_matrix(const double *z, int n, int k, double M[16], bool linear
         -2.0 * p0, -3.0 - 2.0 * p1 - q0, 3.0 - 2.0 * p2 - q1, -q2,
         p0, 2.0 + p1 + q0, -2.0 + p2 + q1, q2};
     memcpy(M, m, sizeof(m));
+    // h00(s) = 1 - 3s^2 + 2s^3, h01(s) = 3s^2 - 2s^3, h10(s) = s - 2s^2 + s^3,
+    // h11(s) = -s^2 + s^3
+    const double ms[16] = {
+        0.0, 0.0, 1.0, 0.0,
+        0.0, -q0, -q1, -q2,
+        p0, 3.0 + p1 + 2.0 * q0, -3.0 + p2 + 2.0 * q1, 2.0 * q2,
+        -p0, -2.0 - p1 - q0, 2.0 - p2 - q1, -q2};
+    memcpy(Ms, ms, sizeof(ms));
 }
 
 static int largest_pow2_below(int n)
@@ -379,18 +401,18 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     std::vector<uint64_t> xbits(nxc);
     std::vector<int64_t> ukey(nxc);
     std::vector<double2> xcell(nxc);
-    std::vector<double> mx((size_t)nxc * 16);
+    std::vector<double> mx((size_t)nxc * 16), mxs((size_t)nxc * 16);
     for (int k = 0; k < nxc; ++k) {
         xbits[k] = dbits(D.x_knots[k]);
         ukey[k] = dkey(g->U[k]);
         xcell[k] = make_double2(g->U[k], 1.0 / (g->U[k + 1] - g->U[k]));
-        cell_matrix(g->U.data(), nx, k, &mx[(size_t)k * 16], x_linear);
+        cell_matrix(g->U.data(), nx, k, &mx[(size_t)k * 16], x_linear, &mxs[(size_t)k * 16]);
     }
     // Q cells, subgrid by subgrid
     std::vector<uint64_t> qbits;
     std::vector<int64_t> wkey;
     std::vector<double2> qcell;
-    std::vector<double> mq;
+    std::vector<double> mq, mqs;
     std::vector<int> qrow, qmask;
     {
         int r0 = 0;
@@ -405,11 +427,12 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
                 qbits.push_back(dbits(Q2[r0 + j]));
                 wkey.push_back(dkey(Ws[j]));
                 qcell.push_back(make_double2(Ws[j], 1.0 / (Ws[j + 1] - Ws[j])));
-                double M[16];
+                double M[16], Ms[16];
                 const bool q_linear = D.interp == PDF_INTERP_LOGBILINEAR ||
                                       (D.interp == PDF_INTERP_LOGBICUBIC_SMALL_LINEAR && n < 4);
-                cell_matrix(Ws, n, j, M, q_linear);
+                cell_matrix(Ws, n, j, M, q_linear, Ms);
                 mq.insert(mq.end(), M, M + 16);
+                mqs.insert(mqs.end(), Ms, Ms + 16);
                 qrow.push_back(r0 + j);
                 int mask = 0x6 | (j > 0 ? 0x1 : 0) | (j + 2 <= n - 1 ? 0x8 : 0);
                 qmask.push_back(mask);
@@ -461,6 +484,8 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     TRY(dev_upload(g, etab.data(), etab.size(), &d.etab));
     TRY(dev_upload(g, mx.data(), mx.size(), &d.mx));
     TRY(dev_upload(g, mq.data(), mq.size(), &d.mq));
+    TRY(dev_upload(g, mxs.data(), mxs.size(), &d.mxs));
+    TRY(dev_upload(g, mqs.data(), mqs.size(), &d.mqs));
     TRY(dev_upload(g, qrow.data(), qrow.size(), &d.qrow));
     TRY(dev_upload(g, qmask.data(), qmask.size(), &d.qmask));
     TRY(dev_upload(g, pidmap.data(), pidmap.size(), &d.pidmap));

@@ -119,6 +119,8 @@ struct GridDev {
     const double *acoef;     // [nqc][4] alpha_s cubic in tq, or null
     const double *mx;        // [nxc][16] stencil -> monomial matrix M[m][i]
     const double *mq;        // [nqc][16]
+    const double *mxs;       // [nxc][16] the same in powers of s = 1 - t
+    const double *mqs;       // [nqc][16]
     const int *qrow;         // [nqc] grid row of each Q cell's lower knot
     const int *qmask;        // [nqc] bit i (0..3): stencil row i-1 exists
     const signed char *pidmap;  // [129] column of pid in [-64, 64], -1 absent
@@ -490,15 +492,6 @@ __device__ __forceinline__ bool tape_get(const GridDev &g, const double *__restr
     make_basis(X, r.x, g.extrap);
     make_basis(Q, r.y, g.extrap);
     return bad;
-}
-
-// Only the cells and flags of point i's tape record (a 16-byte load): the
-// axes' cells and range flags, without local coordinates.
-__device__ __forceinline__ bool tape_get_cells(const GridDev &g, const double *__restrict__ tape, int64_t i,
-                                               Axis &X, Axis &Q)
-{
-    const double2 r = __ldg(reinterpret_cast<const double2 *>(tape + 4 * i + 2));
-    return tape_decode(g, r.x, r.y, X, Q);
 }
 
 __device__ __forceinline__ int pid_col(const GridDev &g, int pid)

@@ -10,8 +10,6 @@ Per point of the x*f kernel with F flavours:
   2 logs x 15 flops (1 FMA reduction, 4 FMA series, 1 multiply, 4 adds),
   2 axes x (subtract, multiply) for t, 15 FMA per flavour for the
   16-coefficient patch by Horner's rule:  34 + 30 F flops.
-The adjoint's derivative and stencil weights use the powers t^2, t^3 of
-each axis (2 more multiplies per axis).
 """
 from __future__ import annotations
 
@@ -54,28 +52,31 @@ def pw_fwd_point_flops() -> int:
 PW_FWD_POINT_BYTES = 28                # x, Q^2, pid, out
 
 
-def pw_bwd_point_flops() -> int:
-    """Adjoint of one pointwise point: recomputed coordinates (2 logs, t,
-    bases), derivative bases (2 multiplies per axis for 2t, 3t^2), patch
-    value-derivatives (12 FMA for the x rows, 8 for their tx-derivatives,
-    3 + 2 for the tq sums), 2 FMA for the weighted sums, stencil weights of
-    both axes (2 x 12 FMA), 4 + 16 multiplies for the 16 cell weights, the
-    16 adds that sum them into the gradient of the grid values, and the
-    chain rule to x and Q^2 (2 x 2 multiplies and a reciprocal)."""
-    coords = 2 * LOG_FLOPS + 2 * (AXIS_FLOPS + POWER_FLOPS)
-    return coords + 4 + 2 * (12 + 8 + 3 + 2) + 4 + 2 * 2 * 12 + 20 + 16 + 2 * 2 + 2 * 4
-
-
 PW_BWD_POINT_BYTES = 44                # grad_out, x, Q^2, pid in; dx, dQ^2 out
 
 
-def pw_bwd_tape_point_flops() -> int:
-    """The same adjoint from the forward pass's tape: the two logs and the
-    two t are read back instead of recomputed."""
-    return pw_bwd_point_flops() - 2 * LOG_FLOPS - 2 * AXIS_FLOPS
-
-
 TAPE_POINT_BYTES = 32                  # written by the forward, read by the adjoint
+
+
+def pw_bwd_sorted_point_flops() -> int:
+    """The pointwise adjoint as the kernels now run it (from the tape, grid
+    gradient sorted by (cell, flavour)).  Record pass: the patch's tx- and
+    tq-derivatives by Horner's rule (4 rows x (3 + 2) FMA, then 3 + 2 FMA:
+    25 FMA), the derivative bases (2t by an add, 3t^2 by 2 multiplies, per
+    axis), and the chain rule to x and Q^2 (3 multiplies and a reciprocal
+    each).  Accumulation: g times the Q basis and the x basis (6
+    multiplies) and the 16 FMAs of g bq_n bx_m.  The map back to the stencil
+    values (20 FMA per lane per bin run) is per bin, not per point, and is
+    not counted."""
+    record = 2 * 25 + 2 * 3 + 2 * 4
+    accumulate = 6 + 2 * 16
+    return record + accumulate
+
+
+def pw_fwd_bwd_point_flops_survey() -> int:
+    """The forward plus backward work of one pointwise point in the
+    separable-weight count of the method (forward 90, backward about 170)."""
+    return 260
 
 
 def lumi_event_flops(n_flav: int) -> int:

@@ -387,3 +387,40 @@ def test_tape_arguments_are_checked():
     from paper_2012_08221_gb300.autograd import xfxQ2 as ad_xfxQ2
     vals = torch.tensor(g.values, device="cuda", requires_grad=True)
     assert torch.equal(ad_xfxQ2(pc, vals, g.pids, X, Q), pc.xfxQ2(g.pids, X, Q))
+
+
+@pytest.mark.parametrize("n_pid", [1, 3, 16, 17])
+def test_matrix_grid_gradient_sorted_and_beyond_16_columns(n_pid):
+    """The matrix form's grid gradient: up to 16 columns the points are
+    sorted by cell and every column accumulates in the same bin; beyond 16
+    the weights are scattered with atomics.  Columns include an absent pid
+    and the gluon twice (0 and 21, both adding to one column); points on
+    every side of the grid and at knots; with and without the tape."""
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_small(seed=1003, pids=synth.PIDS_13)
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    base = [0, 21, 9, -3, 2, 5] + list(synth.PIDS_13)
+    pids = np.array((base * 2)[:n_pid], dtype=np.int32)
+    _, x, q2, _ = _pw_points_with_edges(g, 8_003, 49)
+    gout = np.random.default_rng(50).standard_normal((x.size, pids.size))
+    X, Q = cuda(x), cuda(q2)
+    T = pdf.new_tape(x.size)
+    pdf.xfxQ2(pids, X, Q, tape=T)
+    ref = o.dgrid(pids, x, q2, gout)
+    mag = o.dgrid(pids, x, q2, gout, absval=True)
+    rdx = np.zeros(x.size)
+    rdq = np.zeros(x.size)
+    for p in range(pids.size):
+        dx, dq = o.grad_pw(np.full(x.size, pids[p]), x, q2)
+        rdx += gout[:, p] * dx
+        rdq += gout[:, p] * dq
+    kap = o.kappa(pids, x, q2).sum(axis=1) + 1e-6 * np.max(np.abs(g.values)) * pids.size
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    gs = np.abs(gout).max(axis=1)
+    for tape in (None, T):
+        gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+        gx, gq, _ = pdf.xfxQ2_backward(pids, X, Q, cuda(gout), grad_values=gv, tape=tape)
+        _check(gv.cpu().numpy(), ref, mag, f"matrix dL/dvalues, {n_pid} columns",
+               floor=1e-14 * np.abs(gout).sum())
+        _check(gx.cpu().numpy(), rdx, gs * 4 * kap / (np.min(np.diff(U)) * x), "matrix dL/dx")
+        _check(gq.cpu().numpy(), rdq, gs * 4 * kap / (np.min(np.diff(W)) * q2), "matrix dL/dQ2")
