@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
         double Wx[4], Wq[4];
         int qmask = 0, r0 = 0, k0 = 0;
         if (gval) {
-            stencil_weights(g.mx + (size_t)X.cell * 16, X, Wx);
-            stencil_weights(g.mq + (size_t)Q.cell * 16, Q, Wq);
+            stencil_weights(g.mx + (size_t)X.cell * 16, g.mxs + (size_t)X.cell * 16, X, Wx);
+            stencil_weights(g.mq + (size_t)Q.cell * 16, g.mqs + (size_t)Q.cell * 16, Q, Wq);
             qmask = g.qmask[Q.cell];
             r0 = g.qrow[Q.cell] - 1;
             k0 = X.cell - 1;
@@ -315,8 +315,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const
         }
         if (!(X.in && Q.in)) {
             double Wx[4], Wq[4];
-            stencil_weights(g.mx + (size_t)X.cell * 16, X, Wx);
-            stencil_weights(g.mq + (size_t)Q.cell * 16, Q, Wq);
+            stencil_weights(g.mx + (size_t)X.cell * 16, g.mxs + (size_t)X.cell * 16, X, Wx);
+            stencil_weights(g.mq + (size_t)Q.cell * 16, g.mqs + (size_t)Q.cell * 16, Q, Wq);
             const int qmask = g.qmask[Q.cell], r0 = g.qrow[Q.cell] - 1, k0 = X.cell - 1;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -515,8 +515,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec_m(GridDev g, Cols cols, int 
         }
         if (!(X.in && Q.in)) {
             double Wx[4], Wq[4];
-            stencil_weights(g.mx + (size_t)X.cell * 16, X, Wx);
-            stencil_weights(g.mq + (size_t)Q.cell * 16, Q, Wq);
+            stencil_weights(g.mx + (size_t)X.cell * 16, g.mxs + (size_t)X.cell * 16, X, Wx);
+            stencil_weights(g.mq + (size_t)Q.cell * 16, g.mqs + (size_t)Q.cell * 16, Q, Wq);
             const int qmask = g.qmask[Q.cell], r0 = g.qrow[Q.cell] - 1, k0 = X.cell - 1;
             for (int a = 0; a < npid; ++a) {
                 int col = scol[a];

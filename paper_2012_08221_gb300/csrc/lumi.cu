@@ -342,8 +342,8 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
             Axis Q = axis_from(qc, tq[e], f & 1);
             Axis X = axis_from(xc, tx[rec], (f >> 1) & 1);
             double Wq[4], Wx[4];
-            stencil_weights(g.mq + (size_t)qc * 16, Q, Wq);
-            stencil_weights(g.mx + (size_t)xc * 16, X, Wx);
+            stencil_weights(g.mq + (size_t)qc * 16, g.mqs + (size_t)qc * 16, Q, Wq);
+            stencil_weights(g.mx + (size_t)xc * 16, g.mxs + (size_t)xc * 16, X, Wx);
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj)
 #pragma unroll

@@ -363,22 +363,30 @@ __device__ __forceinline__ void patch_d_horner(const double *__restrict__ C, con
     *dtq = fma(tq3, i[3], fma(tq2, i[2], i[1]));
 }
 
-// Stencil weights W_i = sum_m M[m][i] b_m of one axis (i <-> knot cell-1+i);
-// outside the knot range the exact weights of the linear continuation.
-__device__ __forceinline__ void stencil_weights(const double *__restrict__ M, const Axis &A, double W[4])
+// Stencil weights of one axis (i <-> knot cell-1+i): W_i = sum_m M[m][i] t^m
+// in the lower half of the cell, sum_m Ms[m][i] s^m with s = 1 - t in the
+// upper half (Ms: the cell's matrix in powers of s), so that a weight that
+// vanishes at the near knot comes out of small powers, not of cancelling
+// ones.  Outside the knot range the exact weights of the linear
+// continuation, (1 - t, t) on the cell's two knots.
+__device__ __forceinline__ void stencil_weights(const double *__restrict__ M, const double *__restrict__ Ms,
+                                                const Axis &A, double W[4])
 {
-    D4 r0 = ld4(M), r1 = ld4(M + 4), r2 = ld4(M + 8), r3 = ld4(M + 12);
-    W[0] = fma(A.b3, r3.x, fma(A.b2, r2.x, fma(A.t, r1.x, r0.x)));
-    W[1] = fma(A.b3, r3.y, fma(A.b2, r2.y, fma(A.t, r1.y, r0.y)));
-    W[2] = fma(A.b3, r3.z, fma(A.b2, r2.z, fma(A.t, r1.z, r0.z)));
-    W[3] = fma(A.b3, r3.w, fma(A.b2, r2.w, fma(A.t, r1.w, r0.w)));
     if (!A.in) {
-        // linear continuation: exactly (1 - t, t) on the cell's two knots
         W[0] = 0.0;
         W[1] = 1.0 - A.t;
         W[2] = A.t;
         W[3] = 0.0;
+        return;
     }
+    const bool up = dbits(A.t) > 0x3FE0000000000000ull;   // t > 1/2 (t >= 0 inside)
+    const double *P = up ? Ms : M;
+    const double z = up ? 1.0 - A.t : A.t, z2 = z * z, z3 = z2 * z;
+    D4 r0 = ld4(P), r1 = ld4(P + 4), r2 = ld4(P + 8), r3 = ld4(P + 12);
+    W[0] = fma(z3, r3.x, fma(z2, r2.x, fma(z, r1.x, r0.x)));
+    W[1] = fma(z3, r3.y, fma(z2, r2.y, fma(z, r1.y, r0.y)));
+    W[2] = fma(z3, r3.z, fma(z2, r2.z, fma(z, r1.z, r0.z)));
+    W[3] = fma(z3, r3.w, fma(z2, r2.w, fma(z, r1.w, r0.w)));
 }
 
 // Bulk copy (TMA engine) of `bytes` from shared to global memory: both
