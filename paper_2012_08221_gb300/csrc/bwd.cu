@@ -154,6 +154,8 @@ constexpr int kCountBlock = 1024;         // one such block per SM counts
 constexpr int kCountIlp = 4;
 constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;            // sorted points per warp of the accumulation
+constexpr int kSegmentM = 128;            // the same for the matrix form (npid FMAs per point
+                                          // and lane: shorter runs keep enough warps busy)
 constexpr int64_t kSortChunk = (int64_t)1 << 24;
 
 // Sorted record of one point (32 bytes): t of the x axis, t of the Q axis
@@ -573,9 +575,9 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum_m(GridDev g, Cols 
     const int F = g.nflav;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int nvalid = offs[nbins];
-    const int64_t wbeg = ((int64_t)blockIdx.x * kAccWarps + wid) * kSegment;
+    const int64_t wbeg = ((int64_t)blockIdx.x * kAccWarps + wid) * kSegmentM;
     if (wbeg >= nvalid) return;
-    const int wend = (int)min((int64_t)nvalid, wbeg + kSegment);
+    const int wend = (int)min((int64_t)nvalid, wbeg + kSegmentM);
     const int h = lane >> 4, s = lane & 15, sn = s >> 2, sm = s & 3;
     const unsigned hmask = 0xFFFFu << (16 * h);
     const int half = (wend - (int)wbeg + 1) / 2;
@@ -713,7 +715,8 @@ int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, cons
         PDF_CUDA(cudaGetLastError());
         rc = exclusive_scan(hist, nbins, offs, cursor, st);
         if (rc) return rc;
-        const int64_t warps = (m + kSegment - 1) / kSegment;
+        const int seg = PW ? kSegment : kSegmentM;
+        const int64_t warps = (m + seg - 1) / seg;
         const int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
         if constexpr (PW) {
             k_bwd_rec<<<wave_grid(g, (const void *)k_bwd_rec, kBlock, 0, m), kBlock, 0, st>>>(

@@ -424,3 +424,41 @@ def test_matrix_grid_gradient_sorted_and_beyond_16_columns(n_pid):
                floor=1e-14 * np.abs(gout).sum())
         _check(gx.cpu().numpy(), rdx, gs * 4 * kap / (np.min(np.diff(U)) * x), "matrix dL/dx")
         _check(gq.cpu().numpy(), rdq, gs * 4 * kap / (np.min(np.diff(W)) * q2), "matrix dL/dQ2")
+
+
+def test_grid_gradient_near_the_knots_is_accurate():
+    """Points a little below a knot (t = 1 - 1e-3 ... 1 - 1e-4) and a little
+    above one (t = 1e-3 ... 1e-4) on both axes, each alone in its cell: the
+    stencil weights that vanish at the near knot are of order (1 - t)^2 or
+    t^2 there (powers of t alone would lose 15 ulp / (1 - t)^2 of them, over
+    1e-9 below t = 1 - 1e-3).  Both the pointwise and the matrix form must
+    match the oracle's gradient within 1e-9 of each value's own term scale,
+    with no absolute floor.  (Closer to a knot the rounding of t itself,
+    about 1e-15 between the two sides' logarithms, moves such a weight by
+    more than 1e-9 of itself.)"""
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_small(seed=1003, pids=synth.PIDS_13)
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    us, ws = [], []
+    for k, d in enumerate([1e-3, 5e-4, 2e-4, 1e-4]):
+        for lo in (False, True):
+            kx, kq = 3 + 7 * k + (0 if lo else 3), 2 + 3 * k
+            tx = d if lo else 1.0 - d
+            tq = 1.0 - d if lo else d
+            us.append(U[kx] + tx * (U[kx + 1] - U[kx]))
+            ws.append(W[kq] + tq * (W[kq + 1] - W[kq]))
+    x, q2 = np.exp(np.array(us)), np.exp(np.array(ws))
+    rng = np.random.default_rng(60)
+    pid = g.pids[rng.integers(0, g.n_flav, x.size)].astype(np.int32)
+    w = rng.standard_normal(x.size)
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    pdf.xfxQ2_backward(cuda(pid), cuda(x), cuda(q2), cuda(w), pointwise=True, grad_values=gv)
+    _check(gv.cpu().numpy(), o.dgrid_pw(pid, x, q2, w), o.dgrid_pw(pid, x, q2, w, absval=True),
+           "pointwise dL/dvalues near knots")
+    pids = np.array([-2, 0, 3], dtype=np.int32)
+    gout = rng.standard_normal((x.size, pids.size))
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    pdf.xfxQ2_backward(pids, cuda(x), cuda(q2), cuda(gout), grad_values=gv)
+    _check(gv.cpu().numpy(), o.dgrid(pids, x, q2, gout), o.dgrid(pids, x, q2, gout, absval=True),
+           "matrix dL/dvalues near knots")
