@@ -340,15 +340,37 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const
     }
 }
 
+// Maps a half-warp's 16 accumulators back to the 16 stencil values of their
+// bin.  Lane 4n + m passes G[n][m] in g; lane 4j + i gets
+// sum_{n,m} Mq[n][j] G[n][m] Mx[m][i], in two stages through the half-warp's
+// 16 shared slots buf: T[j][m] = sum_n Mq[n][j] G[n][m] (lane 4j + m), then
+// sum_m T[j][m] Mx[m][i] -- 8 FMAs per lane.
+__device__ __forceinline__ double map_back(double g, double *buf, const double *__restrict__ Mq,
+                                           const double *__restrict__ Mx, int sn, int sm, unsigned hmask)
+{
+    buf[4 * sn + sm] = g;
+    __syncwarp(hmask);
+    double t = 0.0;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) t = fma(Mq[n * 4 + sn], buf[4 * n + sm], t);
+    __syncwarp(hmask);
+    buf[4 * sn + sm] = t;
+    __syncwarp(hmask);
+    double dv = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) dv = fma(buf[4 * sn + m], Mx[m * 4 + sm], dv);
+    __syncwarp(hmask);
+    return dv;
+}
+
 // Accumulation over the sorted records.  Each warp takes a segment of
 // kSegment records and each half-warp half of it, in steps of 16: lane s of
 // the half stages record p + s (g times the Q basis, and the x basis) in
 // shared memory, then, for each of the 16 staged records in order, lane
 // s = 4 n + m adds g bq_n bx_m to its accumulator G[n][m] of the current
 // bin (one FMA).  When the bin changes the half-warp maps its 16
-// accumulators back to the 16 stencil values, lane (j, i) computing
-// sum_n,m Mq[n][j] G[n][m] Mx[m][i] and adding it to the gradient with one
-// atomic.
+// accumulators back to the 16 stencil values (map_back), each lane adding
+// its value to the gradient with one atomic.
 __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum(GridDev g, const double *__restrict__ rec,
                                                               const int *__restrict__ offs, int nbins,
                                                               double *__restrict__ gval)
@@ -371,23 +393,12 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum(GridDev g, const d
     double acc = 0.0;
     int cur = -1;
     auto flush = [&](int b) {
-        sG[wid][row0 + s] = acc;
-        acc = 0.0;
-        __syncwarp(hmask);
         const int cb = b >> 2, cell = cb / F, col = cb - cell * F;
         const int qc = cell / g.nxc, xc = cell - qc * g.nxc;
         const double *Mq = ((b & 2) ? g.mqs : g.mq) + (size_t)qc * 16;
         const double *Mx = ((b & 1) ? g.mxs : g.mx) + (size_t)xc * 16;
-        // lane (j, i) = (sn, sm)
-        double dv = 0.0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            double hm = 0.0;
-#pragma unroll
-            for (int n = 0; n < 4; ++n) hm = fma(Mq[n * 4 + sn], sG[wid][row0 + n * 4 + m], hm);
-            dv = fma(hm, Mx[m * 4 + sm], dv);
-        }
-        __syncwarp(hmask);
+        const double dv = map_back(acc, &sG[wid][row0], Mq, Mx, sn, sm, hmask);   // lane (j, i) = (sn, sm)
+        acc = 0.0;
         const int kk = xc - 1 + sm;
         if (((g.qmask[qc] >> sn) & 1) && kk >= 0 && kk < g.nx && (dbits(dv) << 1)) {
             const int row = checked_index(g.status, g.qrow[qc] - 1 + sn, g.nrows);
@@ -598,17 +609,7 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum_m(GridDev g, Cols 
 #pragma unroll
         for (int a = 0; a < kMaxSortedPids; ++a) {
             if (a < npid && scol[a] >= 0) {
-                sG[wid][row0 + s] = acc[a];
-                __syncwarp(hmask);
-                double dv = 0.0;
-#pragma unroll
-                for (int mm = 0; mm < 4; ++mm) {
-                    double hm = 0.0;
-#pragma unroll
-                    for (int n = 0; n < 4; ++n) hm = fma(Mq[n * 4 + sn], sG[wid][row0 + n * 4 + mm], hm);
-                    dv = fma(hm, Mx[mm * 4 + sm], dv);
-                }
-                __syncwarp(hmask);
+                const double dv = map_back(acc[a], &sG[wid][row0], Mq, Mx, sn, sm, hmask);
                 if (ok && (dbits(dv) << 1)) {
                     const int col = checked_index(g.status, scol[a], F);
                     atomicAdd(gval + ((size_t)row * g.nx + kk) * F + col, dv);
