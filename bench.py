@@ -647,7 +647,8 @@ def main():
                                 "survey_fwd_bwd": work.pw_fwd_bwd_point_flops_survey()},
             "bwd_kernel": {"kernels": "k_bwd_count, k_scan, k_bwd_rec, k_bwd_accum (from the tape; grid "
                                       "gradient sorted by cell and flavour)", "ms": kb,
-                           "frac": n3 * work.pw_bwd_sorted_point_flops() / (kb * 1e-3) / peak},
+                           "frac": n3 * work.pw_bwd_sorted_point_flops() / (kb * 1e-3) / peak,
+                           "frac_survey_count": n3 * work.pw_bwd_point_flops_survey() / (kb * 1e-3) / peak},
             "tape": "the forward pass writes 32 bytes per point (cells, local coordinates, flags) that the "
                     "adjoint reads instead of searching the knots and taking logarithms again",
             "direct_calls": {"ms_per_step": ms3, "value": world * n3 / (ms3 * 1e-3),

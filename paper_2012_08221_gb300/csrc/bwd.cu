@@ -175,10 +175,8 @@ __device__ __forceinline__ void put_rec(double *__restrict__ rec, int pos, doubl
 // s = 1 - t (and maps back with the cell's matrix in s), so that the weights
 // that vanish at the near knot come out of small powers, not of cancelling
 // ones: a bin holds the points of one cell (and flavour) and one half pair.
-// (Inside the knot range t lies in [0, 1], so t > 1/2 is an integer compare
-// of its bit pattern, which keeps the FP64 pipe free.)
-__device__ __forceinline__ bool upper_half(double t) { return dbits(t) > 0x3FE0000000000000ull; }
-
+// (The tape records the same two bits, from the same t, for the counting
+// pass.)
 __device__ __forceinline__ int half_pair(const Axis &X, const Axis &Q)
 {
     return (upper_half(X.t) ? 1 : 0) | (upper_half(Q.t) ? 2 : 0);
@@ -195,19 +193,20 @@ __device__ __forceinline__ double near_coord(double t) { return upper_half(t) ? 
 // record pass both decide through this one function, on the same tape
 // values, so that every record placed was counted.
 __device__ __forceinline__ int sorted_bin(const GridDev &g, const Axis &X, const Axis &Q, bool bad, int col,
-                                          int nbins)
+                                          int halves, int nbins)
 {
     if (bad || col < 0 || !(X.in && Q.in)) return -1;
-    return checked_index(g.status, ((Q.cell * g.nxc + X.cell) * g.nflav + col) * 4 + half_pair(X, Q), nbins);
+    return checked_index(g.status, ((Q.cell * g.nxc + X.cell) * g.nflav + col) * 4 + halves, nbins);
 }
 
 // Bin of a point in the matrix form's sorted accumulation: its cell and
 // half pair (all the call's flavours accumulate together), (cell * 4 + half
 // pair), or -1 as for sorted_bin.
-__device__ __forceinline__ int sorted_cell(const GridDev &g, const Axis &X, const Axis &Q, bool bad, int nbins)
+__device__ __forceinline__ int sorted_cell(const GridDev &g, const Axis &X, const Axis &Q, bool bad, int halves,
+                                           int nbins)
 {
     if (bad || !(X.in && Q.in)) return -1;
-    return checked_index(g.status, (Q.cell * g.nxc + X.cell) * 4 + half_pair(X, Q), nbins);
+    return checked_index(g.status, (Q.cell * g.nxc + X.cell) * 4 + halves, nbins);
 }
 
 // Without a forward tape: the tape records of the chunk's points (domain
@@ -227,8 +226,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd_axes(GridDev g, const double *__
     }
 }
 
-// Histogram of the chunk's bins from the tape records and the pids (36 bytes
-// read per point, no FP64 work).  One block of kCountBlock threads
+// Histogram of the chunk's bins from the tape records' cells, flags and
+// halves and the pids (20 bytes read per point, no FP64 work).  One block of kCountBlock threads
 // per SM, so that flushing the shared-memory counters costs one pass over
 // the bins per SM, not per small block.  `tape` is the chunk's view.
 template <bool PW>
@@ -253,9 +252,10 @@ __global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int 
             b[u] = -1;
             if (k < m) {
                 Axis X, Q;
-                const bool bad = tape_get(g, tape, k, X, Q);
-                b[u] = PW ? sorted_bin(g, X, Q, bad, bad ? -1 : pid_col(g, pid[i0 + k]), nbins)
-                          : sorted_cell(g, X, Q, bad, nbins);
+                unsigned halves;
+                const bool bad = tape_get_cells(g, tape, k, X, Q, &halves);
+                b[u] = PW ? sorted_bin(g, X, Q, bad, bad ? -1 : pid_col(g, pid[i0 + k]), (int)halves, nbins)
+                          : sorted_cell(g, X, Q, bad, (int)halves, nbins);
             }
         }
 #pragma unroll
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const
             }
             continue;
         }
-        const int b = sorted_bin(g, X, Q, false, col, nbins);
+        const int b = sorted_bin(g, X, Q, false, col, half_pair(X, Q), nbins);
         put_rec(rec, atomicAdd(&cursor[b], 1), near_coord(X.t), near_coord(Q.t), ga, b, X.in, Q.in);
     }
 }
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec_m(GridDev g, Cols cols, int 
             }
             continue;
         }
-        const int b = sorted_cell(g, X, Q, false, nbins);
+        const int b = sorted_cell(g, X, Q, false, half_pair(X, Q), nbins);
         const int pos = atomicAdd(&cursor[b], 1);
         const uint64_t bits = (uint64_t)(uint32_t)b | ((uint64_t)X.in << 32) | ((uint64_t)Q.in << 33);
         double2 *d = reinterpret_cast<double2 *>(rec + 4 * (size_t)pos);

@@ -445,16 +445,21 @@ __device__ __forceinline__ bool out_of_range(const GridDev &g, const Axis &X, co
 //   [0] t of the x axis, [1] t of the Q axis (after make_basis),
 //   [2] bits: x cell (low 32) and Q cell (high 32),
 //   [3] bits: 1 x inside, 2 x below, 4 Q inside, 8 Q below, 16 bad point
-//       (domain error, or outside the grid under the error option).
+//       (domain error, or outside the grid under the error option), 32 t of
+//       the x axis above 1/2, 64 t of the Q axis above 1/2.
 // It depends on the points, the knots and the extrapolation option only (not
 // on the member or the values), so it stays valid across pdf_bind_values.
 constexpr unsigned kTapeBad = 16u;
+
+// t > 1/2 for a t in [0, 1] (inside the knot range), as an integer compare of
+// its bit pattern (which keeps the FP64 pipe free).
+__device__ __forceinline__ bool upper_half(double t) { return dbits(t) > 0x3FE0000000000000ull; }
 
 __device__ __forceinline__ void tape_put(double *__restrict__ tape, int64_t i, const Axis &X, const Axis &Q,
                                          bool bad)
 {
     const unsigned f = (X.in ? 1u : 0u) | (X.below ? 2u : 0u) | (Q.in ? 4u : 0u) | (Q.below ? 8u : 0u) |
-                       (bad ? kTapeBad : 0u);
+                       (bad ? kTapeBad : 0u) | (upper_half(X.t) ? 32u : 0u) | (upper_half(Q.t) ? 64u : 0u);
     double2 *d = reinterpret_cast<double2 *>(tape + 4 * i);
     d[0] = make_double2(X.t, Q.t);
     d[1] = make_double2(dfrom((uint64_t)(uint32_t)X.cell | ((uint64_t)(uint32_t)Q.cell << 32)),
@@ -477,7 +482,7 @@ __device__ __forceinline__ int tape_cell(unsigned *status, uint32_t v, int n)
 // Cells and range flags of a tape record from its second half (cells, flag
 // bits); returns whether the point is bad.
 __device__ __forceinline__ bool tape_decode(const GridDev &g, double cells_bits, double flag_bits, Axis &X,
-                                            Axis &Q)
+                                            Axis &Q, unsigned *halves = nullptr)
 {
     const uint64_t cells = dbits(cells_bits);
     const unsigned f = (unsigned)dbits(flag_bits);
@@ -487,7 +492,18 @@ __device__ __forceinline__ bool tape_decode(const GridDev &g, double cells_bits,
     X.below = f & 2u;
     Q.in = f & 4u;
     Q.below = f & 8u;
+    if (halves) *halves = (f >> 5) & 3u;
     return f & kTapeBad;
+}
+
+// Only the cells, range flags and halves (bit 0: t_x > 1/2, bit 1: t_q > 1/2)
+// of point i's tape record, from a 16-byte load; returns whether the point is
+// bad.
+__device__ __forceinline__ bool tape_get_cells(const GridDev &g, const double *__restrict__ tape, int64_t i,
+                                               Axis &X, Axis &Q, unsigned *halves)
+{
+    const double2 r = __ldg(reinterpret_cast<const double2 *>(tape + 4 * i + 2));
+    return tape_decode(g, r.x, r.y, X, Q, halves);
 }
 
 // Rebuilds the two axes of point i from its tape record; returns whether the
