@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int 
 // two knots, to the gradient here with global atomics (rare points; through
 // the monomial basis the two knots that carry no weight would receive
 // rounding-sized terms instead of zeros).
-__global__ void __launch_bounds__(kBlock) k_bwd_rec(GridDev g, int member, const int *__restrict__ pid,
+__global__ void __launch_bounds__(kBlock, 5) k_bwd_rec(GridDev g, int member, const int *__restrict__ pid,
                                                     const double *__restrict__ x,
                                                     const double *__restrict__ q2, int64_t i0, int m,
                                                     const double *__restrict__ tape,
