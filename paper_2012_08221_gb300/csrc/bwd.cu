@@ -14,19 +14,22 @@
 // instead of searching the knots and taking the two logarithms again; the
 // arithmetic that follows is the same.
 //
-// Grid gradient of the pointwise form (one flavour per point): the points
-// are counting-sorted by (cell, flavour) -- a counting pass over the tape's
-// cells (the forward's tape, or one made here), a scan, and the record pass
-// placing each point's record in its bin -- and the gradient is accumulated
-// per bin in the monomial basis of the patch,
+// Grid gradient: the points are counting-sorted into bins of one cell, one
+// flavour (pointwise form; the matrix form bins by cell and keeps every
+// column of the call in the same bin) and one half of the cell along each
+// axis -- a counting pass over the tape's cells (the forward's tape, or one
+// made here), a scan, and the record pass placing each point's record in its
+// bin -- and the gradient is accumulated per bin in the monomial basis of
+// the patch,
 //   G[n][m] = sum over the bin's points of g bq_n bx_m,
 // one FMA per term with no stencil weights, then mapped back to the 16
 // stencil values once per bin run: dL/dv[j][i] = sum_n,m Mq[n][j] G[n][m]
 // Mx[m][i] (the transpose of the map that builds the patch from the
-// values, so the result is the same derivative).  The matrix form (a shared
-// pid list) scatters the 16 stencil weights per flavour with FP64 atomics,
-// into a shared-memory copy per CTA when the member's gradient fits, or
-// straight into global memory.
+// values, so the result is the same derivative).  In the upper half of an
+// axis the basis is in powers of s = 1 - t, with the cell's matrix in s.
+// Beyond 16 columns the matrix form scatters the 16 stencil weights per
+// flavour with FP64 atomics, into a shared-memory copy per CTA when the
+// member's gradient fits, or straight into global memory.
 #include <math.h>
 #include <stdlib.h>
 

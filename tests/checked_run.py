@@ -53,6 +53,12 @@ def main():
             gxt, gqt, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
                                            pointwise=True, grad_values=gt, tape=T)
             res += [gxt, gqt]
+            # the matrix form's sorted adjoint (up to 16 columns)
+            gm = torch.zeros_like(gv)
+            pm = np.array([g.pids[0], 21, 9], dtype=np.int32)                  # 9: absent
+            gxm, gqm, _ = p.xfxQ2_backward(pm, X, Q, torch.ones((x.size, 3), dtype=torch.float64, device=dev),
+                                           member=1, grad_values=gm)
+            res += [gxm, gqm]
         ev = DeviceEvents.from_host(synth.events_lhc(50_001, seed=63))
         L, lum, als = luminosity(p, ev)
         res += [lum, als]
@@ -90,6 +96,11 @@ def main():
             gx, gq, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
                                          pointwise=True, grad_values=gv, tape=T)
             res += [gx, gq]
+            gm = torch.zeros_like(gv)
+            gxm, gqm, _ = p.xfxQ2_backward(gr.pids, X, Q,
+                                           torch.ones((x.size, gr.pids.size), dtype=torch.float64, device=dev),
+                                           grad_values=gm)
+            res += [gxm, gqm]
             if gr.pids.size <= 16:
                 ev = DeviceEvents.from_host(synth.events_lhc(5_001, seed=64 + seed))
                 L, lum, als = luminosity(p, ev)
