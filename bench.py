@@ -373,7 +373,7 @@ def main():
 
     from paper_2012_08221_gb300 import build, synth, work
     build.build()
-    from paper_2012_08221_gb300.pdf import PDF, fp64_peak
+    from paper_2012_08221_gb300.pdf import PDF, fp64_mixed, fp64_mma_peak, fp64_peak
 
     rank, world, local = env_rank()
     torch.cuda.set_device(local)
@@ -390,6 +390,8 @@ def main():
         return reduce_max(v, world, dev)
 
     probe = fp64_peak()                             # FLOP/s, FMA chains (burst)
+    mma_probe = {"m8n8k4_tflops": fp64_mma_peak("m8n8k4") / 1e12,
+                 **{k + "_tflops": v / 1e12 for k, v in fp64_mixed().items()}}
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak, peak_mhz = fp64_derived_peak(sms)
     stream = torch.cuda.current_stream(dev)
@@ -461,6 +463,11 @@ def main():
                                f"(max SM clock)",
                 "probe": {"value": probe / 1e12, "unit": "TFLOP/s",
                           "what": "FP64 FMA chains measured in this run (pdf_probe_fp64_peak)"},
+                "fp64_tensor_probe": {**mma_probe,
+                                      "what": "mma.sync f64 chains alone (pdf_probe_fp64_mma_peak), and equal "
+                                              "FP64 work as DFMA alone, DMMA alone and both interleaved in each "
+                                              "warp (pdf_probe_fp64_mixed): a mixed rate near the slower one, not "
+                                              "their sum, means one shared FP64 pipe"},
                 "traffic": traffic,
                 "ncu_fp64_pipe_active_pct": measured_pipe("k_xfxq2"),
                 "algorithmic_bytes": bytes_launch,

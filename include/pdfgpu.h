@@ -465,6 +465,14 @@ int pdf_probe_fp64_peak(double *flops);
  * leave the DFMA pipe of this GPU.  Synchronous. */
 int pdf_probe_fp64_mma_peak(int32_t shape, double *flops);
 
+/* Whether the FP64 tensor instruction runs beside the FMA pipe or on it: a
+ * kernel whose warps each issue equal FP64 work (in flops) as DFMA chains and
+ * as m8n8k4 mma.sync chains is timed with the DFMA half alone, the DMMA half
+ * alone, and both interleaved; the outputs are the three rates in FLOP/s.
+ * A mixed rate near the harmonic combination of the two (rather than their
+ * sum) says the two share one pipe.  Beyond the paper.  Synchronous. */
+int pdf_probe_fp64_mixed(double *dfma_flops, double *dmma_flops, double *mixed_flops);
+
 /* (Beyond the paper: a test hook.)  The kernels' natural log (table-driven argument reduction after
  * P. T. P. Tang, ACM TOMS 16 (1990) 378, with a degree-5 series for
  * ln(1+r), |r| <= 2^-11) applied to n DEVICE doubles: out[i] = ln(in[i]) for

@@ -85,6 +85,7 @@ SIGNATURES = {
     "pdf_lhapdf_close": [C.c_void_p],
     "pdf_probe_fp64_peak": [_D],
     "pdf_probe_fp64_mma_peak": [C.c_int32, _D],
+    "pdf_probe_fp64_mixed": [_D, _D, _D],
     "pdf_debug_log": [c_grid, _VP, C.c_int64, _VP, _VP],
 }
 

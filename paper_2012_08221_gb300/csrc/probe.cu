@@ -199,3 +199,97 @@ extern "C" int pdf_probe_fp64_mma_peak(int32_t shape, double *flops)
     cudaFree(buf);
     return rc;
 }
+
+// ------------------------------------------------- DFMA and DMMA in one warp
+//
+// Does the FP64 tensor instruction run beside the FMA pipe or on it?  Each
+// iteration issues, per warp, 64 DFMA per thread (8 rounds over 8 chains:
+// 4096 flops per warp) and 8 m8n8k4 DMMA (4096 flops per warp).  MODE 0
+// issues only the DFMA half, 1 only the DMMA half, 2 both, interleaved.  If
+// the two share one pipe the mixed kernel takes about the sum of the two
+// times; if they ran side by side it would take about the longer one.
+
+namespace {
+
+template <int MODE>
+__global__ void k_fp64_mixed(double *out, int iters, double b, double c)
+{
+    double f[kChains], acc[kChains][2];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) {
+        f[k] = threadIdx.x * 1e-3 + k;
+        acc[k][0] = k;
+        acc[k][1] = k + 0.5;
+    }
+    const double a = 1e-3 * threadIdx.x;
+    for (int it = 0; it < iters; ++it) {
+        if (MODE != 1) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int k = 0; k < kChains; ++k) f[k] = fma(f[k], b, c);
+        }
+        if (MODE != 0) {
+#pragma unroll
+            for (int k = 0; k < kChains; ++k) mma_f64<0>(acc[k], &a, &b);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) s += f[k] + acc[k][0] + acc[k][1];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <int MODE>
+int time_mixed(double *buf, int blocks, int block, float *ms_out)
+{
+    const int iters = 1024;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fp64_mixed<MODE><<<blocks, block>>>(buf, 16, 0.999, 1e-3);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0);
+        k_fp64_mixed<MODE><<<blocks, block>>>(buf, iters, 0.999, 1e-3);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+    }
+    cudaError_t err = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return pdfgpu::cuda_fail(err, "mixed probe kernel");
+    *ms_out = best;
+    return PDF_OK;
+}
+
+}  // namespace
+
+extern "C" int pdf_probe_fp64_mixed(double *dfma_flops, double *dmma_flops, double *mixed_flops)
+{
+    PDF_TRACE("pdf_probe_fp64_mixed");
+    pdfgpu::clear_error();
+    if (!dfma_flops || !dmma_flops || !mixed_flops) return pdfgpu::fail(PDF_E_ARG, "null output");
+    int dev = 0, sms = 0;
+    PDF_CUDA(cudaGetDevice(&dev));
+    PDF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int block = 256, per_sm = 4, iters = 1024;
+    const int blocks = sms * per_sm;
+    double *buf = nullptr;
+    int rc = pdfgpu::dev_malloc((void **)&buf, (size_t)blocks * block * sizeof(double), "probe buffer");
+    if (rc) return rc;
+    float ms[3] = {0, 0, 0};
+    rc = time_mixed<0>(buf, blocks, block, &ms[0]);
+    if (!rc) rc = time_mixed<1>(buf, blocks, block, &ms[1]);
+    if (!rc) rc = time_mixed<2>(buf, blocks, block, &ms[2]);
+    cudaFree(buf);
+    if (rc) return rc;
+    const double half = 4096.0 * iters * ((double)blocks * (block / 32));   // flops of one half
+    *dfma_flops = half / (ms[0] * 1e-3);
+    *dmma_flops = half / (ms[1] * 1e-3);
+    *mixed_flops = 2.0 * half / (ms[2] * 1e-3);
+    return PDF_OK;
+}

@@ -334,3 +334,12 @@ def fp64_mma_peak(shape: str = "m8n8k4") -> float:
     v = C.c_double()
     check("pdf_probe_fp64_mma_peak", lib().pdf_probe_fp64_mma_peak(MMA_SHAPES.index(shape), C.byref(v)))
     return v.value
+
+
+def fp64_mixed() -> dict:
+    """Rates (FLOP/s) of equal FP64 work issued as DFMA chains alone, as
+    m8n8k4 ``mma.sync`` chains alone, and as both interleaved in each warp;
+    a mixed rate well below the sum of the two says they share one pipe."""
+    f, m, x = C.c_double(), C.c_double(), C.c_double()
+    check("pdf_probe_fp64_mixed", lib().pdf_probe_fp64_mixed(C.byref(f), C.byref(m), C.byref(x)))
+    return {"dfma": f.value, "dmma": m.value, "mixed": x.value}

@@ -29,6 +29,11 @@ def _dgrid_chunk(args):
     return _oracle(grid_factory, kwargs).dgrid_pw(pid, x, q2, w, absval=absval)
 
 
+def _dgrid_matrix_chunk(args):
+    grid_factory, kwargs, pids, x, q2, gout, absval = args
+    return _oracle(grid_factory, kwargs).dgrid(pids, x, q2, gout, absval=absval)
+
+
 def workers(limit: int = 16) -> int:
     return max(1, min(limit, len(os.sched_getaffinity(0))))
 
@@ -55,4 +60,18 @@ def dgrid_pw_parallel(grid_factory: str, kwargs: dict, pid, x, q2, w, absval: bo
     jobs = [(grid_factory, kwargs, pid[p], x[p], q2[p], w[p], absval) for p in parts]
     with mp.get_context("spawn").Pool(n_workers) as pool:
         grads = pool.map(_dgrid_chunk, jobs)
+    return np.sum(np.stack(grads), axis=0)
+
+
+def dgrid_parallel(grid_factory: str, kwargs: dict, pids, x, q2, gout, absval: bool = False,
+                   n_workers: int | None = None) -> np.ndarray:
+    """The oracle's grid gradient of L = sum_i sum_a gout[i][a] xf_{pids[a]}(x_i, Q^2_i)
+    (the matrix form) over all points, chunked over ``n_workers`` processes
+    (member 0 of ``synth.<grid_factory>(**kwargs)``); with ``absval`` the sums
+    of |terms|."""
+    n_workers = n_workers or workers()
+    parts = np.array_split(np.arange(len(x)), n_workers)
+    jobs = [(grid_factory, kwargs, pids, x[p], q2[p], gout[p], absval) for p in parts]
+    with mp.get_context("spawn").Pool(n_workers) as pool:
+        grads = pool.map(_dgrid_matrix_chunk, jobs)
     return np.sum(np.stack(grads), axis=0)

@@ -275,6 +275,47 @@ def test_full_size_sum_rules(diffgrid):
     _check(gq, w[idx] * rdq, np.abs(w[idx]) * 4 * kap / (Wd * q2[idx]), "full dL/dQ2")
 
 
+def test_matrix_form_full_size_through_autograd(diffgrid):
+    """The matrix form as the benchmark times it: 1e6 points x all 13
+    flavours, L = sum_ia w_ia xf_a(x_i, Q^2_i) through torch.autograd (the
+    forward keeps the tape; the adjoint sorts by cell and half pair with one
+    accumulator per column).  The whole grid gradient against the oracle;
+    sampled dL/dx and dL/dQ^2 against the oracle's analytic derivative; the
+    flavour sum rule sum_cells dL/dv[.][a] = sum_i w_ia."""
+    from paper_2012_08221_gb300.autograd import xfxQ2
+    g, pdf, o = diffgrid
+    nm = 1_000_000
+    _, x, q2, _ = synth.queries_pointwise()
+    x, q2 = x[:nm].copy(), q2[:nm].copy()
+    gout = np.random.default_rng(7).standard_normal((nm, g.n_flav))
+    pids = np.asarray(g.pids, dtype=np.int32)
+    vals = torch.tensor(g.values, device="cuda", requires_grad=True)
+    X = cuda(x).requires_grad_(True)
+    Q = cuda(q2).requires_grad_(True)
+    (xfxQ2(pdf, vals, pids, X, Q) * cuda(gout)).sum().backward()
+    G = vals.grad[0].cpu().numpy()
+    for a in range(g.n_flav):
+        assert abs(G[:, :, a].sum() - gout[:, a].sum()) <= 1e-9 * np.abs(gout[:, a]).sum()
+    from tests.oracle_pool import dgrid_parallel
+    spec = ("grid_small", {"seed": 1003, "pids": synth.PIDS_13})
+    ref = dgrid_parallel(*spec, pids, x, q2, gout)
+    mag = dgrid_parallel(*spec, pids, x, q2, gout, absval=True)
+    _check(G, ref, mag, "full-size matrix-form grid gradient")
+    idx = np.random.default_rng(8).choice(nm, 2000, replace=False)
+    rdx, rdq = np.zeros(idx.size), np.zeros(idx.size)
+    for a, p in enumerate(pids):
+        dx, dq = o.grad_pw(np.full(idx.size, p, dtype=np.int32), x[idx], q2[idx])
+        rdx += gout[idx, a] * dx
+        rdq += gout[idx, a] * dq
+    kap = o.kappa(pids, x[idx], q2[idx]).sum(axis=1)
+    gs = np.abs(gout[idx]).max(axis=1)
+    U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
+    gx = X.grad[cuda(idx)].cpu().numpy()
+    gq = Q.grad[cuda(idx)].cpu().numpy()
+    _check(gx, rdx, gs * 4 * kap / (np.min(np.diff(U)) * x[idx]), "full matrix dL/dx")
+    _check(gq, rdq, gs * 4 * kap / (np.min(np.diff(W)) * q2[idx]), "full matrix dL/dQ2")
+
+
 def test_alphas_derivative_and_autograd():
     from paper_2012_08221_gb300.autograd import alphasQ2
     from paper_2012_08221_gb300.pdf import PDF
