@@ -595,19 +595,20 @@ def main():
         GV = torch.zeros(gs.values.shape[1:], dtype=torch.float64, device=dev)
 
         T3 = p3.new_tape(x3.size)            # the forward's adjoint tape (32 B per point)
+        D3 = p3.new_dtape(x3.size)           # and its patch derivatives (16 B per point)
 
         def step3():
             p3.bind_values(V3)
-            p3.xfxQ2_pw(P3, X3, Q3, out=O3, tape=T3)
+            p3.xfxQ2_pw(P3, X3, Q3, out=O3, tape=T3, dtape=D3)
             GV.zero_()
-            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV, tape=T3)
+            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV, tape=T3, dtape=D3)
 
         def kstep3(a, b):
             p3.bind_values(V3)
-            p3.xfxQ2_pw(P3, X3, Q3, out=O3, tape=T3)
+            p3.xfxQ2_pw(P3, X3, Q3, out=O3, tape=T3, dtape=D3)
             GV.zero_()
             a.record(stream)
-            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV, tape=T3)
+            p3.xfxQ2_backward(P3, X3, Q3, W3, pointwise=True, grad_values=GV, tape=T3, dtape=D3)
             b.record(stream)
 
         def step3n():                        # the same without the tape
@@ -643,21 +644,23 @@ def main():
         ms3n, _ = timed(step3n, max(3, args.steps // 2), args.warmup)
         ms3m, _ = timed(step3m, args.steps, args.warmup)
         n3 = x3.size
-        fl = n3 * (work.pw_fwd_point_flops() + work.pw_bwd_sorted_point_flops())
+        fl = n3 * (work.pw_fwd_point_flops(dtape=True) + work.pw_bwd_sorted_point_flops(dtape=True))
         forms["fwd_bwd"] = {
             "workload": "pointwise x*f and its adjoint (dL/dx, dL/dQ^2, dL/dgrid) at 1e7 points, "
                         "50x20 grid, 13 flavours, L = sum w_i xf_{a_i}, through torch.autograd",
             "value": world * n3 / (ms3a * 1e-3), "unit": "evals/s (fwd+bwd)", "ms_per_step": ms3a,
             "fp64_frac": (fl / (ms3a * 1e-3)) / peak,
             "fp64_frac_survey_count": n3 * work.pw_fwd_bwd_point_flops_survey() / (ms3a * 1e-3) / peak,
-            "flops_per_point": {"fwd": work.pw_fwd_point_flops(), "bwd": work.pw_bwd_sorted_point_flops(),
+            "flops_per_point": {"fwd": work.pw_fwd_point_flops(dtape=True),
+                                "bwd": work.pw_bwd_sorted_point_flops(dtape=True),
                                 "survey_fwd_bwd": work.pw_fwd_bwd_point_flops_survey()},
             "bwd_kernel": {"kernels": "k_bwd_count, k_scan, k_bwd_rec, k_bwd_accum (from the tape; grid "
                                       "gradient sorted by cell and flavour)", "ms": kb,
-                           "frac": n3 * work.pw_bwd_sorted_point_flops() / (kb * 1e-3) / peak,
+                           "frac": n3 * work.pw_bwd_sorted_point_flops(dtape=True) / (kb * 1e-3) / peak,
                            "frac_survey_count": n3 * work.pw_bwd_point_flops_survey() / (kb * 1e-3) / peak},
             "tape": "the forward pass writes 32 bytes per point (cells, local coordinates, flags) that the "
-                    "adjoint reads instead of searching the knots and taking logarithms again",
+                    "adjoint reads instead of searching the knots and taking logarithms again, and 16 bytes "
+                    "of patch derivatives (computed with the value) that spare the adjoint the coefficients",
             "direct_calls": {"ms_per_step": ms3, "value": world * n3 / (ms3 * 1e-3),
                              "what": "the same two library calls without autograd (no torch "
                                      "multiply, sum or gradient accumulation)"},
@@ -667,7 +670,7 @@ def main():
                                         "through torch.autograd (xfxQ2 with the pid list)",
                             "value": world * nm * gs.n_flav / (ms3m * 1e-3), "unit": "evals/s (fwd+bwd)",
                             "ms_per_step": ms3m}}
-        del P3, X3, Q3, W3, O3, T3, VA, XA, QA3, VM, XM, QM, WM
+        del P3, X3, Q3, W3, O3, T3, D3, VA, XA, QA3, VM, XM, QM, WM
 
     # ------------------------------------------------------------- batched
     if "batched" in want:

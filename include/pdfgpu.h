@@ -253,23 +253,34 @@ int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t
  *   every member of the grid.  PDF_E_ARG for a grid loaded with
  *   PDF_EXTRAP_CONTINUATION (which has no adjoint) and for a NULL tape
  *   when n > 0 (with n == 0 the calls do nothing, and the tape may be NULL).
+ *   dtape (xfxQ2_pw_tape only; may be NULL) DEVICE [n][2] doubles,
+ *   caller-owned, 16-byte aligned (PDF_E_ARG otherwise, and without a tape):
+ *   the derivative tape, each point's patch derivatives in its two local
+ *   coordinates (zeros for an absent pid), computed with the value (13 FMAs
+ *   more per point) so that xfxQ2_backward_tape given it takes dL/dx and
+ *   dL/dQ^2 without reloading the point's 16 coefficients.  Unlike the
+ *   tape it depends on the values bound and on the member: it is valid only
+ *   while the values of the forward call are bound, for the same member.
  * Outputs of the forward calls are bit for bit those of xfxQ2 / xfxQ2_pw. */
 int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                const double *x, const double *q2, int64_t n, double *out, double *tape,
                pdfgpu_stream_t stream);
 int xfxQ2_pw_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
-                  const double *q2, int64_t n, double *out, double *tape, pdfgpu_stream_t stream);
+                  const double *q2, int64_t n, double *out, double *tape, double *dtape,
+                  pdfgpu_stream_t stream);
 
 /* xfxQ2_backward from the tape a forward call wrote for the same grid and the
  * same points (beyond the paper: the differentiation form, as above) (x and q2 are still read, for the chain rule of grad_x and
  * grad_q2).  Same arguments and results as xfxQ2_backward, bit for bit in
- * grad_x and grad_q2.  A tape of other points or another grid gives wrong
- * numbers; its cells are clamped into the grid's tables, so no access leaves
- * them. */
+ * grad_x and grad_q2, with or without the derivative tape dtape (NULL, or
+ * the one xfxQ2_pw_tape wrote with this tape: pointwise form only, PDF_E_ARG
+ * otherwise; the forward's values must still be bound).  A tape of other
+ * points or another grid gives wrong numbers; its cells are clamped into the
+ * grid's tables, so no access leaves them. */
 int xfxQ2_backward_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                         int32_t pointwise, const double *x, const double *q2, int64_t n,
-                        const double *tape, const double *grad_out, double *grad_x,
-                        double *grad_q2, double *grad_values, pdfgpu_stream_t stream);
+                        const double *tape, const double *dtape, const double *grad_out,
+                        double *grad_x, double *grad_q2, double *grad_values, pdfgpu_stream_t stream);
 
 /* One request of a batched evaluation (several grids, members, flavour
  * subsets and sizes in one launch).  grid/member/pids are read at prepare

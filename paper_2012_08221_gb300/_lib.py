@@ -56,7 +56,7 @@ SIGNATURES = {
     "xfxQ2_pw": [c_grid, C.c_int32, _VP, _VP, _VP, C.c_int64, _VP, _VP],
     "xfxQ2_alphasQ2": [c_grid, C.c_int32, _I, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP, _VP],
     "xfxQ2_tape": [c_grid, C.c_int32, _I, C.c_int32, _VP, _VP, C.c_int64, _VP, _VP, _VP],
-    "xfxQ2_pw_tape": [c_grid, C.c_int32, _VP, _VP, _VP, C.c_int64, _VP, _VP, _VP],
+    "xfxQ2_pw_tape": [c_grid, C.c_int32, _VP, _VP, _VP, C.c_int64, _VP, _VP, _VP, _VP],
     "alphasQ2": [c_grid, _VP, C.c_int64, _VP, _VP],
     "alphasQ": [c_grid, _VP, C.c_int64, _VP, _VP],
     "alphasQ2_grad": [c_grid, _VP, C.c_int64, _VP, _VP, _VP],
@@ -64,7 +64,7 @@ SIGNATURES = {
     "xfxQ2_backward": [c_grid, C.c_int32, _VP, C.c_int32, C.c_int32, _VP, _VP, C.c_int64,
                        _VP, _VP, _VP, _VP, _VP],
     "xfxQ2_backward_tape": [c_grid, C.c_int32, _VP, C.c_int32, C.c_int32, _VP, _VP, C.c_int64,
-                            _VP, _VP, _VP, _VP, _VP, _VP],
+                            _VP, _VP, _VP, _VP, _VP, _VP, _VP],
     "pdf_batch_prepare": [C.POINTER(BatchDesc), C.c_int32, C.c_int32, _VP, C.POINTER(c_batch)],
     "pdf_batch_run": [c_batch, _VP],
     "pdf_batch_info": [c_batch, _I, _I, _I, _I, C.POINTER(C.c_float)],

@@ -6,7 +6,10 @@ the forward kernel; the backward runs the hand-written adjoint kernel, which
 returns dL/dx, dL/dQ^2 and the scatter of the 16 bicubic stencil weights
 into dL/dvalues (the derivative a PDF fit needs).  The forward keeps a
 32-byte adjoint tape per point (cells, local coordinates, flags), so that the
-backward does not search the knots or take logarithms again.  ``LumiFn`` does the same
+backward does not search the knots or take logarithms again; in the pointwise
+form, when x or Q^2 needs a gradient, also the 16-byte derivative tape (the
+patch derivatives, computed with the value), so that the backward does not
+reload the coefficients and needs no rebinding.  ``LumiFn`` does the same
 for the fused luminosity workload, L = (1/n) sum_e sum_a f_a(x1) f_-a(x2).
 
 The coefficients live in ONE table per PDF handle, rebuilt by every forward and
@@ -30,12 +33,16 @@ class XfxQ2Fn(torch.autograd.Function):
         # knot searches and logarithms; the power-law continuation has no
         # adjoint, so it gets none
         tape = pdf.new_tape(x.numel()) if use_tape and pdf.extrap != EXTRAP["continuation"] else None
+        dtape = None
         if pointwise:
-            out = pdf.xfxQ2_pw(pids, x, q2, member, tape=tape)
+            if tape is not None and (ctx.needs_input_grad[1] or ctx.needs_input_grad[2]):
+                dtape = pdf.new_dtape(x.numel())
+            out = pdf.xfxQ2_pw(pids, x, q2, member, tape=tape, dtape=dtape)
         else:
             out = pdf.xfxQ2(pids, x, q2, member, tape=tape)
         ctx.save_for_backward(values, x, q2)
-        ctx.pdf, ctx.pids, ctx.member, ctx.pointwise, ctx.tape = pdf, pids, member, pointwise, tape
+        ctx.pdf, ctx.pids, ctx.member, ctx.pointwise = pdf, pids, member, pointwise
+        ctx.tape, ctx.dtape = tape, dtape
         return out
 
     @staticmethod
@@ -43,14 +50,16 @@ class XfxQ2Fn(torch.autograd.Function):
         values, x, q2 = ctx.saved_tensors
         pdf: PDF = ctx.pdf
         need_v, need_x, need_q = ctx.needs_input_grad[:3]
-        pdf.bind_values(values)           # the coefficients of these values
+        if ctx.dtape is None:
+            pdf.bind_values(values)       # the coefficients of these values
         gvals = None
         gslice = None
         if need_v:
             gvals = torch.zeros_like(values)
             gslice = gvals[ctx.member] if values.dim() == 4 else gvals
         gx, gq, _ = pdf.xfxQ2_backward(ctx.pids, x, q2, gout, ctx.member, ctx.pointwise,
-                                       grad_x=need_x, grad_q2=need_q, grad_values=gslice, tape=ctx.tape)
+                                       grad_x=need_x, grad_q2=need_q, grad_values=gslice, tape=ctx.tape,
+                                       dtape=ctx.dtape)
         return gvals, gx, gq, None, None, None, None, None
 
 

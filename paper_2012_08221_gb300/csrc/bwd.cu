@@ -12,7 +12,10 @@
 // continuation.  Given the tape of the forward pass over the same points,
 // the adjoint rebuilds each point's cells and local coordinates from it
 // instead of searching the knots and taking the two logarithms again; the
-// arithmetic that follows is the same.
+// arithmetic that follows is the same.  A pointwise forward pass may also
+// keep each point's two patch derivatives (the derivative tape), computed
+// with its value by the same routine the adjoint would use, so that the
+// adjoint reads them instead of reloading the coefficients.
 //
 // Grid gradient: the points are counting-sorted into bins of one cell, one
 // flavour (pointwise form; the matrix form bins by cell and keeps every
@@ -52,6 +55,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
                                                 const double *__restrict__ x,
                                                 const double *__restrict__ q2, int64_t n,
                                                 const double *__restrict__ tape,
+                                                const double *__restrict__ dtape,
                                                 const double *__restrict__ gout,
                                                 double *__restrict__ gx, double *__restrict__ gq,
                                                 double *__restrict__ gval)
@@ -117,7 +121,13 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
             if (col < 0) continue;
             double ga = PW ? gout[i] : gout[i * npid + a];
             double dtx, dtq;
-            patch_d_horner(cell + col * 16, X, Q, &dtx, &dtq);
+            if (PW && TAPE && dtape) {
+                const double2 d = __ldg(reinterpret_cast<const double2 *>(dtape) + i);
+                dtx = d.x;
+                dtq = d.y;
+            } else {
+                patch_vd(cell + col * 16, X, Q, &dtx, &dtq);
+            }
             if (fzx) dtx = 0.0;
             if (fzq) dtq = 0.0;
             sx = fma(ga, dtx, sx);
@@ -284,10 +294,12 @@ __global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int 
 // two knots, to the gradient here with global atomics (rare points; through
 // the monomial basis the two knots that carry no weight would receive
 // rounding-sized terms instead of zeros).
+template <bool DT>
 __global__ void __launch_bounds__(kBlock, 5) k_bwd_rec(GridDev g, int member, const int *__restrict__ pid,
                                                     const double *__restrict__ x,
                                                     const double *__restrict__ q2, int64_t i0, int m,
                                                     const double *__restrict__ tape,
+                                                    const double *__restrict__ dtape,
                                                     const double *__restrict__ gout,
                                                     double *__restrict__ gx, double *__restrict__ gq,
                                                     double *__restrict__ gval, int nbins,
@@ -312,7 +324,13 @@ __global__ void __launch_bounds__(kBlock, 5) k_bwd_rec(GridDev g, int member, co
         const double ga = gout[i];
         if (gx || gq) {
             double dtx, dtq;
-            patch_d_horner(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q, &dtx, &dtq);
+            if (DT) {
+                const double2 d = __ldg(reinterpret_cast<const double2 *>(dtape) + i);
+                dtx = d.x;
+                dtq = d.y;
+            } else {
+                patch_vd(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q, &dtx, &dtq);
+            }
             if (!X.in && g.extrap == PDF_EXTRAP_FREEZE) dtx = 0.0;
             if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dtq = 0.0;
             if (gx) gx[i] = ga * dtx * g.xcell[X.cell].y * __drcp_rn(x[i]);
@@ -457,20 +475,14 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum(GridDev g, const d
 
 constexpr int kMaxSortedPids = 16;
 
-// Derivatives of a patch held in registers (as patch_d_horner).
+// Derivatives of a patch held in registers (as patch_vd).
 __device__ __forceinline__ void patch_d_regs(const double C[16], const Axis &X, const Axis &Q, double *dtx,
                                              double *dtq)
 {
-    const double tx2 = X.in ? X.t + X.t : 1.0, tx3 = X.in ? 3.0 * X.t * X.t : 1.0;
-    const double tq2 = Q.in ? Q.t + Q.t : 1.0, tq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
-    double i[4], j[4];
+    D4 r[4];
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        i[n] = horner(X, C[4 * n], C[4 * n + 1], C[4 * n + 2], C[4 * n + 3]);
-        j[n] = fma(tx3, C[4 * n + 3], fma(tx2, C[4 * n + 2], C[4 * n + 1]));
-    }
-    *dtx = horner(Q, j[0], j[1], j[2], j[3]);
-    *dtq = fma(tq3, i[3], fma(tq2, i[2], i[1]));
+    for (int n = 0; n < 4; ++n) r[n] = D4{C[4 * n], C[4 * n + 1], C[4 * n + 2], C[4 * n + 3]};
+    patch_vd_rows(r, X, Q, dtx, dtq);
 }
 
 // Per point: dL/dx and dL/dQ^2 from the combined patch, and the point's
@@ -670,8 +682,8 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum_m(GridDev g, Cols 
 // record pass and the accumulation.
 template <bool PW>
 int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, const int *pid, const double *x,
-                    const double *q2, int64_t n, const double *tape, const double *gout, double *gx, double *gq,
-                    double *gval, cudaStream_t st)
+                    const double *q2, int64_t n, const double *tape, const double *dtape, const double *gout,
+                    double *gx, double *gq, double *gval, cudaStream_t st)
 {
     const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * (PW ? g->d.nflav : 1) * 4;
     if (nbins64 >= (int64_t)1 << 30) return fail(PDF_E_RANGE, "grid too large for the sorted adjoint");
@@ -723,8 +735,9 @@ int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, cons
         const int64_t warps = (m + seg - 1) / seg;
         const int blocks = (int)((warps + kAccWarps - 1) / kAccWarps);
         if constexpr (PW) {
-            k_bwd_rec<<<wave_grid(g, (const void *)k_bwd_rec, kBlock, 0, m), kBlock, 0, st>>>(
-                g->d, member, pid, x, q2, i0, m, tv, gout, gx, gq, gval, nbins, cursor, rec);
+            auto krec = dtape ? k_bwd_rec<true> : k_bwd_rec<false>;
+            krec<<<wave_grid(g, (const void *)krec, kBlock, 0, m), kBlock, 0, st>>>(
+                g->d, member, pid, x, q2, i0, m, tv, dtape, gout, gx, gq, gval, nbins, cursor, rec);
             PDF_CUDA(cudaGetLastError());
             k_bwd_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, rec, offs, nbins, gval);
         } else {
@@ -740,11 +753,11 @@ int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, cons
 
 template <bool PW, bool TAPE>
 int launch(pdfgpu_grid *g, const Cols &cols, int npid, int member, const int *pid, const double *x,
-           const double *q2, int64_t n, const double *tape, const double *gout, double *gx, double *gq,
-           double *gval, cudaStream_t s)
+           const double *q2, int64_t n, const double *tape, const double *dtape, const double *gout, double *gx,
+           double *gq, double *gval, cudaStream_t s)
 {
     if (gval && (PW || npid <= kMaxSortedPids))
-        return backward_sorted<PW>(g, member, cols, npid, pid, x, q2, n, tape, gout, gx, gq, gval, s);
+        return backward_sorted<PW>(g, member, cols, npid, pid, x, q2, n, tape, dtape, gout, gx, gq, gval, s);
     size_t gbytes = (size_t)g->d.nrows * g->d.nx * g->d.nflav * sizeof(double);
     if constexpr (!PW) {
         if (gval && gbytes <= kSmemGradMax) {
@@ -753,7 +766,7 @@ int launch(pdfgpu_grid *g, const Cols &cols, int npid, int member, const int *pi
             if (rc) return rc;
             int grid = wave_grid(g, kern, kBlock, gbytes, n);
             k_bwd<PW, true, TAPE><<<grid, kBlock, gbytes, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape,
-                                                                gout, gx, gq, gval);
+                                                                dtape, gout, gx, gq, gval);
             PDF_CUDA(cudaGetLastError());
             return PDF_OK;
         }
@@ -761,16 +774,16 @@ int launch(pdfgpu_grid *g, const Cols &cols, int npid, int member, const int *pi
     {
         const void *kern = (const void *)k_bwd<PW, false, TAPE>;
         int grid = wave_grid(g, kern, kBlock, 0, n);
-        k_bwd<PW, false, TAPE><<<grid, kBlock, 0, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape, gout, gx,
-                                                        gq, gval);
+        k_bwd<PW, false, TAPE><<<grid, kBlock, 0, s>>>(g->d, cols, npid, member, pid, x, q2, n, tape, dtape,
+                                                        gout, gx, gq, gval);
     }
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
 
 int backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid, int32_t pointwise,
-             const double *x, const double *q2, int64_t n, const double *tape, const double *grad_out,
-             double *grad_x, double *grad_q2, double *grad_values, cudaStream_t s)
+             const double *x, const double *q2, int64_t n, const double *tape, const double *dtape,
+             const double *grad_out, double *grad_x, double *grad_q2, double *grad_values, cudaStream_t s)
 {
     clear_error();
     int rc = check_grid(g, true);
@@ -781,6 +794,9 @@ int backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid
     if (n < 0) return fail(PDF_E_ARG, "negative n");
     if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
     if (tape && (uintptr_t)tape % 32) return fail(PDF_E_ARG, "tape must be 32-byte aligned");
+    if (dtape && !pointwise) return fail(PDF_E_ARG, "a derivative tape serves the pointwise form only");
+    if (dtape && !tape) return fail(PDF_E_ARG, "a derivative tape goes with the tape of the same forward call");
+    if (dtape && (uintptr_t)dtape % 16) return fail(PDF_E_ARG, "derivative tape must be 16-byte aligned");
     Cols cols;
     memset(&cols, -1, sizeof(cols));
     if (!pointwise) {
@@ -790,14 +806,14 @@ int backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid
     if (n == 0) return PDF_OK;
     if (!x || !q2 || !grad_out || !pids) return fail(PDF_E_ARG, "null array");
     if (pointwise)
-        return tape ? launch<true, true>(g, cols, 1, member, pids, x, q2, n, tape, grad_out, grad_x, grad_q2,
-                                         grad_values, s)
-                    : launch<true, false>(g, cols, 1, member, pids, x, q2, n, nullptr, grad_out, grad_x, grad_q2,
-                                          grad_values, s);
-    return tape ? launch<false, true>(g, cols, n_pid, member, nullptr, x, q2, n, tape, grad_out, grad_x, grad_q2,
-                                      grad_values, s)
-                : launch<false, false>(g, cols, n_pid, member, nullptr, x, q2, n, nullptr, grad_out, grad_x,
-                                       grad_q2, grad_values, s);
+        return tape ? launch<true, true>(g, cols, 1, member, pids, x, q2, n, tape, dtape, grad_out, grad_x,
+                                         grad_q2, grad_values, s)
+                    : launch<true, false>(g, cols, 1, member, pids, x, q2, n, nullptr, nullptr, grad_out, grad_x,
+                                          grad_q2, grad_values, s);
+    return tape ? launch<false, true>(g, cols, n_pid, member, nullptr, x, q2, n, tape, nullptr, grad_out, grad_x,
+                                      grad_q2, grad_values, s)
+                : launch<false, false>(g, cols, n_pid, member, nullptr, x, q2, n, nullptr, nullptr, grad_out,
+                                       grad_x, grad_q2, grad_values, s);
 }
 
 }  // namespace
@@ -808,20 +824,20 @@ extern "C" int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pi
                               double *grad_values, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_backward");
-    return backward(g, member, pids, n_pid, pointwise, x, q2, n, nullptr, grad_out, grad_x, grad_q2, grad_values,
-                    (cudaStream_t)stream);
+    return backward(g, member, pids, n_pid, pointwise, x, q2, n, nullptr, nullptr, grad_out, grad_x, grad_q2,
+                    grad_values, (cudaStream_t)stream);
 }
 
 extern "C" int xfxQ2_backward_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                                    int32_t pointwise, const double *x, const double *q2, int64_t n,
-                                   const double *tape, const double *grad_out, double *grad_x, double *grad_q2,
-                                   double *grad_values, pdfgpu_stream_t stream)
+                                   const double *tape, const double *dtape, const double *grad_out,
+                                   double *grad_x, double *grad_q2, double *grad_values, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_backward_tape");
     if (!tape && n != 0) {
         clear_error();
         return fail(PDF_E_ARG, "null tape");
     }
-    return backward(g, member, pids, n_pid, pointwise, x, q2, n, tape, grad_out, grad_x, grad_q2, grad_values,
-                    (cudaStream_t)stream);
+    return backward(g, member, pids, n_pid, pointwise, x, q2, n, tape, dtape, grad_out, grad_x, grad_q2,
+                    grad_values, (cudaStream_t)stream);
 }

@@ -137,13 +137,16 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pairs(GridDev g, Cols cols, in
     }
 }
 
-template <bool CONT, bool TAPE>
+// DT (with TAPE): also keep each point's patch derivatives in t_x and t_q,
+// computed with the value (patch_vd: the value's bits are unchanged), in
+// dtape[i] = (dP/dtx, dP/dtq); zeros for an absent pid.
+template <bool CONT, bool TAPE, bool DT = false>
 __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
                                                      const int *__restrict__ pid,
                                                      const double *__restrict__ x,
                                                      const double *__restrict__ q2,
                                                      int64_t n, double *__restrict__ out,
-                                                     double *__restrict__ tape)
+                                                     double *__restrict__ tape, double *__restrict__ dtape)
 {
     const size_t cell_stride = (size_t)g.nflav * 16;
     const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
@@ -165,7 +168,13 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
         bad |= oor;
         if (TAPE) tape_put(tape, i, X, Q, bad);
         double v = 0.0;
-        if (col >= 0) v = patch_any<CONT>(g, cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
+        if (DT) {
+            double dtx = 0.0, dtq = 0.0;
+            if (col >= 0) v = patch_vd(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q, &dtx, &dtq);
+            reinterpret_cast<double2 *>(dtape)[i] = make_double2(dtx, dtq);
+        } else if (col >= 0) {
+            v = patch_any<CONT>(g, cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
+        }
         out[i] = bad ? qnan() : v;
     }
 }
@@ -349,7 +358,7 @@ int launch_alphas(pdfgpu_grid *g, const double *q, int64_t n, double *out, cudaS
 }
 
 int launch_pw(pdfgpu_grid *g, int32_t member, const int32_t *pid, const double *x, const double *q2, int64_t n,
-              double *out, double *tape, cudaStream_t s)
+              double *out, double *tape, double *dtape, cudaStream_t s)
 {
     clear_error();
     int rc = check_grid(g, true);
@@ -358,12 +367,15 @@ int launch_pw(pdfgpu_grid *g, int32_t member, const int32_t *pid, const double *
     if (member < 0 || member >= g->d.nmem) return fail(PDF_E_ARG, "member out of range");
     rc = check_tape(g, tape);
     if (rc) return rc;
+    if (dtape && !tape) return fail(PDF_E_ARG, "a derivative tape goes with a tape");
+    if (dtape && (uintptr_t)dtape % 16) return fail(PDF_E_ARG, "derivative tape must be 16-byte aligned");
     if (n == 0) return PDF_OK;
     if (!pid || !x || !q2 || !out) return fail(PDF_E_ARG, "null array");
-    auto k = tape ? k_xfxq2_pw<false, true>
+    auto k = dtape  ? k_xfxq2_pw<false, true, true>
+             : tape ? k_xfxq2_pw<false, true>
              : g->d.extrap == PDF_EXTRAP_CONTINUATION ? k_xfxq2_pw<true, false> : k_xfxq2_pw<false, false>;
     int grid = wave_grid(g, (const void *)k, kBlock, 0, n);
-    k<<<grid, kBlock, 0, s>>>(g->d, member, pid, x, q2, n, out, tape);
+    k<<<grid, kBlock, 0, s>>>(g->d, member, pid, x, q2, n, out, tape, dtape);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
@@ -396,7 +408,7 @@ extern "C" int xfxQ2_pw(pdfgpu_grid_t g, int32_t member, const int32_t *pid, con
                         const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_pw");
-    return launch_pw(g, member, pid, x, q2, n, out, nullptr, (cudaStream_t)stream);
+    return launch_pw(g, member, pid, x, q2, n, out, nullptr, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
@@ -412,14 +424,15 @@ extern "C" int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, 
 }
 
 extern "C" int xfxQ2_pw_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pid, const double *x,
-                             const double *q2, int64_t n, double *out, double *tape, pdfgpu_stream_t stream)
+                             const double *q2, int64_t n, double *out, double *tape, double *dtape,
+                             pdfgpu_stream_t stream)
 {
     PDF_TRACE("xfxQ2_pw_tape");
     if (!tape && n != 0) {
         clear_error();
         return fail(PDF_E_ARG, "null tape");
     }
-    return launch_pw(g, member, pid, x, q2, n, out, tape, (cudaStream_t)stream);
+    return launch_pw(g, member, pid, x, q2, n, out, tape, dtape, (cudaStream_t)stream);
 }
 
 extern "C" int alphasQ2(pdfgpu_grid_t g, const double *q2, int64_t n, double *out, pdfgpu_stream_t stream)

@@ -343,24 +343,47 @@ __device__ __forceinline__ double alphas_any(const GridDev &g, const D4 &a, cons
     return horner(Q, a.x, a.y, a.z, a.w);
 }
 
-// Derivatives of a patch with respect to tx and tq, by Horner's rule along
-// both axes with no powers of t: the rows' values i[n] = c0 + t (c1 + h (c2 + h c3)) and tx-derivatives
-// j[n] = c1 + t2 c2 + t3 c3 with (t2, t3) = (2t, 3t^2) inside and (1, 1)
-// outside; dP/dtx = horner over tq of j[n], dP/dtq = i1 + q2 i2 + q3 i3.
-__device__ __forceinline__ void patch_d_horner(const double *__restrict__ C, const Axis &X, const Axis &Q,
-                                               double *dtx, double *dtq)
+// Value and derivative in t of one cubic by Horner's rule: the value
+// c0 + t B1 with B1 = c1 + h B2, B2 = c2 + h c3 (the operations of horner(),
+// so the same bits), and the derivative B1 + g (B2 + g c3): with g = h = t
+// inside the knot range that is c1 + 2 c2 t + 3 c3 t^2; outside, g = 0 and
+// the derivative of the linear basis (1, t, t, t) is B1 = c1 + c2 + c3.
+// Two FMAs beyond the value.
+struct VD {
+    double v, d;
+};
+__device__ __forceinline__ VD horner_vd(const Axis &A, double c0, double c1, double c2, double c3)
 {
-    const double tx2 = X.in ? X.t + X.t : 1.0, tx3 = X.in ? 3.0 * X.t * X.t : 1.0;
-    const double tq2 = Q.in ? Q.t + Q.t : 1.0, tq3 = Q.in ? 3.0 * Q.t * Q.t : 1.0;
-    double i[4], j[4];
+    const double b2 = fma(A.h, c3, c2);
+    const double b1 = fma(A.h, b2, c1);
+    const double gt = A.in ? A.t : 0.0;
+    return {fma(A.t, b1, c0), fma(gt, fma(gt, c3, b2), b1)};
+}
+
+// A patch and its derivatives in t_x and t_q in one pass over its four
+// coefficient rows: each row's value i_n and t_x-derivative j_n, then the
+// value and the t_q-derivative from the i_n and the t_x-derivative by
+// Horner's rule over the j_n.  The value is patch()'s, bit for bit; the
+// two derivatives cost 13 FMAs beyond it (28 in all).  Every adjoint takes
+// its patch derivatives from here, so that derivatives kept by a forward
+// pass and derivatives recomputed later are the same bits.
+__device__ __forceinline__ double patch_vd_rows(const D4 r[4], const Axis &X, const Axis &Q, double *dtx,
+                                                double *dtq)
+{
+    VD row[4];
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-        D4 r = ld4(C + 4 * n);
-        i[n] = horner(X, r.x, r.y, r.z, r.w);
-        j[n] = fma(tx3, r.w, fma(tx2, r.z, r.y));
-    }
-    *dtx = horner(Q, j[0], j[1], j[2], j[3]);
-    *dtq = fma(tq3, i[3], fma(tq2, i[2], i[1]));
+    for (int n = 0; n < 4; ++n) row[n] = horner_vd(X, r[n].x, r[n].y, r[n].z, r[n].w);
+    const VD q = horner_vd(Q, row[0].v, row[1].v, row[2].v, row[3].v);
+    *dtx = horner(Q, row[0].d, row[1].d, row[2].d, row[3].d);
+    *dtq = q.d;
+    return q.v;
+}
+
+__device__ __forceinline__ double patch_vd(const double *__restrict__ C, const Axis &X, const Axis &Q, double *dtx,
+                                           double *dtq)
+{
+    const D4 r[4] = {ld4(C), ld4(C + 4), ld4(C + 8), ld4(C + 12)};
+    return patch_vd_rows(r, X, Q, dtx, dtq);
 }
 
 // Stencil weights of one axis (i <-> knot cell-1+i): W_i = sum_m M[m][i] t^m

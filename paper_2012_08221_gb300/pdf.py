@@ -178,13 +178,19 @@ class PDF:
         """Device buffer for the adjoint tape of ``n`` points (32 bytes each)."""
         return torch.empty((n, 4), dtype=torch.float64, device=self.device)
 
-    def _check_tape(self, tape, n):
-        assert tape.dtype == torch.float64 and tape.is_cuda and tape.is_contiguous(), "tape: contiguous float64"
-        assert tape.numel() >= 4 * n, "tape too small (4 doubles per point)"
+    def new_dtape(self, n):
+        """Device buffer for the derivative tape of ``n`` pointwise points (16
+        bytes each): the patch derivatives the forward keeps for the adjoint."""
+        return torch.empty((n, 2), dtype=torch.float64, device=self.device)
 
-    def xfxQ2_pw(self, pid, x, q2, member=0, out=None, tape=None):
+    def _check_tape(self, tape, n, per_point=4):
+        assert tape.dtype == torch.float64 and tape.is_cuda and tape.is_contiguous(), "tape: contiguous float64"
+        assert tape.numel() >= per_point * n, f"tape too small ({per_point} doubles per point)"
+
+    def xfxQ2_pw(self, pid, x, q2, member=0, out=None, tape=None, dtape=None):
         """One pid per point: ``out[i] = x*f_{pid_i}(x_i, Q^2_i)``; ``tape`` as
-        for ``xfxQ2``."""
+        for ``xfxQ2``; ``dtape`` (with ``tape``, from ``new_dtape``) also keeps
+        each point's patch derivatives for ``xfxQ2_backward``."""
         x = _f64_cuda(x, self.device)
         q2 = _f64_cuda(q2, self.device)
         pid = torch.as_tensor(pid, device=self.device).to(torch.int32).contiguous()
@@ -193,9 +199,13 @@ class PDF:
             out = torch.empty(n, dtype=torch.float64, device=self.device)
         if tape is not None:
             self._check_tape(tape, n)
+            if dtape is not None:
+                self._check_tape(dtape, n, 2)
             check("xfxQ2_pw_tape", lib().xfxQ2_pw_tape(self.handle, int(member), _ptr(pid), _ptr(x), _ptr(q2),
-                                                       n, _ptr(out), _ptr(tape), _stream(self.device)))
+                                                       n, _ptr(out), _ptr(tape), _ptr(dtape),
+                                                       _stream(self.device)))
             return out
+        assert dtape is None, "a derivative tape goes with a tape"
         check("xfxQ2_pw", lib().xfxQ2_pw(self.handle, int(member), _ptr(pid), _ptr(x), _ptr(q2), n,
                                          _ptr(out), _stream(self.device)))
         return out
@@ -243,11 +253,13 @@ class PDF:
 
     # --------------------------------------------------------------- adjoint
     def xfxQ2_backward(self, pids, x, q2, grad_out, member=0, pointwise=False,
-                       grad_x=True, grad_q2=True, grad_values=None, tape=None):
+                       grad_x=True, grad_q2=True, grad_values=None, tape=None, dtape=None):
         """dL/dx, dL/dQ^2 and (accumulated into ``grad_values``, shape
         ``[rows][n_x][n_flav]``) dL/dvalues for
         L = sum grad_out * xf.  Returns (grad_x, grad_q2, grad_values).
-        ``tape``: the adjoint tape a forward call wrote for the same points."""
+        ``tape``: the adjoint tape a forward call wrote for the same points;
+        ``dtape``: the derivative tape of that (pointwise) call, valid while
+        its values are bound."""
         x = _f64_cuda(x, self.device)
         q2 = _f64_cuda(q2, self.device)
         n = x.numel()
@@ -261,11 +273,15 @@ class PDF:
             arr, _ = _pids_host(pids)
             keep = arr
             pp, npid = C.c_void_p(arr.ctypes.data), arr.size
+        assert dtape is None or tape is not None, "a derivative tape goes with a tape"
         if tape is not None:
             self._check_tape(tape, n)
+            if dtape is not None:
+                self._check_tape(dtape, n, 2)
             check("xfxQ2_backward_tape", lib().xfxQ2_backward_tape(
                 self.handle, int(member), pp, npid, int(bool(pointwise)), _ptr(x), _ptr(q2), n,
-                _ptr(tape), _ptr(gout), _ptr(gx), _ptr(gq), _ptr(grad_values), _stream(self.device)))
+                _ptr(tape), _ptr(dtape), _ptr(gout), _ptr(gx), _ptr(gq), _ptr(grad_values),
+                _stream(self.device)))
         else:
             check("xfxQ2_backward", lib().xfxQ2_backward(
                 self.handle, int(member), pp, npid, int(bool(pointwise)), _ptr(x), _ptr(q2), n,

@@ -45,8 +45,14 @@ def alphas_point_flops() -> int:
 ALPHAS_POINT_BYTES = 16
 
 
-def pw_fwd_point_flops() -> int:
-    return xfxq2_point_flops(1)
+PATCH_D_FLOPS = 52      # the two patch derivatives alone: 26 FMA (patch_vd without the value)
+PATCH_VD_EXTRA_FLOPS = 26  # the two derivatives beside the value: 13 FMA
+
+
+def pw_fwd_point_flops(dtape: bool = False) -> int:
+    """One pointwise forward point; with the derivative tape the patch's two
+    derivatives are computed with its value (13 FMA more)."""
+    return xfxq2_point_flops(1) + (PATCH_VD_EXTRA_FLOPS if dtape else 0)
 
 
 PW_FWD_POINT_BYTES = 28                # x, Q^2, pid, out
@@ -58,17 +64,18 @@ PW_BWD_POINT_BYTES = 44                # grad_out, x, Q^2, pid in; dx, dQ^2 out
 TAPE_POINT_BYTES = 32                  # written by the forward, read by the adjoint
 
 
-def pw_bwd_sorted_point_flops() -> int:
+def pw_bwd_sorted_point_flops(dtape: bool = False) -> int:
     """The pointwise adjoint as the kernels now run it (from the tape, grid
     gradient sorted by (cell, flavour)).  Record pass: the patch's tx- and
-    tq-derivatives by Horner's rule (4 rows x (3 + 2) FMA, then 3 + 2 FMA:
-    25 FMA), the derivative bases (2t by an add, 3t^2 by 2 multiplies, per
-    axis), and the chain rule to x and Q^2 (3 multiplies and a reciprocal
-    each).  Accumulation: g times the Q basis and the x basis (6
-    multiplies) and the 16 FMAs of g bq_n bx_m.  The map back to the stencil
-    values (20 FMA per lane per bin run) is per bin, not per point, and is
-    not counted."""
-    record = 2 * 25 + 2 * 3 + 2 * 4
+    tq-derivatives by Horner's rule (rows 1-3: 5 FMA each, row 0: 4, the Q
+    step: 4, the tx-derivative over the rows: 3; 26 FMA), unless the
+    forward kept them in the derivative tape, and the chain rule to x and
+    Q^2 (3 multiplies and a reciprocal each).  Accumulation: g times the Q
+    basis and the x basis (6 multiplies) and the 16 FMAs of g bq_n bx_m.
+    The map back to the stencil values (8 FMA per lane per bin run) is per
+    bin, not per point, and is not counted."""
+    chain = 2 * 4
+    record = chain if dtape else PATCH_D_FLOPS + chain
     accumulate = 6 + 2 * 16
     return record + accumulate
 

@@ -53,6 +53,13 @@ def main():
             gxt, gqt, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
                                            pointwise=True, grad_values=gt, tape=T)
             res += [gxt, gqt]
+            # and with the derivative tape
+            D = p.new_dtape(x.size)
+            res.append(p.xfxQ2_pw(pid, X, Q, tape=T, dtape=D))
+            gd = torch.zeros_like(gv)
+            gxd, gqd, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
+                                           pointwise=True, grad_values=gd, tape=T, dtape=D)
+            res += [D.flatten(), gxd, gqd]
             # the matrix form's sorted adjoint (up to 16 columns)
             gm = torch.zeros_like(gv)
             pm = np.array([g.pids[0], 21, 9], dtype=np.int32)                  # 9: absent

@@ -360,10 +360,12 @@ def test_tape_gives_the_same_forward_and_adjoint(extrap):
         pid = cuda(rng.choice(np.append(g.pids, 7), x.size).astype(np.int32))   # 7: absent
         pids = np.array([g.pids[0], 21, g.pids[-1], 7], dtype=np.int32)
         T = pdf.new_tape(x.size)
+        D = pdf.new_dtape(x.size)
         for pointwise in (True, False):
             if pointwise:
                 ref = pdf.xfxQ2_pw(pid, X, Q)
                 got = pdf.xfxQ2_pw(pid, X, Q, tape=T)
+                assert same(pdf.xfxQ2_pw(pid, X, Q, tape=T, dtape=D), ref)
                 gout = cuda(rng.standard_normal(x.size))
                 ids = pid
             else:
@@ -379,6 +381,18 @@ def test_tape_gives_the_same_forward_and_adjoint(extrap):
             assert same(gx1, gx0) and same(gq1, gq0)
             assert torch.allclose(gv1, gv0, rtol=1e-12, atol=1e-15 * float(gv0.abs().max()))
             assert bool(torch.isnan(gx1[[0, 1, 2, 4, 5, 6]]).all()) and not bool(torch.isnan(gx1[3]))   # x = 1 is valid
+            if pointwise:
+                # the derivative tape: the same bits, with and without the grid
+                # gradient (sorted record pass / plain adjoint)
+                gv2 = torch.zeros_like(gv0)
+                gx2, gq2, _ = pdf.xfxQ2_backward(ids, X, Q, gout, pointwise=True, grad_values=gv2, tape=T,
+                                                 dtape=D)
+                assert same(gx2, gx0) and same(gq2, gq0)
+                assert torch.allclose(gv2, gv0, rtol=1e-12, atol=1e-15 * float(gv0.abs().max()))
+                gx3, gq3, _ = pdf.xfxQ2_backward(ids, X, Q, gout, pointwise=True, tape=T, dtape=D)
+                assert same(gx3, gx0) and same(gq3, gq0)
+                absent = (pid == 7).nonzero().flatten()
+                assert bool((D[absent] == 0).all())
         torch.cuda.synchronize()
 
 
@@ -405,6 +419,45 @@ def test_tape_survives_new_values_and_other_members():
         assert torch.allclose(gv1, gv0, rtol=1e-12, atol=1e-15 * float(gv0.abs().max()))
 
 
+def test_derivative_tape_keeps_the_forward_values():
+    """The derivative tape holds the patch derivatives of the values bound
+    at the forward call: after other values are bound, the adjoint from it
+    still gives dL/dx and dL/dQ^2 of the forward's values (the same bits as
+    the adjoint with those values bound again), and its grid gradient, which
+    does not depend on the values, is unchanged.  Through autograd two
+    evaluations with different values on one handle, backward in the
+    opposite order, each get their own values' gradients."""
+    from paper_2012_08221_gb300.autograd import xfxQ2_pw as ad_xfxQ2_pw
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_small(seed=1003, pids=synth.PIDS_13)
+    pdf = PDF.from_grid(g)
+    pid, x, q2, w = synth.queries_pointwise(20_011, seed=57)
+    P, X, Q, W_ = cuda(pid), cuda(x), cuda(q2), cuda(w)
+    T, D = pdf.new_tape(x.size), pdf.new_dtape(x.size)
+    V1, V2 = cuda(g.values), cuda(g.values * 1.5 - 0.25)
+    pdf.bind_values(V1)
+    pdf.xfxQ2_pw(P, X, Q, tape=T, dtape=D)
+    pdf.bind_values(V2)
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    gx, gq, _ = pdf.xfxQ2_backward(P, X, Q, W_, pointwise=True, grad_values=gv, tape=T, dtape=D)
+    pdf.bind_values(V1)
+    gv0 = torch.zeros_like(gv)
+    gx0, gq0, _ = pdf.xfxQ2_backward(P, X, Q, W_, pointwise=True, grad_values=gv0, tape=T)
+    assert torch.equal(gx, gx0) and torch.equal(gq, gq0)
+    assert torch.allclose(gv, gv0, rtol=1e-12, atol=1e-15 * float(gv0.abs().max()))
+    # autograd: forward V1, forward V2, backward V2, backward V1
+    A1, A2 = V1.clone().requires_grad_(True), V2.clone().requires_grad_(True)
+    X1, X2 = X.clone().requires_grad_(True), X.clone().requires_grad_(True)
+    L1 = (ad_xfxQ2_pw(pdf, A1, P, X1, Q) * W_).sum()
+    L2 = (ad_xfxQ2_pw(pdf, A2, P, X2, Q) * W_).sum()
+    L2.backward()
+    L1.backward()
+    assert torch.equal(X1.grad, gx0)
+    pdf.bind_values(V2)
+    gx2, _, _ = pdf.xfxQ2_backward(P, X, Q, W_, pointwise=True, tape=T)
+    assert torch.equal(X2.grad, gx2)
+
+
 def test_tape_arguments_are_checked():
     from paper_2012_08221_gb300._lib import PdfError
     from paper_2012_08221_gb300.pdf import PDF
@@ -424,6 +477,26 @@ def test_tape_arguments_are_checked():
         pc.xfxQ2(g.pids, X, Q, tape=pc.new_tape(x.size))
     with pytest.raises(AssertionError):
         pdf.xfxQ2_pw(pid, X, Q, tape=pdf.new_tape(x.size - 1))
+    # the derivative tape: 16-byte aligned, with a tape, pointwise form only
+    from paper_2012_08221_gb300._lib import lib
+    from paper_2012_08221_gb300.pdf import _ptr, _stream
+    T = pdf.new_tape(x.size)
+    D = pdf.new_dtape(x.size)
+    dbuf = torch.empty(2 * x.size + 2, dtype=torch.float64, device="cuda")
+    out = torch.empty(x.size, dtype=torch.float64, device="cuda")
+    gout = cuda(np.ones(x.size))
+    st = _stream(pdf.device)
+    assert lib().xfxQ2_pw_tape(pdf.handle, 0, _ptr(pid), _ptr(X), _ptr(Q), x.size, _ptr(out), _ptr(T),
+                               _ptr(dbuf[1:]), st) != 0
+    assert lib().xfxQ2_pw_tape(pdf.handle, 0, _ptr(pid), _ptr(X), _ptr(Q), x.size, _ptr(out), None,
+                               _ptr(D), st) != 0
+    pdf.xfxQ2_pw(pid, X, Q, tape=T, dtape=D)
+    pids = np.array([2], dtype=np.int32)
+    assert lib().xfxQ2_backward_tape(pdf.handle, 0, pids.ctypes.data, 1, 0, _ptr(X), _ptr(Q), x.size,
+                                     _ptr(T), _ptr(D), _ptr(gout), None, None, None, st) != 0
+    assert lib().xfxQ2_backward_tape(pdf.handle, 0, _ptr(pid), 0, 1, _ptr(X), _ptr(Q), x.size,
+                                     _ptr(T), _ptr(dbuf[1:]), _ptr(gout), None, None, None, st) != 0
+    torch.cuda.synchronize()
     # autograd on a continuation grid still runs its forward (no tape)
     from paper_2012_08221_gb300.autograd import xfxQ2 as ad_xfxQ2
     vals = torch.tensor(g.values, device="cuda", requires_grad=True)
