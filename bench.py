@@ -650,14 +650,14 @@ def main():
                         "50x20 grid, 13 flavours, L = sum w_i xf_{a_i}, through torch.autograd",
             "value": world * n3 / (ms3a * 1e-3), "unit": "evals/s (fwd+bwd)", "ms_per_step": ms3a,
             "fp64_frac": (fl / (ms3a * 1e-3)) / peak,
-            "fp64_frac_survey_count": n3 * work.pw_fwd_bwd_point_flops_survey() / (ms3a * 1e-3) / peak,
+            "fp64_frac_separable_count": n3 * work.pw_fwd_bwd_point_flops_separable() / (ms3a * 1e-3) / peak,
             "flops_per_point": {"fwd": work.pw_fwd_point_flops(dtape=True),
                                 "bwd": work.pw_bwd_sorted_point_flops(dtape=True),
-                                "survey_fwd_bwd": work.pw_fwd_bwd_point_flops_survey()},
+                                "separable_fwd_bwd": work.pw_fwd_bwd_point_flops_separable()},
             "bwd_kernel": {"kernels": "k_bwd_count, k_scan, k_bwd_rec, k_bwd_accum (from the tape; grid "
                                       "gradient sorted by cell and flavour)", "ms": kb,
                            "frac": n3 * work.pw_bwd_sorted_point_flops(dtape=True) / (kb * 1e-3) / peak,
-                           "frac_survey_count": n3 * work.pw_bwd_point_flops_survey() / (kb * 1e-3) / peak},
+                           "frac_separable_count": n3 * work.pw_bwd_point_flops_separable() / (kb * 1e-3) / peak},
             "tape": "the forward pass writes 32 bytes per point (cells, local coordinates, flags) that the "
                     "adjoint reads instead of searching the knots and taking logarithms again, and 16 bytes "
                     "of patch derivatives (computed with the value) that spare the adjoint the coefficients",

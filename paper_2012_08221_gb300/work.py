@@ -80,17 +80,17 @@ def pw_bwd_sorted_point_flops(dtape: bool = False) -> int:
     return record + accumulate
 
 
-def pw_bwd_point_flops_survey() -> int:
+def pw_bwd_point_flops_separable() -> int:
     """The backward work of one pointwise point in the separable-weight count
     of the method (derivative weights of both axes, the contraction and its
     derivatives, and the 16-weight scatter into the grid: about 170)."""
     return 170
 
 
-def pw_fwd_bwd_point_flops_survey() -> int:
+def pw_fwd_bwd_point_flops_separable() -> int:
     """The forward plus backward work of one pointwise point in the
     separable-weight count of the method (forward 90, backward about 170)."""
-    return 90 + pw_bwd_point_flops_survey()
+    return 90 + pw_bwd_point_flops_separable()
 
 
 def lumi_event_flops(n_flav: int) -> int:
