@@ -256,9 +256,20 @@ __global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int 
     }
     // kCountIlp points per thread at a time: the pass is bound by memory
     // latency, so each thread keeps that many loads in flight
+    // (all of a group's loads, the tape records' cells and flags and the
+    // pids, are issued before any is used)
     const int stride = gridDim.x * blockDim.x;
     for (int k0 = blockIdx.x * blockDim.x + threadIdx.x; k0 < m; k0 += kCountIlp * stride) {
-        int b[kCountIlp];
+        int b[kCountIlp], pv[kCountIlp];
+        double2 r[kCountIlp];
+#pragma unroll
+        for (int u = 0; u < kCountIlp; ++u) {
+            const int k = k0 + u * stride;
+            if (k < m) {
+                r[u] = tape_cells_raw(tape, k);
+                if (PW) pv[u] = __ldg(pid + i0 + k);
+            }
+        }
 #pragma unroll
         for (int u = 0; u < kCountIlp; ++u) {
             const int k = k0 + u * stride;
@@ -266,8 +277,8 @@ __global__ void __launch_bounds__(kCountBlock) k_bwd_count(GridDev g, const int 
             if (k < m) {
                 Axis X, Q;
                 unsigned halves;
-                const bool bad = tape_get_cells(g, tape, k, X, Q, &halves);
-                b[u] = PW ? sorted_bin(g, X, Q, bad, bad ? -1 : pid_col(g, pid[i0 + k]), (int)halves, nbins)
+                const bool bad = tape_decode(g, r[u].x, r[u].y, X, Q, &halves);
+                b[u] = PW ? sorted_bin(g, X, Q, bad, bad ? -1 : pid_col(g, pv[u]), (int)halves, nbins)
                           : sorted_cell(g, X, Q, bad, (int)halves, nbins);
             }
         }

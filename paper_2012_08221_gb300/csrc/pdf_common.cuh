@@ -519,14 +519,11 @@ __device__ __forceinline__ bool tape_decode(const GridDev &g, double cells_bits,
     return f & kTapeBad;
 }
 
-// Only the cells, range flags and halves (bit 0: t_x > 1/2, bit 1: t_q > 1/2)
-// of point i's tape record, from a 16-byte load; returns whether the point is
-// bad.
-__device__ __forceinline__ bool tape_get_cells(const GridDev &g, const double *__restrict__ tape, int64_t i,
-                                               Axis &X, Axis &Q, unsigned *halves)
+// The half of point i's tape record that holds the cells and the flags (for
+// tape_decode), from one 16-byte load.
+__device__ __forceinline__ double2 tape_cells_raw(const double *__restrict__ tape, int64_t i)
 {
-    const double2 r = __ldg(reinterpret_cast<const double2 *>(tape + 4 * i + 2));
-    return tape_decode(g, r.x, r.y, X, Q, halves);
+    return __ldg(reinterpret_cast<const double2 *>(tape + 4 * i + 2));
 }
 
 // Rebuilds the two axes of point i from its tape record; returns whether the
