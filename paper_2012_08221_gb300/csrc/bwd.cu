@@ -49,6 +49,29 @@ constexpr size_t kSmemGradMax = 200 * 1024;
 
 __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7FF8000000000000ll); }
 
+// Chain rule from the local coordinates to x and Q^2: given sx = g dP/dtx
+// and sq = g dP/dtq, dL/dx = sx (1/dU) / x and dL/dQ^2 = sq (1/dW) / Q^2,
+// with one reciprocal of x Q^2 for both (1/x = Q^2 / (x Q^2), 1/Q^2 =
+// x / (x Q^2)); where the product leaves the normal range the two
+// reciprocals are taken apart.  Every adjoint goes through here, so their
+// dL/dx and dL/dQ^2 stay the same bits.
+__device__ __forceinline__ void chain_rule(double sx, double sq, double ydu, double ydw, double x, double q2,
+                                           double *__restrict__ gx, double *__restrict__ gq, int64_t i)
+{
+    const double xq = x * q2;
+    double rx, rq;
+    if (dbits(xq) - 0x0010000000000000ull < 0x7FE0000000000000ull) {   // normal and finite
+        const double r = __drcp_rn(xq);
+        rx = q2 * r;
+        rq = x * r;
+    } else {
+        rx = __drcp_rn(x);
+        rq = __drcp_rn(q2);
+    }
+    if (gx) gx[i] = sx * ydu * rx;
+    if (gq) gq[i] = sq * ydw * rq;
+}
+
 template <bool PW, bool SMEM, bool TAPE>
 __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, int member,
                                                 const int *__restrict__ pid,
@@ -148,8 +171,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd(GridDev g, Cols cols, int npid, 
                 }
             }
         }
-        if (gx) gx[i] = sx * g.xcell[X.cell].y * __drcp_rn(xi);
-        if (gq) gq[i] = sq * g.qcell[Q.cell].y * __drcp_rn(qi);
+        chain_rule(sx, sq, g.xcell[X.cell].y, g.qcell[Q.cell].y, xi, qi, gx, gq, i);
     }
     if (SMEM) {
         __syncthreads();
@@ -344,8 +366,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_bwd_rec(GridDev g, int member, co
             }
             if (!X.in && g.extrap == PDF_EXTRAP_FREEZE) dtx = 0.0;
             if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dtq = 0.0;
-            if (gx) gx[i] = ga * dtx * g.xcell[X.cell].y * __drcp_rn(x[i]);
-            if (gq) gq[i] = ga * dtq * g.qcell[Q.cell].y * __drcp_rn(q2[i]);
+            chain_rule(ga * dtx, ga * dtq, g.xcell[X.cell].y, g.qcell[Q.cell].y, x[i], q2[i], gx, gq, i);
         }
         if (!(X.in && Q.in)) {
             double Wx[4], Wq[4];
@@ -549,8 +570,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_rec_m(GridDev g, Cols cols, int 
             patch_d_regs(C, X, Q, &dtx, &dtq);
             if (!X.in && g.extrap == PDF_EXTRAP_FREEZE) dtx = 0.0;
             if (!Q.in && g.extrap == PDF_EXTRAP_FREEZE) dtq = 0.0;
-            if (gx) gx[i] = dtx * g.xcell[X.cell].y * __drcp_rn(x[i]);
-            if (gq) gq[i] = dtq * g.qcell[Q.cell].y * __drcp_rn(q2[i]);
+            chain_rule(dtx, dtq, g.xcell[X.cell].y, g.qcell[Q.cell].y, x[i], q2[i], gx, gq, i);
         }
         if (!(X.in && Q.in)) {
             double Wx[4], Wq[4];
