@@ -204,6 +204,44 @@ static void cell_matrix(const double *z, int n, int k, double M[16], bool linear
     memcpy(Ms, ms, sizeof(ms));
 }
 
+// Guide table of a cell search over ascending lower keys (see
+// find_cell_guided): the widest bucket width 2^shift, at most kGuideMax
+// buckets from the first key to key_hi, for which no bucket holds more than
+// kGuideRun further lower keys (the last bucket counts every cell above it,
+// since keys beyond key_hi fall into it).  Left empty when no width
+// qualifies (knots clustered far more densely in one place than another);
+// the kernels then search by bisection.
+static constexpr uint64_t kGuideMax = 4096;
+
+static void build_guide(const std::vector<uint64_t> &keys, uint64_t key_hi, std::vector<int> &guide, int *shift)
+{
+    guide.clear();
+    *shift = 0;
+    const int ncell = (int)keys.size();
+    const uint64_t key0 = keys[0];
+    auto cell_of = [&](uint64_t key) {   // largest c with keys[c] <= key (key >= key0)
+        return (int)(std::upper_bound(keys.begin(), keys.end(), key) - keys.begin()) - 1;
+    };
+    std::vector<int> gd;
+    for (int s = 63; s >= 0; --s) {
+        const uint64_t nb = ((key_hi - key0) >> s) + 1;
+        if (nb > kGuideMax) return;
+        gd.assign(nb, 0);
+        bool ok = true;
+        for (uint64_t b = 0; b < nb && ok; ++b) {
+            const uint64_t first = key0 + (b << s);
+            gd[b] = cell_of(first);
+            const int last = b + 1 < nb ? cell_of(first + ((((uint64_t)1) << s) - 1)) : ncell - 1;
+            ok = last - gd[b] <= kGuideRun;
+        }
+        if (ok) {
+            guide.swap(gd);
+            *shift = s;
+            return;
+        }
+    }
+}
+
 static int largest_pow2_below(int n)
 {
     int s = 0;
@@ -464,6 +502,11 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     d.nmem = D.n_members;
     d.xstep = largest_pow2_below(nxc);
     d.qstep = largest_pow2_below(nqc);
+    std::vector<int> xguide, qguide;
+    build_guide(xbits, dbits(D.x_knots[nx - 1]), xguide, &d.xgshift);
+    build_guide(qbits, dbits(Q2[rows - 1]), qguide, &d.qgshift);
+    d.nxg = (int)xguide.size();
+    d.nqg = (int)qguide.size();
     d.xlo = dbits(D.x_knots[0]);
     d.xhi = dbits(D.x_knots[nx - 1]);
     d.qlo = dbits(Q2[0]);
@@ -478,6 +521,8 @@ extern "C" int pdf_load_grid(const pdfgpu_grid_desc *desc, pdfgpu_grid_t *out)
     TRY(dev_upload(g, ukey.data(), ukey.size(), &d.ukey));
     TRY(dev_upload(g, xcell.data(), xcell.size(), &d.xcell));
     TRY(dev_upload(g, qbits.data(), qbits.size(), &d.qbits));
+    if (d.nxg) TRY(dev_upload(g, xguide.data(), xguide.size(), &d.xguide));
+    if (d.nqg) TRY(dev_upload(g, qguide.data(), qguide.size(), &d.qguide));
     TRY(dev_upload(g, wkey.data(), wkey.size(), &d.wkey));
     TRY(dev_upload(g, qcell.data(), qcell.size(), &d.qcell));
     TRY(dev_upload(g, ltab.data(), ltab.size(), &d.logtab));

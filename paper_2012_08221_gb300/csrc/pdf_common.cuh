@@ -103,6 +103,8 @@ struct GridDev {
     int nqc;              // Q cells over all subgrids
     int nrows, nsub, nflav, nmem;
     int xstep, qstep;     // search start steps (largest power of two < cells)
+    int nxg, nqg;         // guide-table buckets per axis (0: no guide, binary search)
+    int xgshift, qgshift; // log2 of the guide buckets' width in key units
     uint64_t xlo, xhi;    // bit patterns of the first / last x knot
     uint64_t qlo, qhi;    // bit patterns of the first / last Q^2 knot
     int64_t ulo, uhi;     // order keys of ln(first / last x knot)
@@ -111,6 +113,8 @@ struct GridDev {
     const int64_t *ukey;     // [nxc] order keys of each x cell's lower ln x
     const double2 *xcell;    // [nxc] (U_k, 1/dU_k)
     const uint64_t *qbits;   // [nqc] bits of each Q cell's lower Q^2 knot
+    const int *xguide;       // [nxg] first cell of each x guide bucket
+    const int *qguide;       // [nqg] the same for Q^2
     const int64_t *wkey;     // [nqc] order keys of each Q cell's lower ln Q^2
     const double2 *qcell;    // [nqc] (W_c, 1/dW_c)
     const LogEntry *logtab;  // [kLogTab]
@@ -139,6 +143,30 @@ __device__ __forceinline__ int find_cell(const K *keys, int ncell, int step, K k
         if (c < ncell && keys[c] <= key) lo = c;
     }
     return lo;
+}
+
+// The same search through a guide table: bucket b covers the keys
+// key0 + [b 2^shift, (b + 1) 2^shift) (the last bucket also everything
+// above) and holds the largest cell whose lower key is <= the bucket's first
+// key; the host builds the table so that no bucket holds more than
+// kGuideRun further lower keys.  The cell of a key is then the bucket's cell
+// plus the number of the next kGuideRun lower keys that are <= it (the keys
+// ascend): one table load and kGuideRun independent key loads, instead of a
+// chain of log2(cells) dependent ones.  Without a table (nguide == 0) the
+// binary search.
+constexpr int kGuideRun = 3;
+
+__device__ __forceinline__ int find_cell_guided(const uint64_t *keys, int ncell, int step, const int *guide,
+                                                int nguide, int shift, uint64_t key0, uint64_t key)
+{
+    if (nguide == 0) return find_cell<uint64_t>(keys, ncell, step, key);
+    if (key < key0) return 0;
+    const uint64_t off = (key - key0) >> shift;
+    const int c = __ldg(guide + (off < (uint64_t)nguide ? (int)off : nguide - 1));
+    int add = 0;
+#pragma unroll
+    for (int r = 1; r <= kGuideRun; ++r) add += (c + r < ncell && keys[c + r] <= key) ? 1 : 0;
+    return c + add;
 }
 
 // Checked builds (-DPDFGPU_CHECKED, the library built with PDFGPU_CHECKED=1):
@@ -208,7 +236,8 @@ __device__ __forceinline__ Axis axis_x(const GridDev &g, double x, double *u)
 {
     uint64_t b = dbits(x);
     Axis A;
-    A.cell = checked_index(g.status, find_cell<uint64_t>(g.xbits, g.nxc, g.xstep, b), g.nxc);
+    A.cell = checked_index(g.status, find_cell_guided(g.xbits, g.nxc, g.xstep, g.xguide, g.nxg, g.xgshift, g.xlo, b),
+                           g.nxc);
     A.in = (b >= g.xlo) & (b <= g.xhi);
     A.below = b < g.xlo;
     double uu = dlog(g, x);
@@ -235,7 +264,8 @@ __device__ __forceinline__ Axis axis_q2(const GridDev &g, double q2, double *w)
 {
     uint64_t b = dbits(q2);
     Axis A;
-    A.cell = checked_index(g.status, find_cell<uint64_t>(g.qbits, g.nqc, g.qstep, b), g.nqc);
+    A.cell = checked_index(g.status, find_cell_guided(g.qbits, g.nqc, g.qstep, g.qguide, g.nqg, g.qgshift, g.qlo, b),
+                           g.nqc);
     A.in = (b >= g.qlo) & (b <= g.qhi);
     A.below = b < g.qlo;
     double ww = dlog(g, q2);
