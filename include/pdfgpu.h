@@ -491,6 +491,15 @@ int pdf_probe_fp64_mixed(double *dfma_flops, double *dmma_flops, double *mixed_f
 int pdf_debug_log(pdfgpu_grid_t g, const double *in, int64_t n, double *out,
                   pdfgpu_stream_t stream);
 
+/* (Beyond the paper: a test hook.)  The cells the kernels' knot searches give
+ * for n DEVICE points x, q2 (positive, finite): x_cell[i], q_cell[i] DEVICE
+ * int32, the largest cell whose lower knot is at or below the point (0 below
+ * the grid, the last cell above it; a Q^2 on an internal threshold is in the
+ * upper subgrid's first cell), and in guided (HOST [2], may be NULL) whether
+ * the x and the Q^2 search run through a guide table (else by bisection). */
+int pdf_debug_cells(pdfgpu_grid_t g, const double *x, const double *q2, int64_t n, int32_t *x_cell,
+                    int32_t *q_cell, int32_t *guided, pdfgpu_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ SIGNATURES = {
     "pdf_probe_fp64_mma_peak": [C.c_int32, _D],
     "pdf_probe_fp64_mixed": [_D, _D, _D],
     "pdf_debug_log": [c_grid, _VP, C.c_int64, _VP, _VP],
+    "pdf_debug_cells": [c_grid, _VP, _VP, C.c_int64, _VP, _VP, C.POINTER(C.c_int32), _VP],
 }
 
 

@@ -230,6 +230,19 @@ __global__ void __launch_bounds__(kBlock) k_alphas_grad(GridDev g, const double 
     }
 }
 
+// The cells the kernels' knot searches give (x, Q^2 given as bit patterns;
+// the guide table when the grid has one): a test hook.
+__global__ void k_cells(GridDev g, const double *__restrict__ x, const double *__restrict__ q2, int64_t n,
+                        int *__restrict__ xc, int *__restrict__ qc)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double u, w;
+        xc[i] = axis_x(g, x[i], &u).cell;
+        qc[i] = axis_q2(g, q2[i], &w).cell;
+    }
+}
+
 __global__ void k_log(GridDev g, const double *__restrict__ in, int64_t n, double *__restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -476,6 +489,26 @@ extern "C" int pdf_debug_log(pdfgpu_grid_t g, const double *in, int64_t n, doubl
     if (!in || !out) return fail(PDF_E_ARG, "null array");
     int grid = wave_grid(g, (const void *)k_log, kBlock, 0, n);
     k_log<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, in, n, out);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
+
+extern "C" int pdf_debug_cells(pdfgpu_grid_t g, const double *x, const double *q2, int64_t n, int32_t *x_cell,
+                               int32_t *q_cell, int32_t *guided, pdfgpu_stream_t stream)
+{
+    PDF_TRACE("pdf_debug_cells");
+    clear_error();
+    int rc = check_grid(g, false);
+    if (rc) return rc;
+    if (n < 0) return fail(PDF_E_ARG, "negative n");
+    if (guided) {
+        guided[0] = g->d.nxg > 0;
+        guided[1] = g->d.nqg > 0;
+    }
+    if (n == 0) return PDF_OK;
+    if (!x || !q2 || !x_cell || !q_cell) return fail(PDF_E_ARG, "null array");
+    int grid = wave_grid(g, (const void *)k_cells, kBlock, 0, n);
+    k_cells<<<grid, kBlock, 0, (cudaStream_t)stream>>>(g->d, x, q2, n, x_cell, q_cell);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }

@@ -318,6 +318,19 @@ class PDF:
                                                    _stream(self.device)))
         return out
 
+    def debug_cells(self, x, q2):
+        """(x cells, Q^2 cells, (x guided, Q^2 guided)) of the kernels' knot
+        searches at the points: a test hook."""
+        x = _f64_cuda(x, self.device)
+        q2 = _f64_cuda(q2, self.device)
+        n = x.numel()
+        xc = torch.empty(n, dtype=torch.int32, device=self.device)
+        qc = torch.empty(n, dtype=torch.int32, device=self.device)
+        guided = (C.c_int32 * 2)()
+        check("pdf_debug_cells", lib().pdf_debug_cells(self.handle, _ptr(x), _ptr(q2), n, _ptr(xc), _ptr(qc),
+                                                       guided, _stream(self.device)))
+        return xc, qc, (bool(guided[0]), bool(guided[1]))
+
 
 def mkPDF(grid, dirname=None, device="cuda:0", **kw) -> PDF:
     """Build a PDF object (PDFFlow Sec. 2.1 `mkPDF`): from an in-memory grid,

@@ -113,3 +113,51 @@ def test_out_of_device_memory_is_reported_and_leaves_nothing_behind(nn):
     p2 = PDF.from_grid(g)
     got = p2.xfxQ2(g.pids, torch.as_tensor(x, device="cuda"), torch.as_tensor(q2, device="cuda"))
     assert torch.equal(got, pdf.xfxQ2(g.pids, torch.as_tensor(x, device="cuda"), torch.as_tensor(q2, device="cuda")))
+
+
+def _expected_cells(g, x, q2):
+    """Largest cell whose lower knot is at or below the point (0 below the
+    grid, the last cell above it), on the x knots and on the Q cells of all
+    subgrids (a subgrid's last knot opens no cell: an internal threshold
+    belongs to the upper subgrid)."""
+    xk = np.asarray(g.x_knots)[:-1]
+    q2k = np.asarray(g.q_knots, dtype=np.float64) ** 2
+    lower, r0 = [], 0
+    for n in g.n_q:
+        lower.extend(q2k[r0:r0 + n - 1])
+        r0 += n
+    lower = np.array(lower)
+    xc = np.clip(np.searchsorted(xk, x, side="right") - 1, 0, xk.size - 1)
+    qc = np.clip(np.searchsorted(lower, q2, side="right") - 1, 0, lower.size - 1)
+    return xc, qc
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_knot_search_guided_and_bisected(clustered):
+    """The knot searches give the largest cell at or below each point, at
+    every knot, one ulp either side of it, on internal thresholds and
+    outside the grid: through the guide table on the NNPDF-shaped grid, and
+    by bisection on a grid whose x knots cluster within a few hundred ulps
+    (no guide width separates them) and whose Q^2 search keeps its guide."""
+    import math
+    from paper_2012_08221_gb300.pdf import PDF
+    g = synth.grid_nnpdf()
+    if clustered:
+        x = np.concatenate([[1e-9 * (1 + k * 1e-13) for k in range(5)], np.geomspace(1e-6, 1.0, 12)])
+        v = np.random.default_rng(70).uniform(0.1, 1.0, (1, g.values.shape[1], x.size, g.values.shape[3]))
+        g = synth.Grid(x, g.n_q, g.q_knots, g.pids, v, g.alphas, "clustered")
+    pdf = PDF.from_grid(g)
+    rng = np.random.default_rng(71)
+    xk = np.asarray(g.x_knots)
+    q2k = np.asarray(g.q_knots, dtype=np.float64) ** 2
+    xs = [np.exp(rng.uniform(math.log(xk[0]) - 2, 0.0, 200_000)), xk, np.nextafter(xk, 0), np.nextafter(xk, 2)]
+    qs = [np.exp(rng.uniform(math.log(q2k[0]) - 2, math.log(q2k[-1]) + 2, 200_000)), q2k,
+          np.nextafter(q2k, 0), np.nextafter(q2k, np.inf)]
+    x, q2 = np.minimum(np.concatenate(xs), 1.0), np.concatenate(qs)
+    n = max(x.size, q2.size)                     # every knot of both axes, paired cyclically
+    x, q2 = np.resize(x, n), np.resize(q2, n)
+    xc, qc, guided = pdf.debug_cells(x, q2)
+    assert guided == ((not clustered), True)
+    ex, eq = _expected_cells(g, x, q2)
+    assert np.array_equal(xc.cpu().numpy(), ex)
+    assert np.array_equal(qc.cpu().numpy(), eq)
