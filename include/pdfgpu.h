@@ -29,6 +29,14 @@
  *     Calls are asynchronous unless documented otherwise.
  *   - Arrays documented as HOST are read during the call (copied) unless
  *     documented otherwise.
+ *   - A grid handle holds state that some calls change while their kernels
+ *     run: the interpolation coefficients (pdf_bind_values, which the
+ *     differentiable bindings call), the adjoints' and the luminosity
+ *     adjoint's scratch (xfxQ2_backward*, pdf_lumi_backward) and the
+ *     host-buffer path's staging (xfxQ2_host, which serialises its own
+ *     callers).  Such calls on one handle from different streams or host
+ *     threads race unless the caller orders them; use one handle per stream
+ *     to run them concurrently.  The other calls only read the handle.
  *   - xfxQ2 and alphasQ2 (and their Q forms) may be captured in a CUDA graph
  *     on `stream` once a first call on the grid has run outside the capture
  *     (that call may raise a kernel's shared-memory limit, which a capture
