@@ -545,7 +545,10 @@ def main():
         A1 = torch.empty(n1, dtype=torch.float64, device=dev)
         flush = torch.empty(64 * 2 ** 20, dtype=torch.float32, device=dev)     # 256 MB > L2
 
-        def step1():
+        def step1():                     # alpha_s at the same Q^2: one launch
+            p1.xfxQ2_alphasQ2(g1.pids, X1, Q1, out=O1, alphas=A1)
+
+        def step1_two():
             p1.xfxQ2(g1.pids, X1, Q1, out=O1)
             p1.alphasQ2(Q1, out=A1)
 
@@ -567,6 +570,7 @@ def main():
             return max_ranks(statistics.mean(a.elapsed_time(b) for a, b in evs))
 
         ms1 = flushed(step1, 20)
+        ms1_two = flushed(step1_two, 20)
         graph1 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(graph1):
             step1()
@@ -576,8 +580,9 @@ def main():
                         f"{n1} points x {g1.n_flav} flavours + alpha_s at the same {n1} Q^2",
             "value": whole_job_rate(n1 * g1.n_flav, world, ms1), "unit": "evals/s", "ms_per_step": ms1,
             "ms_graph": ms1g, "value_graph": whole_job_rate(n1 * g1.n_flav, world, ms1g),
-            "fp64_frac": n1 * (work.xfxq2_point_flops(g1.n_flav) + work.alphas_point_flops())
-                         / (ms1 * 1e-3) / peak,
+            "entry_point": "xfxQ2_alphasQ2 (x*f and alpha_s at the same Q^2 in one launch)",
+            "two_calls": {"ms_per_step": ms1_two, "what": "xfxQ2 then alphasQ2 on the same arrays"},
+            "fp64_frac": n1 * (work.xfxq2_point_flops(g1.n_flav) + 6) / (ms1 * 1e-3) / peak,
             "l2": "flushed (256 MB write) before every timed step; the step's data fit in L2",
             "note": "1e5 points occupy about half of one wave of resident threads (152 SMs x 1280): "
                     "the time is mostly one thread's latency (11 patches after coefficient loads that "
