@@ -47,12 +47,20 @@ def cuda(a):
 
 
 def test_small_grid_full_workload(small):
+    """The small-grid workload in full, as the benchmark runs it: x*f of all
+    11 flavours and alpha_s at the same Q^2, in one launch (the same bits as
+    the two calls) and against the oracle."""
     g, pdf, o = small
     x, q2 = synth.queries_small()
-    got = pdf.xfxQ2(g.pids, cuda(x), cuda(q2)).cpu().numpy()
+    X, Q = cuda(x), cuda(q2)
+    got = pdf.xfxQ2(g.pids, X, Q)
     ref = o.xfxq2_batch(g.pids, x, q2)
     kap = o.kappa(g.pids, x, q2)
-    parity.check(got, ref, kap, what="small grid xfxQ2")
+    parity.check(got.cpu().numpy(), ref, kap, what="small grid xfxQ2")
+    out, a_s = pdf.xfxQ2_alphasQ2(g.pids, X, Q)
+    assert torch.equal(out.view(torch.int64), got.view(torch.int64))
+    assert torch.equal(a_s.view(torch.int64), pdf.alphasQ2(Q).view(torch.int64))
+    parity.check(a_s.cpu().numpy(), o.alphas_batch(q2), o.alphas_kappa(q2), what="small grid alpha_s")
     assert pdf.status() == 0
 
 
