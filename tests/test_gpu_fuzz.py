@@ -4,7 +4,8 @@ knots each (duplicated threshold rows equal or not), 1 to 14 flavours with
 random distinct pids (the gluon as 0 or 21), 1 to 3 members, every
 interpolation kind with the linear, freeze and error options.  Checked per
 grid: x*f for a pid list with an absent pid, the pointwise form, alpha_s, and
-the adjoint (dL/dx, dL/dQ^2, dL/dgrid, also through the tape)."""
+the adjoint (dL/dx, dL/dQ^2, dL/dgrid, also through the tape and the derivative
+tape)."""
 import math
 
 import numpy as np
@@ -58,10 +59,12 @@ def test_random_grid_against_the_oracle(seed):
                  what=f"fuzz {seed} pointwise")
     ra = o.alphas_batch(q2)
     parity.check(pdf.alphasQ2(Q).cpu().numpy(), ra, o.alphas_kappa(q2), what=f"fuzz {seed} alpha_s")
-    # the adjoint, pointwise, from scratch and from the tape
+    # the adjoint, pointwise, from scratch, from the tape and from the tape
+    # with the forward's patch derivatives
     w = rng.standard_normal(x.size)
     T = pdf.new_tape(x.size)
-    pdf.xfxQ2_pw(cuda(pid), X, Q, member, tape=T)
+    D = pdf.new_dtape(x.size)
+    pdf.xfxQ2_pw(cuda(pid), X, Q, member, tape=T, dtape=D)
     rdx, rdq = o.grad_pw(pid, x, q2, member=member)
     U, W = np.log(g.x_knots), np.log(g.q_knots ** 2)
     vmax = np.max(np.abs(g.values))
@@ -69,10 +72,10 @@ def test_random_grid_against_the_oracle(seed):
              "q": np.abs(w) * vmax * 8 / np.min(np.diff(W)[np.diff(W) > 0])}
     ref = o.dgrid_pw(pid, x, q2, w)
     kg = o.dgrid_pw(pid, x, q2, w, absval=True)
-    for tape in (None, T):
+    for tape, dtape in ((None, None), (T, None), (T, D)):
         gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
         gx, gq, _ = pdf.xfxQ2_backward(cuda(pid), X, Q, cuda(w), member=member, pointwise=True,
-                                       grad_values=gv, tape=tape)
+                                       grad_values=gv, tape=tape, dtape=dtape)
         for got, want, z, sc in ((gx, w * rdx, x, scale["x"]), (gq, w * rdq, q2, scale["q"])):
             got = got.cpu().numpy()
             assert np.array_equal(np.isnan(got), np.isnan(want)), seed
