@@ -707,6 +707,115 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum_m(GridDev g, Cols 
     if (cur >= 0) flush(cur);
 }
 
+// The same accumulation with the columns split between the two halves of a
+// warp (for 5 or more columns): the whole warp walks its segment's records
+// together, 16 at a time -- lanes 0-15 stage a record's 16 basis products
+// bq_n bx_m (9 multiplies, the rest are copies), lanes 16-31 its gout row --
+// and half h accumulates columns [h C, min(npid, (h + 1) C)), C = ceil(npid
+// / 2), lane s owning G[s >> 2][s & 3] of each.  Every record reaches both
+// halves, so a bin's run can span the whole segment and each half maps back
+// half of the columns: half as many map-backs per record as with the
+// records split between the halves, the same FMAs.
+constexpr int kHalfPids = kMaxSortedPids / 2;
+
+__global__ void __launch_bounds__(kAccWarps * 32) k_bwd_accum_mc(GridDev g, Cols cols, int npid,
+                                                                 const double *__restrict__ rec,
+                                                                 const int *__restrict__ offs, int nbins,
+                                                                 const double *__restrict__ gout,
+                                                                 double *__restrict__ gval)
+{
+    __shared__ double sW[kAccWarps][16][17];                   // a record's basis products (padded)
+    __shared__ double sGo[kAccWarps][16][kMaxSortedPids + 1];  // its gout row (padded)
+    __shared__ int sK[kAccWarps][16];
+    __shared__ double sG[kAccWarps][32];
+    __shared__ signed char scol[PDF_MAX_PIDS];
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < PDF_MAX_PIDS; ++k) scol[k] = cols.c[k];
+    }
+    __syncthreads();
+    const int F = g.nflav;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nvalid = offs[nbins];
+    const int64_t wbeg = ((int64_t)blockIdx.x * kAccWarps + wid) * kSegmentM;
+    if (wbeg >= nvalid) return;
+    const int wend = (int)min((int64_t)nvalid, wbeg + kSegmentM);
+    const int h = lane >> 4, s = lane & 15, sn = s >> 2, sm = s & 3;
+    const unsigned hmask = 0xFFFFu << (16 * h);
+    const int row0 = h * 16;
+    const int C = (npid + 1) / 2;
+    const int a0 = h * C;
+    const int na = min(npid - a0, C);
+    double acc[kHalfPids];
+#pragma unroll
+    for (int a = 0; a < kHalfPids; ++a) acc[a] = 0.0;
+    int cur = -1;
+    auto flush = [&](int b) {
+        const int cell = b >> 2, qc = cell / g.nxc, xc = cell - qc * g.nxc;
+        const double *Mq = ((b & 2) ? g.mqs : g.mq) + (size_t)qc * 16;
+        const double *Mx = ((b & 1) ? g.mxs : g.mx) + (size_t)xc * 16;
+        const int kk = xc - 1 + sm;
+        const bool ok = ((g.qmask[qc] >> sn) & 1) && kk >= 0 && kk < g.nx;
+        const int row = ok ? checked_index(g.status, g.qrow[qc] - 1 + sn, g.nrows) : 0;
+#pragma unroll
+        for (int a = 0; a < kHalfPids; ++a) {
+            if (a < na && scol[a0 + a] >= 0) {   // the same for the 16 lanes of a half
+                const double dv = map_back(acc[a], &sG[wid][row0], Mq, Mx, sn, sm, hmask);
+                if (ok && (dbits(dv) << 1)) {
+                    const int col = checked_index(g.status, scol[a0 + a], F);
+                    atomicAdd(gval + ((size_t)row * g.nx + kk) * F + col, dv);
+                }
+            }
+            acc[a] = 0.0;
+        }
+    };
+    for (int p = (int)wbeg; p < wend; p += 16) {
+        const int r = p + s;
+        int kr = -1;
+        if (r < wend) {
+            const D4 t = ld4(rec + 4 * (size_t)r);
+            const uint64_t bits = dbits(t.z);
+            kr = (int)(uint32_t)bits;
+            if (h == 0) {
+                const bool xin = (bits >> 32) & 1, qin = (bits >> 33) & 1;
+                const double tq2 = t.y * t.y, tx2 = t.x * t.x;
+                const double bq[4] = {1.0, t.y, qin ? tq2 : t.y, qin ? tq2 * t.y : t.y};
+                const double bx[4] = {1.0, t.x, xin ? tx2 : t.x, xin ? tx2 * t.x : t.x};
+                double *w = sW[wid][s];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) w[m] = bx[m];
+#pragma unroll
+                for (int n = 1; n < 4; ++n) {
+                    w[4 * n] = bq[n];
+#pragma unroll
+                    for (int m = 1; m < 4; ++m) w[4 * n + m] = bq[n] * bx[m];
+                }
+                sK[wid][s] = kr;
+            } else {
+                const double *go = gout + (size_t)(int64_t)dbits(t.w) * npid;
+                for (int a = 0; a < npid; ++a) sGo[wid][s][a] = go[a];
+            }
+        } else if (h == 0) {
+            sK[wid][s] = -1;
+        }
+        __syncwarp();
+        const int nb = min(16, wend - p);
+        for (int q = 0; q < nb; ++q) {
+            const int kq = sK[wid][q];
+            if (kq != cur) {
+                if (cur >= 0) flush(cur);
+                cur = kq;
+            }
+            const double w = sW[wid][q][s];
+#pragma unroll
+            for (int a = 0; a < kHalfPids; ++a)
+                if (a < na) acc[a] = fma(w, sGo[wid][q][a0 + a], acc[a]);
+        }
+        __syncwarp();
+    }
+    if (cur >= 0) flush(cur);
+}
+
 // The sorted adjoint, pointwise (PW: bins by cell and flavour) or matrix
 // form (bins by cell, up to kMaxSortedPids columns): per chunk of points, the
 // coordinates (without a forward tape), the counting pass, the scan, the
@@ -775,7 +884,11 @@ int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, cons
             k_bwd_rec_m<<<wave_grid(g, (const void *)k_bwd_rec_m, kBlock, 0, m), kBlock, 0, st>>>(
                 g->d, cols, npid, member, x, q2, i0, m, tv, gout, gx, gq, gval, nbins, cursor, rec);
             PDF_CUDA(cudaGetLastError());
-            k_bwd_accum_m<<<blocks, kAccWarps * 32, 0, st>>>(g->d, cols, npid, rec, offs, nbins, gout, gval);
+            if (npid >= 5)
+                k_bwd_accum_mc<<<blocks, kAccWarps * 32, 0, st>>>(g->d, cols, npid, rec, offs, nbins, gout,
+                                                                   gval);
+            else
+                k_bwd_accum_m<<<blocks, kAccWarps * 32, 0, st>>>(g->d, cols, npid, rec, offs, nbins, gout, gval);
         }
         PDF_CUDA(cudaGetLastError());
     }
