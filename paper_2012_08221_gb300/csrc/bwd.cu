@@ -39,6 +39,7 @@
 #include <algorithm>
 
 #include "pdf_internal.h"
+#include "sort_acc.cuh"
 
 using namespace pdfgpu;
 
@@ -391,29 +392,6 @@ __global__ void __launch_bounds__(kBlock, 5) k_bwd_rec(GridDev g, int member, co
         const int b = sorted_bin(g, X, Q, false, col, half_pair(X, Q), nbins);
         put_rec(rec, atomicAdd(&cursor[b], 1), near_coord(X.t), near_coord(Q.t), ga, b, X.in, Q.in);
     }
-}
-
-// Maps a half-warp's 16 accumulators back to the 16 stencil values of their
-// bin.  Lane 4n + m passes G[n][m] in g; lane 4j + i gets
-// sum_{n,m} Mq[n][j] G[n][m] Mx[m][i], in two stages through the half-warp's
-// 16 shared slots buf: T[j][m] = sum_n Mq[n][j] G[n][m] (lane 4j + m), then
-// sum_m T[j][m] Mx[m][i] -- 8 FMAs per lane.
-__device__ __forceinline__ double map_back(double g, double *buf, const double *__restrict__ Mq,
-                                           const double *__restrict__ Mx, int sn, int sm, unsigned hmask)
-{
-    buf[4 * sn + sm] = g;
-    __syncwarp(hmask);
-    double t = 0.0;
-#pragma unroll
-    for (int n = 0; n < 4; ++n) t = fma(Mq[n * 4 + sn], buf[4 * n + sm], t);
-    __syncwarp(hmask);
-    buf[4 * sn + sm] = t;
-    __syncwarp(hmask);
-    double dv = 0.0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) dv = fma(buf[4 * sn + m], Mx[m * 4 + sm], dv);
-    __syncwarp(hmask);
-    return dv;
 }
 
 // Accumulation over the sorted records.  Each warp takes a segment of

@@ -8,6 +8,7 @@
 #include <algorithm>
 
 #include "pdf_internal.h"
+#include "sort_acc.cuh"
 
 using namespace pdfgpu;
 
@@ -138,21 +139,35 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 // over each parton's 4x4 stencil.  Instead of 16 x F global atomics per
 // parton, partons are grouped by grid cell and accumulated in registers:
 //   1. k_lumi_rec: per event the two partons' F values (the partner factors)
-//      and, per parton, its cell key, local coordinates and range flags;
-//      a histogram of the keys;
-//   2. exclusive_scan: bin offsets;  3. k_scatter: parton ids in cell order;
-//   4. k_lumi_accum: each half-warp walks half of a warp's run of cell-sorted
-//      partons in batches of 16 (one parton per lane computes its 16 stencil
-//      weights and paired partner factors into shared memory); lane s of a
-//      half owns stencil slot s of the current cell for all F flavours and
-//      adds F FMAs per parton (both halves busy: F/2 warp instructions per
-//      parton); accumulators go to the gradient with one atomic per output
-//      when the cell changes.
+//      and, per parton, its bin key, local coordinates and range flags;
+//   2. k_lumi_count: a histogram of the keys; exclusive_scan: bin offsets;
+//      k_scatter_tiled: parton ids in bin order;
+//   4. k_lumi_accum: each half-warp walks half of a warp's run of sorted
+//      partons in batches of 16 (one parton per lane stages its 16 basis
+//      products and its partner factors, already paired, in shared
+//      memory); lane s of a half owns slot s of the current bin for all F
+//      flavours and adds F FMAs per parton; when the bin changes the
+//      accumulators go to the gradient with one atomic per output.
+// A bin is one cell and one kind: a parton inside the knot range on both
+// axes accumulates in the monomial basis of the patch, bq_n bx_m in the
+// near-knot coordinate of each axis (t, or 1 - t in the upper half of the
+// cell; kinds 0-3 by the two halves), and the bin maps its accumulators back
+// to the stencil values once per run (as the grid gradients of the x*f
+// adjoint do); a parton outside the range on either axis (kind 4) takes its
+// exact stencil weights, whose products are accumulated directly.
 // Events are processed in chunks so that the scratch stays bounded.
 
 constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;        // partons per warp
-constexpr int kMaxSmemBins = 12 * 1024;
+constexpr int kKinds = 5;             // bin kinds per cell: 4 half pairs inside, 1 outside
+constexpr int kCountSmemBins = 50 * 1024;  // bin counters in shared memory (one 1024-thread block per SM)
+constexpr int kCountBlock = 1024;
+
+__device__ __forceinline__ int parton_kind(const Axis &X, const Axis &Q)
+{
+    if (!(X.in && Q.in)) return 4;
+    return (upper_half(X.t) ? 1 : 0) | (upper_half(Q.t) ? 2 : 0);
+}
 
 template <bool PATCHES>
 __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
@@ -163,15 +178,8 @@ __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
                                                      const double *__restrict__ ln_x1, double ln_s,
                                                      int64_t e0, int m, int *__restrict__ key,
                                                      double *__restrict__ tx, double *__restrict__ tq,
-                                                     uint8_t *__restrict__ fin, double *__restrict__ P,
-                                                     int *__restrict__ hist, int nbins)
+                                                     uint8_t *__restrict__ fin, double *__restrict__ P)
 {
-    extern __shared__ int shist[];
-    const bool sh = nbins <= kMaxSmemBins;
-    if (sh) {
-        for (int k = threadIdx.x; k < nbins; k += blockDim.x) shist[k] = 0;
-        __syncthreads();
-    }
     const int F = g.nflav;
     const size_t cell_stride = (size_t)F * 16;
     const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
@@ -200,20 +208,41 @@ __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
                 p2[a] = patch(c2 + a * 16, X2, Q);
             }
         }
-        int k1 = Q.cell * g.nxc + X1.cell, k2 = Q.cell * g.nxc + X2.cell;
-        key[2 * i] = k1;
-        key[2 * i + 1] = k2;
+        const int cq = Q.cell * g.nxc;
+        key[2 * i] = (cq + X1.cell) * kKinds + parton_kind(X1, Q);
+        key[2 * i + 1] = (cq + X2.cell) * kKinds + parton_kind(X2, Q);
         tx[2 * i] = X1.t;
         tx[2 * i + 1] = X2.t;
         tq[i] = Q.t;
         fin[2 * i] = (uint8_t)(Q.in | (X1.in << 1));
         fin[2 * i + 1] = (uint8_t)(Q.in | (X2.in << 1));
-        if (sh) {
-            atomicAdd(&shist[k1], 1);
-            atomicAdd(&shist[k2], 1);
-        } else {
-            atomicAdd(&hist[k1], 1);
-            atomicAdd(&hist[k2], 1);
+    }
+}
+
+// Histogram of the chunk's bin keys (-1: no record), in shared memory when
+// the bins fit (one block of kCountBlock threads per SM, so the counters
+// are flushed once per SM), else with global atomics.
+__global__ void __launch_bounds__(kCountBlock) k_lumi_count(const int *__restrict__ key, int nrec,
+                                                            int *__restrict__ hist, int nbins,
+                                                            unsigned *status)
+{
+    extern __shared__ int shist[];
+    const bool sh = nbins <= kCountSmemBins;
+    if (sh) {
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x) shist[k] = 0;
+        __syncthreads();
+    }
+    const int stride = gridDim.x * blockDim.x;
+    for (int r0 = blockIdx.x * blockDim.x + threadIdx.x; r0 < nrec; r0 += 4 * stride) {
+        int k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = r0 + u * stride < nrec ? __ldg(key + r0 + u * stride) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k[u] < 0) continue;
+            const int b = checked_index(status, k[u], nbins);
+            if (sh) atomicAdd(&shist[b], 1);
+            else atomicAdd(&hist[b], 1);
         }
     }
     if (sh) {
@@ -232,14 +261,15 @@ __global__ void k_scatter(const int *__restrict__ key, int nrec, int *__restrict
     }
 }
 
-// The same scatter with one global atomic per (tile, cell) instead of one
-// per record: a block counts its tile's records per cell in shared memory,
-// reserves a range for each cell present, then places the records in their
-// ranges with shared-memory atomics.  The order inside a cell is free (the
-// accumulation sums the cell's records).  nbins <= kMaxSmemBins.
+// The same scatter with one global atomic per (tile, bin) instead of one
+// per record: a block counts its tile's records per bin in shared memory,
+// reserves a range for each bin present, then places the records in their
+// ranges with shared-memory atomics.  The order inside a bin is free (the
+// accumulation sums the bin's records).  nbins <= kCountSmemBins; one block
+// of kCountBlock threads per SM.
 constexpr int kScatterTile = 32768;
 
-__global__ void __launch_bounds__(kBlock) k_scatter_tiled(const int *__restrict__ key, int nrec, int nbins,
+__global__ void __launch_bounds__(kCountBlock) k_scatter_tiled(const int *__restrict__ key, int nrec, int nbins,
                                                           int *__restrict__ cursor, int *__restrict__ perm)
 {
     extern __shared__ int sc[];
@@ -286,12 +316,13 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
                                                                const double *__restrict__ P, double scale,
                                                                double *__restrict__ gval)
 {
-    // per warp: 32 staged partons (16 per half-warp), their 16 stencil
-    // weights and their partner factors already paired: sP[.][b] is the
-    // partner parton's value of the flavour paired with b (0 if none)
+    // per warp: 32 staged partons (16 per half-warp), their 16 basis products
+    // (or stencil weights) and their partner factors already paired: sP[.][b]
+    // is the partner parton's value of the flavour paired with b (0 if none)
     __shared__ double sW[kAccWarps][32][17];
     __shared__ double sP[kAccWarps][32][kF + 1];
     __shared__ int sK[kAccWarps][32];
+    __shared__ double sG[kAccWarps][32];                      // map-back slots, 16 per half
     __shared__ signed char santi[PDF_MAX_PIDS];
     if (threadIdx.x == 0) {
 #pragma unroll
@@ -305,8 +336,9 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
     if (wbeg >= nvalid) return;
     const int wend = (int)min((int64_t)nvalid, wbeg + kSegment);
     // the two half-warps walk the two halves of the warp's segment; a lane
-    // owns stencil slot s of its half's current cell for every flavour
+    // owns slot s = 4 j + i of its half's current bin for every flavour
     const int h = lane >> 4, s = lane & 15, j = s >> 2, i = s & 3;
+    const unsigned hmask = 0xFFFFu << (16 * h);
     const int half = (wend - (int)wbeg + 1) / 2;
     const int beg = (int)wbeg + h * half;
     const int end = h ? wend : (int)wbeg + half;
@@ -315,39 +347,67 @@ __global__ void __launch_bounds__(kAccWarps * 32) k_lumi_accum(GridDev g, Cols a
 #pragma unroll
     for (int b = 0; b < kF; ++b) acc[b] = 0.0;
     int cur = -1;
-    auto flush = [&](int cell) {
-        int qc = cell / g.nxc, xc = cell - qc * g.nxc;
-        int row = g.qrow[qc] - 1 + j, col = xc - 1 + i;
-        bool ok = ((g.qmask[qc] >> j) & 1) && col >= 0 && col < g.nx;
+    auto flush = [&](int bin) {
+        const int cell = bin / kKinds, kind = bin - cell * kKinds;
+        const int qc = cell / g.nxc, xc = cell - qc * g.nxc;
+        int row = g.qrow[qc] - 1 + j;
+        const int col = xc - 1 + i;
+        const bool ok = ((g.qmask[qc] >> j) & 1) && col >= 0 && col < g.nx;
         if (ok) row = checked_index(g.status, row, g.nrows);
+        const double *Mq = ((kind & 2) ? g.mqs : g.mq) + (size_t)qc * 16;
+        const double *Mx = ((kind & 1) ? g.mxs : g.mx) + (size_t)xc * 16;
 #pragma unroll
         for (int b = 0; b < kF; ++b) {
-            if (ok && b < F && santi[b] >= 0 && (dbits(acc[b]) << 1))
-                atomicAdd(gval + ((size_t)row * g.nx + col) * F + b, scale * acc[b]);
+            if (kF == kMaxLumiFlav && b >= F) break;       // the same for the whole warp
+            double v = acc[b];
+            if (kind < 4) v = map_back(v, &sG[wid][row0], Mq, Mx, j, i, hmask);   // the same for the half
+            if (ok && santi[b] >= 0 && (dbits(v) << 1))
+                atomicAdd(gval + ((size_t)row * g.nx + col) * F + b, scale * v);
             acc[b] = 0.0;
         }
     };
     const int steps = (half + 15) / 16;
     for (int step = 0; step < steps; ++step) {
         const int p = beg + step * 16;
-        // one parton per lane: stencil weights and the paired partner factors
+        // one parton per lane: basis products (or stencil weights) and the
+        // paired partner factors
         int r = p + s;
         int kr = -1;
         if (r < end) {
             int rec = perm[r];
             int e = rec >> 1, side = rec & 1;
-            kr = checked_index(g.status, key[rec], g.nqc * g.nxc);
-            int qc = kr / g.nxc, xc = kr - qc * g.nxc;
-            uint8_t f = fin[rec];
-            Axis Q = axis_from(qc, tq[e], f & 1);
-            Axis X = axis_from(xc, tx[rec], (f >> 1) & 1);
-            double Wq[4], Wx[4];
-            stencil_weights(g.mq + (size_t)qc * 16, g.mqs + (size_t)qc * 16, Q, Wq);
-            stencil_weights(g.mx + (size_t)xc * 16, g.mxs + (size_t)xc * 16, X, Wx);
+            kr = checked_index(g.status, key[rec], nbins);
+            const int cell = kr / kKinds, kind = kr - cell * kKinds;
+            const int qc = cell / g.nxc, xc = cell - qc * g.nxc;
+            double *w = sW[wid][row0 + s];
+            if (kind < 4) {
+                // the near-knot coordinates of the bin's halves and the
+                // products of their powers
+                const double a = (kind & 1) ? 1.0 - tx[rec] : tx[rec];
+                const double c = (kind & 2) ? 1.0 - tq[e] : tq[e];
+                const double a2 = a * a, c2 = c * c;
+                const double bx[4] = {1.0, a, a2, a2 * a};
+                const double bq[4] = {1.0, c, c2, c2 * c};
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
+                for (int m = 0; m < 4; ++m) w[m] = bx[m];
 #pragma unroll
-                for (int ii = 0; ii < 4; ++ii) sW[wid][row0 + s][jj * 4 + ii] = Wq[jj] * Wx[ii];
+                for (int n = 1; n < 4; ++n) {
+                    w[4 * n] = bq[n];
+#pragma unroll
+                    for (int m = 1; m < 4; ++m) w[4 * n + m] = bq[n] * bx[m];
+                }
+            } else {
+                uint8_t f = fin[rec];
+                Axis Q = axis_from(qc, tq[e], f & 1);
+                Axis X = axis_from(xc, tx[rec], (f >> 1) & 1);
+                double Wq[4], Wx[4];
+                stencil_weights(g.mq + (size_t)qc * 16, g.mqs + (size_t)qc * 16, Q, Wq);
+                stencil_weights(g.mx + (size_t)xc * 16, g.mxs + (size_t)xc * 16, X, Wx);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) w[jj * 4 + ii] = Wq[jj] * Wx[ii];
+            }
             const double *po = P + (size_t)e * 2 * F + (size_t)(1 - side) * F;
             for (int b = 0; b < F; ++b) {
                 int a = santi[b];
@@ -451,7 +511,9 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     if (n == 0) return PDF_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int F = g->d.nflav;
-    const int nbins = g->d.nqc * g->d.nxc;
+    const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * kKinds;
+    if (nbins64 >= (int64_t)1 << 30) return fail(PDF_E_RANGE, "grid too large for the luminosity adjoint");
+    const int nbins = (int)nbins64;
     const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 23);
     // scratch layout per chunk of m events
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
@@ -481,29 +543,33 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     int *offs = (int *)(base += bbins);
     int *cursor = (int *)(base += bbins);
     const double scale = dL / (double)n;
-    size_t hsmem = nbins <= kMaxSmemBins ? (size_t)nbins * sizeof(int) : 0;
+    const size_t hsmem = nbins <= kCountSmemBins ? (size_t)nbins * sizeof(int) : 0;
     const void *krec = saved_p ? (const void *)k_lumi_rec<false> : (const void *)k_lumi_rec<true>;
-    rc = allow_dynamic_smem(krec, hsmem);
+    rc = allow_dynamic_smem((const void *)k_lumi_count, hsmem);
     if (rc) return rc;
     rc = allow_dynamic_smem((const void *)k_scatter_tiled, hsmem);
     if (rc) return rc;
     for (int64_t e0 = 0; e0 < n; e0 += chunk) {
         const int m = (int)std::min(chunk, n - e0);
         PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
-        int grid = wave_grid(g, krec, kBlock, hsmem, m);
+        int grid = wave_grid(g, krec, kBlock, 0, m);
         const double *Pc = saved_p ? saved_p + (size_t)e0 * 2 * F : P;
         if (saved_p)
-            k_lumi_rec<false><<<grid, kBlock, hsmem, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
-                                                           e0, m, key, tx, tq, fin, nullptr, hist, nbins);
+            k_lumi_rec<false><<<grid, kBlock, 0, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
+                                                       e0, m, key, tx, tq, fin, nullptr);
         else
-            k_lumi_rec<true><<<grid, kBlock, hsmem, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
-                                                          e0, m, key, tx, tq, fin, P, hist, nbins);
+            k_lumi_rec<true><<<grid, kBlock, 0, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
+                                                      e0, m, key, tx, tq, fin, P);
+        PDF_CUDA(cudaGetLastError());
+        const int gc = std::min(g->sm_count, std::max(1, (int)((2 * (int64_t)m + 4 * kCountBlock - 1) /
+                                                               (4 * kCountBlock))));
+        k_lumi_count<<<gc, kCountBlock, hsmem, st>>>(key, 2 * m, hist, nbins, g->d.status);
         PDF_CUDA(cudaGetLastError());
         rc = exclusive_scan(hist, nbins, offs, cursor, st);
         if (rc) return rc;
         if (hsmem) {
             const int tiles = (int)((2 * (int64_t)m + kScatterTile - 1) / kScatterTile);
-            k_scatter_tiled<<<tiles, kBlock, hsmem, st>>>(key, 2 * m, nbins, cursor, perm);
+            k_scatter_tiled<<<tiles, kCountBlock, hsmem, st>>>(key, 2 * m, nbins, cursor, perm);
         } else {
             int gs = wave_grid(g, (const void *)k_scatter, kBlock, 0, 2 * (int64_t)m);
             k_scatter<<<gs, kBlock, 0, st>>>(key, 2 * m, cursor, perm);

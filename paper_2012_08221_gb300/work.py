@@ -106,10 +106,12 @@ LUMI_EVENT_BYTES = 8 + 8 + 1 + 16      # ln tau, y, flags in; lum, alpha_s out
 def lumi_bwd_event_flops(n_flav: int, saved: bool = False) -> int:
     """Adjoint of one event, as the kernels organise it: the kinematics and
     3 axes, the 2 F patch values (the partner factors; skipped when the
-    forward pass saved them), then per parton the stencil weights of its two
-    axes (2 x 12 FMA), their 16 products, and 16 F FMAs into the cell's
-    accumulators."""
-    per_parton = 2 * 12 * 2 + 16 + 16 * n_flav * 2
+    forward pass saved them), then per parton the products of the powers of
+    its two near-knot coordinates (4 multiplies for the powers, 9 for the
+    products) and 16 F FMAs into its bin's accumulators.  The map back per
+    bin run, and the stencil weights of the few partons outside the knot
+    range, are not counted."""
+    per_parton = 4 + 9 + 16 * n_flav * 2
     patches = 0 if saved else 2 * PATCH_FLOPS * n_flav
     return 4 + 3 * (AXIS_FLOPS + POWER_FLOPS) + patches + 2 * per_parton
 
