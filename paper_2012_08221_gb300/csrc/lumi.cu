@@ -142,7 +142,7 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 //      and, per parton, its bin key, local coordinates and range flags;
 //   2. k_lumi_count: a histogram of the keys; exclusive_scan: bin offsets;
 //      k_scatter_tiled: parton ids in bin order;
-//   4. k_lumi_accum: each half-warp walks half of a warp's run of sorted
+//   3. k_lumi_accum: each half-warp walks half of a warp's run of sorted
 //      partons in batches of 16 (one parton per lane stages its 16 basis
 //      products and its partner factors, already paired, in shared
 //      memory); lane s of a half owns slot s of the current bin for all F
