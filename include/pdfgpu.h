@@ -261,14 +261,17 @@ int xfxQ2_backward(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t
  *   every member of the grid.  PDF_E_ARG for a grid loaded with
  *   PDF_EXTRAP_CONTINUATION (which has no adjoint) and for a NULL tape
  *   when n > 0 (with n == 0 the calls do nothing, and the tape may be NULL).
- *   dtape (xfxQ2_pw_tape only; may be NULL) DEVICE [n][2] doubles,
- *   caller-owned, 16-byte aligned (PDF_E_ARG otherwise, and without a tape):
- *   the derivative tape, each point's patch derivatives in its two local
- *   coordinates (zeros for an absent pid), computed with the value (13 FMAs
- *   more per point) so that xfxQ2_backward_tape given it takes dL/dx and
- *   dL/dQ^2 without reloading the point's 16 coefficients.  Unlike the
- *   tape it depends on the values bound and on the member: it is valid only
- *   while the values of the forward call are bound, for the same member.
+ *   dtape (xfxQ2_pw_tape only; may be NULL) DEVICE, 20 bytes per point:
+ *   [n][2] doubles then [n] int32, caller-owned, 16-byte aligned (PDF_E_ARG
+ *   otherwise, and without a tape; PDF_E_RANGE for a grid of 2^28 or more
+ *   cell-flavour pairs): the derivative tape, each point's patch
+ *   derivatives in its two local coordinates (zeros for an absent pid),
+ *   computed with the value (13 FMAs more per point), and the point's bin
+ *   in the sorted grid gradient, so that xfxQ2_backward_tape given it takes
+ *   dL/dx and dL/dQ^2 without reloading the point's 16 coefficients and
+ *   counts its bins from 4 bytes per point.  Unlike the tape it depends on
+ *   the values bound and on the member: it is valid only while the values
+ *   of the forward call are bound, for the same member.
  * Outputs of the forward calls are bit for bit those of xfxQ2 / xfxQ2_pw. */
 int xfxQ2_tape(pdfgpu_grid_t g, int32_t member, const int32_t *pids, int32_t n_pid,
                const double *x, const double *q2, int64_t n, double *out, double *tape,

@@ -206,35 +206,6 @@ __device__ __forceinline__ void put_rec(double *__restrict__ rec, int pos, doubl
     d[1] = make_double2(ga, dfrom(bits));
 }
 
-// Half of a cell a point lies in along each axis: bit 0 set when t_x > 1/2,
-// bit 1 when t_q > 1/2.  In an upper half the accumulation runs in powers of
-// s = 1 - t (and maps back with the cell's matrix in s), so that the weights
-// that vanish at the near knot come out of small powers, not of cancelling
-// ones: a bin holds the points of one cell (and flavour) and one half pair.
-// (The tape records the same two bits, from the same t, for the counting
-// pass.)
-__device__ __forceinline__ int half_pair(const Axis &X, const Axis &Q)
-{
-    return (upper_half(X.t) ? 1 : 0) | (upper_half(Q.t) ? 2 : 0);
-}
-
-// The local coordinate the accumulation uses: t, or 1 - t in an upper half
-// (exact: t lies in [1/2, 1] there).
-__device__ __forceinline__ double near_coord(double t) { return upper_half(t) ? 1.0 - t : t; }
-
-// Bin of a point in the sorted accumulation, ((cell * F + flavour column) * 4
-// + half pair), or -1 for a point that adds nothing there: a domain error,
-// outside the grid under the error option, an absent pid, or outside the
-// knot range on either axis (see k_bwd_rec).  The counting pass and the
-// record pass both decide through this one function, on the same tape
-// values, so that every record placed was counted.
-__device__ __forceinline__ int sorted_bin(const GridDev &g, const Axis &X, const Axis &Q, bool bad, int col,
-                                          int halves, int nbins)
-{
-    if (bad || col < 0 || !(X.in && Q.in)) return -1;
-    return checked_index(g.status, ((Q.cell * g.nxc + X.cell) * g.nflav + col) * 4 + halves, nbins);
-}
-
 // Bin of a point in the matrix form's sorted accumulation: its cell and
 // half pair (all the call's flavours accumulate together), (cell * 4 + half
 // pair), or -1 as for sorted_bin.
@@ -334,6 +305,7 @@ __global__ void __launch_bounds__(kBlock, 5) k_bwd_rec(GridDev g, int member, co
                                                     const double *__restrict__ q2, int64_t i0, int m,
                                                     const double *__restrict__ tape,
                                                     const double *__restrict__ dtape,
+                                                    const int *__restrict__ dbins,
                                                     const double *__restrict__ gout,
                                                     double *__restrict__ gx, double *__restrict__ gq,
                                                     double *__restrict__ gval, int nbins,
@@ -389,7 +361,8 @@ __global__ void __launch_bounds__(kBlock, 5) k_bwd_rec(GridDev g, int member, co
             }
             continue;
         }
-        const int b = sorted_bin(g, X, Q, false, col, half_pair(X, Q), nbins);
+        const int b = DT ? checked_index(g.status, __ldg(dbins + i), nbins)
+                         : sorted_bin(g, X, Q, false, col, half_pair(X, Q), nbins);
         put_rec(rec, atomicAdd(&cursor[b], 1), near_coord(X.t), near_coord(Q.t), ga, b, X.in, Q.in);
     }
 }
@@ -806,6 +779,8 @@ int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, cons
     const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * (PW ? g->d.nflav : 1) * 4;
     if (nbins64 >= (int64_t)1 << 30) return fail(PDF_E_RANGE, "grid too large for the sorted adjoint");
     const int nbins = (int)nbins64;
+    // the derivative tape's bin words (pointwise form): after the n derivative pairs
+    const int *dbins = PW && dtape ? reinterpret_cast<const int *>(dtape + 2 * n) : nullptr;
     // points per round of count, records and accumulation ($PDFGPU_SORT_CHUNK
     // overrides the default; the scratch grows with it)
     int64_t chunk_max = kSortChunk;
@@ -844,9 +819,15 @@ int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, cons
             PDF_CUDA(cudaGetLastError());
         }
         PDF_CUDA(cudaMemsetAsync(hist, 0, (size_t)(nbins + 1) * sizeof(int), st));
-        const int gc = std::min(g->sm_count, std::max(1, (m + kCountIlp * kCountBlock - 1) / (kCountIlp * kCountBlock)));
-        k_bwd_count<PW><<<gc, kCountBlock, hsmem, st>>>(g->d, pid, tv, i0, m, hist, nbins);
-        PDF_CUDA(cudaGetLastError());
+        if (dbins) {   // the bins the forward pass wrote: 4 bytes per point to count
+            rc = key_histogram(dbins + i0, m, hist, nbins, g->d.status, g->sm_count, st);
+            if (rc) return rc;
+        } else {
+            const int gc =
+                std::min(g->sm_count, std::max(1, (m + kCountIlp * kCountBlock - 1) / (kCountIlp * kCountBlock)));
+            k_bwd_count<PW><<<gc, kCountBlock, hsmem, st>>>(g->d, pid, tv, i0, m, hist, nbins);
+            PDF_CUDA(cudaGetLastError());
+        }
         rc = exclusive_scan(hist, nbins, offs, cursor, st);
         if (rc) return rc;
         const int seg = PW ? kSegment : kSegmentM;
@@ -855,7 +836,7 @@ int backward_sorted(pdfgpu_grid *g, int member, const Cols &cols, int npid, cons
         if constexpr (PW) {
             auto krec = dtape ? k_bwd_rec<true> : k_bwd_rec<false>;
             krec<<<wave_grid(g, (const void *)krec, kBlock, 0, m), kBlock, 0, st>>>(
-                g->d, member, pid, x, q2, i0, m, tv, dtape, gout, gx, gq, gval, nbins, cursor, rec);
+                g->d, member, pid, x, q2, i0, m, tv, dtape, dbins, gout, gx, gq, gval, nbins, cursor, rec);
             PDF_CUDA(cudaGetLastError());
             k_bwd_accum<<<blocks, kAccWarps * 32, 0, st>>>(g->d, rec, offs, nbins, gval);
         } else {

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "pdf_internal.h"
+#include "sort_acc.cuh"
 
 using namespace pdfgpu;
 
@@ -139,14 +140,16 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pairs(GridDev g, Cols cols, in
 
 // DT (with TAPE): also keep each point's patch derivatives in t_x and t_q,
 // computed with the value (patch_vd: the value's bits are unchanged), in
-// dtape[i] = (dP/dtx, dP/dtq); zeros for an absent pid.
+// dtape[i] = (dP/dtx, dP/dtq) (zeros for an absent pid), and the point's bin
+// in the pointwise sorted adjoint in dbins[i] (-1 for none).
 template <bool CONT, bool TAPE, bool DT = false>
 __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
                                                      const int *__restrict__ pid,
                                                      const double *__restrict__ x,
                                                      const double *__restrict__ q2,
                                                      int64_t n, double *__restrict__ out,
-                                                     double *__restrict__ tape, double *__restrict__ dtape)
+                                                     double *__restrict__ tape, double *__restrict__ dtape,
+                                                     int *__restrict__ dbins, int nbins)
 {
     const size_t cell_stride = (size_t)g.nflav * 16;
     const double *cm = g.coef + (size_t)member * g.nqc * g.nxc * cell_stride;
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(kBlock) k_xfxq2_pw(GridDev g, int member,
             double dtx = 0.0, dtq = 0.0;
             if (col >= 0) v = patch_vd(cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q, &dtx, &dtq);
             reinterpret_cast<double2 *>(dtape)[i] = make_double2(dtx, dtq);
+            dbins[i] = sorted_bin(g, X, Q, bad, col, half_pair(X, Q), nbins);
         } else if (col >= 0) {
             v = patch_any<CONT>(g, cm + ((size_t)Q.cell * g.nxc + X.cell) * cell_stride + col * 16, X, Q);
         }
@@ -382,13 +386,17 @@ int launch_pw(pdfgpu_grid *g, int32_t member, const int32_t *pid, const double *
     if (rc) return rc;
     if (dtape && !tape) return fail(PDF_E_ARG, "a derivative tape goes with a tape");
     if (dtape && (uintptr_t)dtape % 16) return fail(PDF_E_ARG, "derivative tape must be 16-byte aligned");
+    const int64_t nbins64 = (int64_t)g->d.nqc * g->d.nxc * g->d.nflav * 4;   // the pointwise adjoint's bins
+    if (dtape && nbins64 >= (int64_t)1 << 30) return fail(PDF_E_RANGE, "grid too large for the derivative tape");
     if (n == 0) return PDF_OK;
     if (!pid || !x || !q2 || !out) return fail(PDF_E_ARG, "null array");
     auto k = dtape  ? k_xfxq2_pw<false, true, true>
              : tape ? k_xfxq2_pw<false, true>
              : g->d.extrap == PDF_EXTRAP_CONTINUATION ? k_xfxq2_pw<true, false> : k_xfxq2_pw<false, false>;
     int grid = wave_grid(g, (const void *)k, kBlock, 0, n);
-    k<<<grid, kBlock, 0, s>>>(g->d, member, pid, x, q2, n, out, tape, dtape);
+    int *dbins = dtape ? reinterpret_cast<int *>(dtape + 2 * n) : nullptr;
+    k<<<grid, kBlock, 0, s>>>(g->d, member, pid, x, q2, n, out, tape, dtape, dbins,
+                              (int)std::min<int64_t>(nbins64, (int64_t)1 << 30));
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }

@@ -140,7 +140,7 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 // parton, partons are grouped by grid cell and accumulated in registers:
 //   1. k_lumi_rec: per event the two partons' F values (the partner factors)
 //      and, per parton, its bin key, local coordinates and range flags;
-//   2. k_lumi_count: a histogram of the keys; exclusive_scan: bin offsets;
+//   2. key_histogram: a histogram of the keys; exclusive_scan: bin offsets;
 //      k_scatter_tiled: parton ids in bin order;
 //   3. k_lumi_accum: each half-warp walks half of a warp's run of sorted
 //      partons in batches of 16 (one parton per lane stages its 16 basis
@@ -160,8 +160,8 @@ __global__ void k_lumi_final(const double *__restrict__ partials, int nb, double
 constexpr int kAccWarps = 4;
 constexpr int kSegment = 1024;        // partons per warp
 constexpr int kKinds = 5;             // bin kinds per cell: 4 half pairs inside, 1 outside
-constexpr int kCountSmemBins = 50 * 1024;  // bin counters in shared memory (one 1024-thread block per SM)
-constexpr int kCountBlock = 1024;
+constexpr int kScatterSmemBins = 50 * 1024;  // bin counters of the scatter in shared memory
+constexpr int kScatterBlock = 1024;         // (one 1024-thread block per SM)
 
 __device__ __forceinline__ int parton_kind(const Axis &X, const Axis &Q)
 {
@@ -219,39 +219,6 @@ __global__ void __launch_bounds__(kBlock) k_lumi_rec(GridDev g, int member,
     }
 }
 
-// Histogram of the chunk's bin keys (-1: no record), in shared memory when
-// the bins fit (one block of kCountBlock threads per SM, so the counters
-// are flushed once per SM), else with global atomics.
-__global__ void __launch_bounds__(kCountBlock) k_lumi_count(const int *__restrict__ key, int nrec,
-                                                            int *__restrict__ hist, int nbins,
-                                                            unsigned *status)
-{
-    extern __shared__ int shist[];
-    const bool sh = nbins <= kCountSmemBins;
-    if (sh) {
-        for (int k = threadIdx.x; k < nbins; k += blockDim.x) shist[k] = 0;
-        __syncthreads();
-    }
-    const int stride = gridDim.x * blockDim.x;
-    for (int r0 = blockIdx.x * blockDim.x + threadIdx.x; r0 < nrec; r0 += 4 * stride) {
-        int k[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) k[u] = r0 + u * stride < nrec ? __ldg(key + r0 + u * stride) : -1;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (k[u] < 0) continue;
-            const int b = checked_index(status, k[u], nbins);
-            if (sh) atomicAdd(&shist[b], 1);
-            else atomicAdd(&hist[b], 1);
-        }
-    }
-    if (sh) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < nbins; k += blockDim.x)
-            if (shist[k]) atomicAdd(&hist[k], shist[k]);
-    }
-}
-
 __global__ void k_scatter(const int *__restrict__ key, int nrec, int *__restrict__ cursor,
                           int *__restrict__ perm)
 {
@@ -265,11 +232,11 @@ __global__ void k_scatter(const int *__restrict__ key, int nrec, int *__restrict
 // per record: a block counts its tile's records per bin in shared memory,
 // reserves a range for each bin present, then places the records in their
 // ranges with shared-memory atomics.  The order inside a bin is free (the
-// accumulation sums the bin's records).  nbins <= kCountSmemBins; one block
-// of kCountBlock threads per SM.
+// accumulation sums the bin's records).  nbins <= kScatterSmemBins; one block
+// of kScatterBlock threads per SM.
 constexpr int kScatterTile = 32768;
 
-__global__ void __launch_bounds__(kCountBlock) k_scatter_tiled(const int *__restrict__ key, int nrec, int nbins,
+__global__ void __launch_bounds__(kScatterBlock) k_scatter_tiled(const int *__restrict__ key, int nrec, int nbins,
                                                           int *__restrict__ cursor, int *__restrict__ perm)
 {
     extern __shared__ int sc[];
@@ -543,10 +510,8 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
     int *offs = (int *)(base += bbins);
     int *cursor = (int *)(base += bbins);
     const double scale = dL / (double)n;
-    const size_t hsmem = nbins <= kCountSmemBins ? (size_t)nbins * sizeof(int) : 0;
+    const size_t hsmem = nbins <= kScatterSmemBins ? (size_t)nbins * sizeof(int) : 0;
     const void *krec = saved_p ? (const void *)k_lumi_rec<false> : (const void *)k_lumi_rec<true>;
-    rc = allow_dynamic_smem((const void *)k_lumi_count, hsmem);
-    if (rc) return rc;
     rc = allow_dynamic_smem((const void *)k_scatter_tiled, hsmem);
     if (rc) return rc;
     for (int64_t e0 = 0; e0 < n; e0 += chunk) {
@@ -561,15 +526,13 @@ extern "C" int pdf_lumi_backward(pdfgpu_grid_t g, int32_t member, const double *
             k_lumi_rec<true><<<grid, kBlock, 0, st>>>(g->d, member, ln_tau, y, flags, ln_mu2, ln_x1, ln_s,
                                                       e0, m, key, tx, tq, fin, P);
         PDF_CUDA(cudaGetLastError());
-        const int gc = std::min(g->sm_count, std::max(1, (int)((2 * (int64_t)m + 4 * kCountBlock - 1) /
-                                                               (4 * kCountBlock))));
-        k_lumi_count<<<gc, kCountBlock, hsmem, st>>>(key, 2 * m, hist, nbins, g->d.status);
-        PDF_CUDA(cudaGetLastError());
+        rc = key_histogram(key, 2 * (int64_t)m, hist, nbins, g->d.status, g->sm_count, st);
+        if (rc) return rc;
         rc = exclusive_scan(hist, nbins, offs, cursor, st);
         if (rc) return rc;
         if (hsmem) {
             const int tiles = (int)((2 * (int64_t)m + kScatterTile - 1) / kScatterTile);
-            k_scatter_tiled<<<tiles, kCountBlock, hsmem, st>>>(key, 2 * m, nbins, cursor, perm);
+            k_scatter_tiled<<<tiles, kScatterBlock, hsmem, st>>>(key, 2 * m, nbins, cursor, perm);
         } else {
             int gs = wave_grid(g, (const void *)k_scatter, kBlock, 0, 2 * (int64_t)m);
             k_scatter<<<gs, kBlock, 0, st>>>(key, 2 * m, cursor, perm);

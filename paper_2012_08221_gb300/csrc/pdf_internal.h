@@ -88,10 +88,18 @@ struct Cols {
 };
 int resolve_cols(const pdfgpu_grid *g, const int32_t *pids, int32_t n_pid, Cols *cols);
 
-// Exclusive scan of a bin histogram (one block on `s`): offs[k] = cursor[k] =
+// Exclusive scan of a bin histogram (on `s`): offs[k] = cursor[k] =
 // sum of hist[0..k), offs[nbins] = the total.  offs and cursor hold nbins + 1
 // and nbins ints.
 int exclusive_scan(const int *hist, int nbins, int *offs, int *cursor, cudaStream_t s);
+
+// Histogram of n bin keys (a negative key adds nothing) into hist[0..nbins),
+// which the caller has zeroed: in shared memory, one block of 1024 threads
+// per SM (sm_count blocks at most), when the bins fit in 50 * 1024 counters,
+// else with global atomics.  A key >= nbins sets PDF_S_BOUNDS in the checked
+// build.
+int key_histogram(const int *keys, int64_t n, int *hist, int nbins, unsigned *status, int sm_count,
+                  cudaStream_t s);
 
 // Shared argument checks.
 int check_grid(const pdfgpu_grid *g, bool need_values);

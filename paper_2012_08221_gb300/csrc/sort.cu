@@ -3,6 +3,8 @@
 // bin histogram into bin offsets.
 #include "pdf_internal.h"
 
+#include <algorithm>
+
 namespace {
 
 constexpr int kScanBlock = 1024;
@@ -127,9 +129,57 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_blocks(const int *__restric
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) offs[nbins] = c;
 }
 
+constexpr int kHistBlock = 1024;
+constexpr int kHistSmemBins = 50 * 1024;   // 200 KB of counters, one block per SM
+
+// Histogram of the keys, four loads in flight per thread; counters in
+// shared memory (flushed once per block) when they fit.
+__global__ void __launch_bounds__(kHistBlock) k_key_hist(const int *__restrict__ keys, int64_t n,
+                                                         int *__restrict__ hist, int nbins, unsigned *status)
+{
+    extern __shared__ int shist[];
+    const bool sh = nbins <= kHistSmemBins;
+    if (sh) {
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x) shist[k] = 0;
+        __syncthreads();
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r0 < n; r0 += 4 * stride) {
+        int k[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) k[u] = r0 + u * stride < n ? __ldg(keys + r0 + u * stride) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (k[u] < 0) continue;
+            const int b = pdfgpu::checked_index(status, k[u], nbins);
+            if (sh) atomicAdd(&shist[b], 1);
+            else atomicAdd(&hist[b], 1);
+        }
+    }
+    if (sh) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+            if (shist[k]) atomicAdd(&hist[k], shist[k]);
+    }
+}
+
 }  // namespace
 
 namespace pdfgpu {
+
+int key_histogram(const int *keys, int64_t n, int *hist, int nbins, unsigned *status, int sm_count,
+                  cudaStream_t s)
+{
+    if (n <= 0) return PDF_OK;
+    const size_t smem = nbins <= kHistSmemBins ? (size_t)nbins * sizeof(int) : 0;
+    int rc = allow_dynamic_smem((const void *)k_key_hist, smem);
+    if (rc) return rc;
+    const int64_t want = (n + 4 * kHistBlock - 1) / (4 * kHistBlock);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count, want));
+    k_key_hist<<<grid, kHistBlock, smem, s>>>(keys, n, hist, nbins, status);
+    PDF_CUDA(cudaGetLastError());
+    return PDF_OK;
+}
 
 int exclusive_scan(const int *hist, int nbins, int *offs, int *cursor, cudaStream_t s)
 {

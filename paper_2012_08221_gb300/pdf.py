@@ -178,14 +178,27 @@ class PDF:
         """Device buffer for the adjoint tape of ``n`` points (32 bytes each)."""
         return torch.empty((n, 4), dtype=torch.float64, device=self.device)
 
+    @staticmethod
+    def dtape_doubles(n):
+        """Size in doubles of a derivative tape of ``n`` points: 2 n doubles of
+        patch derivatives, then n int32 bins (20 bytes per point)."""
+        return 2 * n + (n + 1) // 2
+
     def new_dtape(self, n):
-        """Device buffer for the derivative tape of ``n`` pointwise points (16
-        bytes each): the patch derivatives the forward keeps for the adjoint."""
-        return torch.empty((n, 2), dtype=torch.float64, device=self.device)
+        """Device buffer for the derivative tape of ``n`` pointwise points (20
+        bytes each): the patch derivatives and the accumulation bin the
+        forward keeps for the adjoint.  ``dtape[:2 * n].view(n, 2)`` are the
+        derivatives."""
+        return torch.empty(self.dtape_doubles(n), dtype=torch.float64, device=self.device)
 
     def _check_tape(self, tape, n, per_point=4):
         assert tape.dtype == torch.float64 and tape.is_cuda and tape.is_contiguous(), "tape: contiguous float64"
         assert tape.numel() >= per_point * n, f"tape too small ({per_point} doubles per point)"
+
+    def _check_dtape(self, dtape, n):
+        assert dtape.dtype == torch.float64 and dtape.is_cuda and dtape.is_contiguous(), \
+            "derivative tape: contiguous float64"
+        assert dtape.numel() >= self.dtape_doubles(n), "derivative tape too small (20 bytes per point)"
 
     def xfxQ2_pw(self, pid, x, q2, member=0, out=None, tape=None, dtape=None):
         """One pid per point: ``out[i] = x*f_{pid_i}(x_i, Q^2_i)``; ``tape`` as
@@ -200,7 +213,7 @@ class PDF:
         if tape is not None:
             self._check_tape(tape, n)
             if dtape is not None:
-                self._check_tape(dtape, n, 2)
+                self._check_dtape(dtape, n)
             check("xfxQ2_pw_tape", lib().xfxQ2_pw_tape(self.handle, int(member), _ptr(pid), _ptr(x), _ptr(q2),
                                                        n, _ptr(out), _ptr(tape), _ptr(dtape),
                                                        _stream(self.device)))
@@ -277,7 +290,7 @@ class PDF:
         if tape is not None:
             self._check_tape(tape, n)
             if dtape is not None:
-                self._check_tape(dtape, n, 2)
+                self._check_dtape(dtape, n)
             check("xfxQ2_backward_tape", lib().xfxQ2_backward_tape(
                 self.handle, int(member), pp, npid, int(bool(pointwise)), _ptr(x), _ptr(q2), n,
                 _ptr(tape), _ptr(dtape), _ptr(gout), _ptr(gx), _ptr(gq), _ptr(grad_values),

@@ -59,7 +59,7 @@ def main():
             gd = torch.zeros_like(gv)
             gxd, gqd, _ = p.xfxQ2_backward(pid, X, Q, torch.ones(x.size, dtype=torch.float64, device=dev),
                                            pointwise=True, grad_values=gd, tape=T, dtape=D)
-            res += [D.flatten(), gxd, gqd]
+            res += [D[:2 * x.size], D[2 * x.size:].view(torch.int32)[:x.size], gxd, gqd]
             # the matrix form's sorted adjoint (up to 16 columns)
             gm = torch.zeros_like(gv)
             pm = np.array([g.pids[0], 21, 9], dtype=np.int32)                  # 9: absent
@@ -80,7 +80,8 @@ def main():
         u = torch.as_tensor(np.random.default_rng(64).uniform(0, 1, (40_000, 2)), device=dev)
         VegasLumi(p, math.log(1e-6), 2 * math.log(13000.0), n_bins=40).iteration(u)
         torch.cuda.synchronize()
-        out[extrap] = {"status": p.status(), "digest": digest(*[r for r in res if r.dtype == torch.float64])}
+        out[extrap] = {"status": p.status(),
+                       "digest": digest(*[r for r in res if r.dtype in (torch.float64, torch.int32)])}
     vg = Vegas(3, n_bins=20)
     r, jac, bins = vg.map(torch.rand((20_000, 3), dtype=torch.float64, device=dev))
     vg.accumulate(jac, bins)

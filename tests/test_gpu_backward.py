@@ -392,7 +392,10 @@ def test_tape_gives_the_same_forward_and_adjoint(extrap):
                 gx3, gq3, _ = pdf.xfxQ2_backward(ids, X, Q, gout, pointwise=True, tape=T, dtape=D)
                 assert same(gx3, gx0) and same(gq3, gq0)
                 absent = (pid == 7).nonzero().flatten()
-                assert bool((D[absent] == 0).all())
+                n = x.size
+                assert bool((D[:2 * n].view(n, 2)[absent] == 0).all())
+                bins = D[2 * n:].view(torch.int32)[:n]
+                assert bool((bins[absent] == -1).all()) and bool((bins[[0, 1, 2, 4, 5, 6]] == -1).all())
         torch.cuda.synchronize()
 
 
@@ -482,7 +485,7 @@ def test_tape_arguments_are_checked():
     from paper_2012_08221_gb300.pdf import _ptr, _stream
     T = pdf.new_tape(x.size)
     D = pdf.new_dtape(x.size)
-    dbuf = torch.empty(2 * x.size + 2, dtype=torch.float64, device="cuda")
+    dbuf = torch.empty(pdf.dtape_doubles(x.size) + 2, dtype=torch.float64, device="cuda")
     out = torch.empty(x.size, dtype=torch.float64, device="cuda")
     gout = cuda(np.ones(x.size))
     st = _stream(pdf.device)
