@@ -600,7 +600,7 @@ def main():
         GV = torch.zeros(gs.values.shape[1:], dtype=torch.float64, device=dev)
 
         T3 = p3.new_tape(x3.size)            # the forward's adjoint tape (32 B per point)
-        D3 = p3.new_dtape(x3.size)           # and its patch derivatives (16 B per point)
+        D3 = p3.new_dtape(x3.size)           # its patch derivatives and bins (20 B per point)
 
         def step3():
             p3.bind_values(V3)
@@ -664,8 +664,9 @@ def main():
                            "frac": n3 * work.pw_bwd_sorted_point_flops(dtape=True) / (kb * 1e-3) / peak,
                            "frac_separable_count": n3 * work.pw_bwd_point_flops_separable() / (kb * 1e-3) / peak},
             "tape": "the forward pass writes 32 bytes per point (cells, local coordinates, flags) that the "
-                    "adjoint reads instead of searching the knots and taking logarithms again, and 16 bytes "
-                    "of patch derivatives (computed with the value) that spare the adjoint the coefficients",
+                    "adjoint reads instead of searching the knots and taking logarithms again, and 20 bytes "
+                    "of patch derivatives (computed with the value) and the point's bin, which spare the "
+                    "adjoint the coefficients and let it count its bins from 4 bytes per point",
             "direct_calls": {"ms_per_step": ms3, "value": world * n3 / (ms3 * 1e-3),
                              "what": "the same two library calls without autograd (no torch "
                                      "multiply, sum or gradient accumulation)"},

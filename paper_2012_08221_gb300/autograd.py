@@ -7,9 +7,10 @@ returns dL/dx, dL/dQ^2 and the scatter of the 16 bicubic stencil weights
 into dL/dvalues (the derivative a PDF fit needs).  The forward keeps a
 32-byte adjoint tape per point (cells, local coordinates, flags), so that the
 backward does not search the knots or take logarithms again; in the pointwise
-form, when x or Q^2 needs a gradient, also the 16-byte derivative tape (the
-patch derivatives, computed with the value), so that the backward does not
-reload the coefficients and needs no rebinding.  ``LumiFn`` does the same
+form, when x or Q^2 needs a gradient, also the 20-byte derivative tape (the
+patch derivatives, computed with the value, and the point's bin in the grid
+gradient), so that the backward does not reload the coefficients, counts its
+bins from 4 bytes per point and needs no rebinding.  ``LumiFn`` does the same
 for the fused luminosity workload, L = (1/n) sum_e sum_a f_a(x1) f_-a(x2).
 
 The coefficients live in ONE table per PDF handle, rebuilt by every forward and
