@@ -209,6 +209,18 @@ def test_pointwise_grid_gradient_large_grid_and_edges():
     dW = np.diff(W)
     _check(gx.cpu().numpy(), w * rdx, np.abs(w) * 4 * kap / (np.min(np.diff(U)) * x), "NNPDF dL/dx")
     _check(gq.cpu().numpy(), w * rdq, np.abs(w) * 4 * kap / (np.min(dW[dW > 0]) * q2), "NNPDF dL/dQ2")
+    # the same from the forward's tapes: its bins (466k of them) are counted in
+    # global memory too, and dL/dx, dL/dQ^2 keep their bits
+    X, Q = cuda(x), cuda(q2)
+    T, D = pdf.new_tape(x.size), pdf.new_dtape(x.size)
+    pdf.xfxQ2_pw(cuda(pid), X, Q, tape=T, dtape=D)
+    gv2 = torch.zeros_like(gv)
+    gx2, gq2, _ = pdf.xfxQ2_backward(cuda(pid), X, Q, cuda(w), pointwise=True, grad_values=gv2, tape=T, dtape=D)
+    same = lambda a, b: torch.equal(torch.nan_to_num(a, nan=7.0), torch.nan_to_num(b, nan=7.0))
+    assert same(gx2, gx) and same(gq2, gq)
+    _check(gv2.cpu().numpy(), o.dgrid_pw(pid, x, q2, w), o.dgrid_pw(pid, x, q2, w, absval=True),
+           "NNPDF pointwise dL/dvalues from the tapes", floor=1e-14 * np.abs(w).sum())
+    assert pdf.status() & 4 == 0                     # no bin out of range (checked builds)
 
 
 def test_pointwise_grid_gradient_in_several_sort_rounds(diffgrid, monkeypatch):
