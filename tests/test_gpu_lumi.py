@@ -130,6 +130,27 @@ def test_luminosity_gradient_near_the_knots(lhc):
     assert np.count_nonzero(ref) > 0
 
 
+def test_luminosity_gradient_on_a_grid_with_more_bins_than_shared_memory():
+    """A grid of 400 x knots and the NNPDF Q subgrids: 399 x 46 cells x 5
+    bin kinds are more than the shared-memory counters of the histogram and
+    the scatter hold, so both take their global-memory paths; the gradient
+    against the oracle (events with the low tail)."""
+    from paper_2012_08221_gb300.lumi import DeviceEvents, luminosity_backward
+    from paper_2012_08221_gb300.pdf import PDF
+    xk = synth.log_knots(1e-9, 1.0, 400)
+    qk, nq = synth.subgrid_knots([1.0, 1.51, 4.92, 172.5, 1e5], [8, 12, 20, 10])
+    g = synth._grid("lumi-400x50", xk, qk, nq, synth.PIDS_13, [1009])
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    ev = synth.events_lhc(20_001, seed=95)
+    gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+    luminosity_backward(pdf, DeviceEvents.from_host(ev), 1.0, gv)
+    ref = o.lumi_dgrid(ev)
+    got = gv.cpu().numpy()
+    tol = 1e-9 * np.maximum(np.abs(ref), o.lumi_dgrid(ev, absval=True)) + 1e-300
+    assert np.all(np.abs(got - ref) <= tol), float(np.max(np.abs(got - ref) / tol))
+    assert pdf.status() & 4 == 0
+
+
 def test_saved_partner_factors_give_the_same_gradient(lhc):
     """The backward pass from the forward's saved partner factors equals the
     one that recomputes them (up to the summation order of the atomics)."""
