@@ -223,6 +223,27 @@ def test_pointwise_grid_gradient_large_grid_and_edges():
     assert pdf.status() & 4 == 0                     # no bin out of range (checked builds)
 
 
+def test_pointwise_grid_gradient_with_more_bins_than_the_block_scan_takes():
+    """400 x knots and the NNPDF Q subgrids, 13 flavours: 954k bins, more than
+    the scan's one block per 8192 bins goes to (64 blocks), so one block
+    scans them all in passes; from the tapes and without."""
+    from paper_2012_08221_gb300.pdf import PDF
+    xk = synth.log_knots(1e-9, 1.0, 400)
+    qk, nq = synth.subgrid_knots([1.0, 1.51, 4.92, 172.5, 1e5], [8, 12, 20, 10])
+    g = synth._grid("pw-400x50", xk, qk, nq, synth.PIDS_13, [1010])
+    pdf, o = PDF.from_grid(g), OracleGrid.from_synth(g)
+    pid, x, q2, w = _pw_points_with_edges(g, 20_011, 48)
+    X, Q = cuda(x), cuda(q2)
+    ref = o.dgrid_pw(pid, x, q2, w)
+    mag = o.dgrid_pw(pid, x, q2, w, absval=True)
+    T, D = pdf.new_tape(x.size), pdf.new_dtape(x.size)
+    pdf.xfxQ2_pw(cuda(pid), X, Q, tape=T, dtape=D)
+    for tape, dtape in ((None, None), (T, D)):
+        gv = torch.zeros(g.values.shape[1:], dtype=torch.float64, device="cuda")
+        pdf.xfxQ2_backward(cuda(pid), X, Q, cuda(w), pointwise=True, grad_values=gv, tape=tape, dtape=dtape)
+        _check(gv.cpu().numpy(), ref, mag, "400x50 pointwise dL/dvalues", floor=1e-14 * np.abs(w).sum())
+
+
 def test_pointwise_grid_gradient_in_several_sort_rounds(diffgrid, monkeypatch):
     """The sorted adjoint works in rounds of at most $PDFGPU_SORT_CHUNK points:
     with rounds of 1000 points (several rounds, a ragged last one), with and
