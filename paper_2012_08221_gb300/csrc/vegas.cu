@@ -160,15 +160,21 @@ __global__ void __launch_bounds__(kBlock) k_vegas_map(int dim, int n_bins, const
 // Sums of one iteration from the caller's weights: per block, sum w and
 // sum (w - shift)^2 by shuffles and the per-bin sums of w^2 in shared
 // memory, then one atomic per nonzero block total.
+// PER_WARP: each warp adds into its own copy of the per-bin sums (fewer
+// lanes of different warps waiting on one shared-memory address), the
+// copies summed per block at the end.
+template <bool PER_WARP>
 __global__ void __launch_bounds__(kBlock) k_vegas_accumulate(int dim, int n_bins, const double *__restrict__ w,
                                                              const int *__restrict__ bins, int64_t n,
                                                              double shift, double *__restrict__ sums)
 {
-    extern __shared__ double sb[];           // [dim][n_bins]
+    extern __shared__ double sb_all[];       // [copies][dim][n_bins]
     __shared__ double red[2][kBlock / 32];
     const int nsb = dim * n_bins;
-    for (int k = threadIdx.x; k < nsb; k += blockDim.x) sb[k] = 0.0;
+    const int copies = PER_WARP ? kBlock / 32 : 1;
+    for (int k = threadIdx.x; k < copies * nsb; k += blockDim.x) sb_all[k] = 0.0;
     __syncthreads();
+    double *sb = sb_all + (PER_WARP ? (threadIdx.x >> 5) * nsb : 0);
     double s1 = 0.0, s2 = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -198,8 +204,12 @@ __global__ void __launch_bounds__(kBlock) k_vegas_accumulate(int dim, int n_bins
         atomicAdd(&sums[0], t1);
         atomicAdd(&sums[1], t2);
     }
-    for (int k = threadIdx.x; k < nsb; k += blockDim.x)
-        if (dbits(sb[k]) << 1) atomicAdd(&sums[2 + k], sb[k]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nsb; k += blockDim.x) {
+        double t = sb_all[k];
+        for (int c = 1; c < copies; ++c) t += sb_all[c * nsb + k];
+        if (dbits(t) << 1) atomicAdd(&sums[2 + k], t);
+    }
 }
 
 int vegas_grid(int64_t n)
@@ -322,10 +332,16 @@ extern "C" int pdf_vegas_accumulate(int32_t dim, int32_t n_bins, const double *w
     cudaStream_t s = (cudaStream_t)stream;
     PDF_CUDA(cudaMemsetAsync(sums, 0, (2 + (size_t)dim * n_bins) * sizeof(double), s));
     if (n == 0) return PDF_OK;
-    size_t smem = (size_t)dim * n_bins * sizeof(double);
-    int rc = allow_dynamic_smem((const void *)k_vegas_accumulate, smem);
+    const size_t one = (size_t)dim * n_bins * sizeof(double);
+    const bool per_warp = one * (kBlock / 32) <= 48 * 1024;
+    const void *kern = per_warp ? (const void *)k_vegas_accumulate<true> : (const void *)k_vegas_accumulate<false>;
+    const size_t smem = per_warp ? one * (kBlock / 32) : one;
+    int rc = allow_dynamic_smem(kern, smem);
     if (rc) return rc;
-    k_vegas_accumulate<<<vegas_grid(n), kBlock, smem, s>>>(dim, n_bins, w, bins, n, shift, sums);
+    if (per_warp)
+        k_vegas_accumulate<true><<<vegas_grid(n), kBlock, smem, s>>>(dim, n_bins, w, bins, n, shift, sums);
+    else
+        k_vegas_accumulate<false><<<vegas_grid(n), kBlock, smem, s>>>(dim, n_bins, w, bins, n, shift, sums);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
