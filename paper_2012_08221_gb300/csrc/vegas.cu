@@ -135,22 +135,44 @@ constexpr int kMaxVegasDim = 16;
 
 // The VEGAS map for an integrand the caller evaluates: one point per
 // thread, every dimension through its own bin edges.
+// TABLE: the block first tabulates each bin's lower edge, width and
+// n_bins x width in shared memory (the same operations as computing them
+// per point, so the same bits), which the points then read.
+template <bool TABLE>
 __global__ void __launch_bounds__(kBlock) k_vegas_map(int dim, int n_bins, const double *__restrict__ edges,
                                                       const double *__restrict__ v, int64_t n,
                                                       double *__restrict__ r, double *__restrict__ jac,
                                                       int *__restrict__ bins)
 {
+    extern __shared__ double tab[];          // [dim * n_bins][3]: lower edge, width, n_bins x width
     const double nb = (double)n_bins;
+    if (TABLE) {
+        for (int k = threadIdx.x; k < dim * n_bins; k += blockDim.x) {
+            const int d = k / n_bins, b = k - d * n_bins;
+            const double *e = edges + (size_t)d * (n_bins + 1);
+            const double lo = e[b], width = e[b + 1] - lo;
+            tab[3 * k] = lo;
+            tab[3 * k + 1] = width;
+            tab[3 * k + 2] = nb * width;
+        }
+        __syncthreads();
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double j = 1.0;
         for (int d = 0; d < dim; ++d) {
-            const double *e = edges + (size_t)d * (n_bins + 1);
             double vn = v[i * dim + d] * nb;
             int b = min(max((int)vn, 0), n_bins - 1);    // uniforms outside [0, 1) stay in range
-            double lo = __ldg(e + b), width = __ldg(e + b + 1) - lo;
-            r[i * dim + d] = fma(vn - (double)b, width, lo);
-            j *= nb * width;
+            if (TABLE) {
+                const double *t = tab + 3 * (d * n_bins + b);
+                r[i * dim + d] = fma(vn - (double)b, t[1], t[0]);
+                j *= t[2];
+            } else {
+                const double *e = edges + (size_t)d * (n_bins + 1);
+                double lo = __ldg(e + b), width = __ldg(e + b + 1) - lo;
+                r[i * dim + d] = fma(vn - (double)b, width, lo);
+                j *= nb * width;
+            }
             bins[i * dim + d] = b;
         }
         jac[i] = j;
@@ -314,7 +336,11 @@ extern "C" int pdf_vegas_map(int32_t dim, int32_t n_bins, const double *edges, c
     if (n == 0) return PDF_OK;
     if (!edges || !v || !r || !jac || !bins) return fail(PDF_E_ARG, "null array");
     cudaStream_t s = (cudaStream_t)stream;
-    k_vegas_map<<<vegas_grid(n), kBlock, 0, s>>>(dim, n_bins, edges, v, n, r, jac, bins);
+    const size_t tsmem = (size_t)dim * n_bins * 3 * sizeof(double);
+    if (tsmem <= 48 * 1024)
+        k_vegas_map<true><<<vegas_grid(n), kBlock, tsmem, s>>>(dim, n_bins, edges, v, n, r, jac, bins);
+    else
+        k_vegas_map<false><<<vegas_grid(n), kBlock, 0, s>>>(dim, n_bins, edges, v, n, r, jac, bins);
     PDF_CUDA(cudaGetLastError());
     return PDF_OK;
 }
